@@ -1,0 +1,185 @@
+"""Dual problem and Proximal-ADMM (Sec. 4: Eq. 3, Eq. 4, Alg. 1 and Sec. 4.1), FP64.
+
+Test infrastructure only (see ``oracle/__init__``).
+
+Conventions.  Constraint rows are the bilateral joint rows followed by one (t1, t2, n) triple
+per active contact.  ``cone_mu[k]`` is the friction coefficient of contact k.  All iterates live in
+the Jacobi-scaled space of Sec. 4.1: x~ = P^-1 x, v~ = P v, D~ = P D P.  The two tangential
+rows of a contact share one scale so the cone stays circular with mu~ = mu p_n / p_t.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+from scipy.linalg import solve_triangular
+
+
+# ----------------------------------------------------------------------------- Eq. 4
+def delassus(J, Minv):
+    """Eq. 4 with R = 0: D = J M^-1 J^T."""
+    return J @ Minv @ J.T
+
+
+def free_velocity(J, u_free, v_star):
+    """Eq. 4: v_f = J (u^- + dt M^-1 h) + v*, with u_free = u^- + dt M^-1 h."""
+    return J @ u_free + v_star
+
+
+def jacobi_scaling(D, n_bilateral, n_contacts, precond=True):
+    """Sec. 4.1: P = diag(D)^-1/2, once per step.  Tangential rows of a contact share
+    p_t = ((D_t1t1 + D_t2t2) / 2)^-1/2 so that the scaled friction cone stays a circular cone."""
+    m = D.shape[0]
+    if not precond:
+        return np.ones(m)
+    d = np.diag(D).copy()
+    p = 1.0 / np.sqrt(d)
+    for k in range(n_contacts):
+        i = n_bilateral + 3 * k
+        pt = 1.0 / math.sqrt(0.5 * (d[i] + d[i + 1]))
+        p[i] = p[i + 1] = pt
+    return p
+
+
+# ----------------------------------------------------------------------------- cones
+def desaxce(v, n_bilateral, mu):
+    """De Saxce operator (Sec. 4, Eq. 3): Gamma(v)_k = (0, 0, mu_k ||v_k,t||) on every contact
+    triple (t1, t2, n), zero on bilateral rows."""
+    s = np.zeros_like(v)
+    if len(mu):
+        vc = v[n_bilateral:].reshape(-1, 3)
+        s[n_bilateral + 2::3] = np.asarray(mu) * np.hypot(vc[:, 0], vc[:, 1])
+    return s
+
+
+def project_cone(x, n_bilateral, mu):
+    """Projection onto K = R^(bilateral) x prod_k K_mu_k, K_mu = {(t, n): ||t|| <= mu n}: the
+    closed-form Euclidean projection onto a second-order cone, contact by contact:
+    inside K -> unchanged; inside the polar cone (mu ||t|| <= -n) -> 0; otherwise onto the
+    boundary ray, n' = (mu ||t|| + n) / (1 + mu^2), t' = mu n' t / ||t||."""
+    y = x.copy()
+    if not len(mu):
+        return y
+    mu = np.asarray(mu, dtype=np.float64)
+    xc = x[n_bilateral:].reshape(-1, 3)
+    yc = y[n_bilateral:].reshape(-1, 3)
+    tn = np.hypot(xc[:, 0], xc[:, 1])
+    n = xc[:, 2]
+    inside = tn <= mu * n
+    polar = (~inside) & (mu * tn <= -n)
+    side = ~(inside | polar)
+    yc[polar] = 0.0
+    nn = (mu * tn + n) / (1.0 + mu * mu)
+    scale = np.where(side, mu * nn / np.where(tn > 0, tn, 1.0), 0.0)
+    yc[side, 0] = scale[side] * xc[side, 0]
+    yc[side, 1] = scale[side] * xc[side, 1]
+    yc[side, 2] = nn[side]
+    return y
+
+
+# ----------------------------------------------------------------------------- Alg. 1
+@dataclass
+class PadmmResult:
+    x: np.ndarray
+    y: np.ndarray
+    z: np.ndarray
+    iterations: int
+    r_p: float
+    r_d: float
+    r_c: float
+    converged: bool
+    restarts: int
+
+
+def residuals(x, x_prev, y, y_hat_prev, z, eta, rho, n_bilateral, n_contacts):
+    """Infinity-norm residuals of Sec. 4.1.  Primal: x - y.  Dual: the deviation of the x-step's
+    stationarity condition once the new iterates are substituted,
+    eta (x^i - x^{i-1}) + rho (y^i - y^_{i-1}).  Complementarity: max over contacts |y_k . z_k|."""
+    r_p = float(np.max(np.abs(x - y))) if x.size else 0.0
+    r_d = float(np.max(np.abs(eta * (x - x_prev) + rho * (y - y_hat_prev)))) if x.size else 0.0
+    r_c = 0.0
+    if n_contacts:
+        yc = y[n_bilateral:].reshape(-1, 3)
+        zc = z[n_bilateral:].reshape(-1, 3)
+        r_c = float(np.max(np.abs(np.sum(yc * zc, axis=1))))
+    return r_p, r_d, r_c
+
+
+def padmm(D, v_f, n_bilateral, mu, eta, rho, eps, n_max, x0=None, z0=None, nesterov=True,
+          restart_factor=0.999):
+    """Alg. 1 (one time step), on an already scaled problem (D, v_f, mu).
+
+    Steps per iteration i (hats are the Nesterov-extrapolated iterates, equal to the plain ones
+    without acceleration):
+      s^i  = Gamma(z^_{i-1})
+      x^i  = -(D + (eta + rho) I)^-1 (v_f + s^i - eta x^{i-1} - rho y^_{i-1} - z^_{i-1})
+      y^i  = Pi_K(x^i - z^_{i-1} / rho)
+      z^i  = z^_{i-1} - rho (x^i - y^i)
+      Nesterov with adaptive restart (O'Donoghue & Candes; Fast ADMM of Goldstein et al. 2014):
+      c^i = ||z^i - z^_{i-1}||^2 / rho + rho ||y^i - y^_{i-1}||^2; if c^i < 0.999 c^{i-1} then
+      a' = (1 + sqrt(1 + 4 a^2)) / 2 and (y^, z^) = (y, z)^i + (a - 1)/a' ((y, z)^i - (y, z)^{i-1}),
+      otherwise a = 1, (y^, z^) = (y, z)^{i-1} and c^i = c^{i-1} / 0.999.
+      stop when r_p, r_d, r_c < eps.
+    The factorisation of D + (eta + rho) I is computed once (Sec. 4: the left-hand side is
+    constant across iterations).  Returns y^N as lambda~.
+    """
+    m = D.shape[0]
+    n_contacts = len(mu)
+    A = D + (eta + rho) * np.eye(m)
+    L = np.linalg.cholesky(A) if m else np.zeros((0, 0))
+
+    def solve(b):
+        t = _forward(L, b)
+        return _backward(L, t)
+
+    x = np.zeros(m) if x0 is None else x0.copy()
+    y = x.copy()
+    z = np.zeros(m) if z0 is None else z0.copy()
+    y_hat, z_hat = y.copy(), z.copy()
+    a = 1.0
+    c_prev = math.inf
+    it = 0
+    r_p = r_d = r_c = math.inf
+    converged = False
+    restarts = 0
+    for it in range(1, n_max + 1):
+        s = desaxce(z_hat, n_bilateral, mu)
+        b = v_f + s - eta * x - rho * y_hat - z_hat
+        x_new = -solve(b)
+        y_new = project_cone(x_new - z_hat / rho, n_bilateral, mu)
+        z_new = z_hat - rho * (x_new - y_new)
+        r_p, r_d, r_c = residuals(x_new, x, y_new, y_hat, z_new, eta, rho, n_bilateral, n_contacts)
+        if nesterov:
+            c = float(np.dot(z_new - z_hat, z_new - z_hat) / rho + rho * np.dot(y_new - y_hat, y_new - y_hat))
+            if c < restart_factor * c_prev:
+                a_next = 0.5 * (1.0 + math.sqrt(1.0 + 4.0 * a * a))
+                beta = (a - 1.0) / a_next
+                y_hat_next = y_new + beta * (y_new - y)
+                z_hat_next = z_new + beta * (z_new - z)
+                a = a_next
+                c_prev = c
+            else:
+                restarts += 1
+                a = 1.0
+                y_hat_next, z_hat_next = y.copy(), z.copy()
+                c_prev = c_prev / restart_factor
+        else:
+            y_hat_next, z_hat_next = y_new, z_new
+        x, y, z = x_new, y_new, z_new
+        y_hat, z_hat = y_hat_next, z_hat_next
+        if r_p < eps and r_d < eps and r_c < eps:
+            converged = True
+            break
+    return PadmmResult(x=x, y=y, z=z, iterations=it, r_p=r_p, r_d=r_d, r_c=r_c, converged=converged,
+                       restarts=restarts)
+
+
+def _forward(L, b):
+    """Solve L t = b (forward substitution; library triangular solve)."""
+    return solve_triangular(L, b, lower=True, check_finite=False)
+
+
+def _backward(L, t):
+    """Solve L^T x = t (backward substitution; library triangular solve)."""
+    return solve_triangular(L, t, lower=True, trans="T", check_finite=False)

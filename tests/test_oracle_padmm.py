@@ -1,0 +1,231 @@
+"""Pins of the oracle's dual solver (Sec. 4: Eq. 3, Eq. 4, Alg. 1): cone projection against its
+definition, Proximal-ADMM against a direct KKT solve and against brute-force enumeration of
+contact modes, and the NCP conditions of the returned impulses."""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+import worldgen as wg
+from oracle import audit as A, padmm as PA, timestep as T
+
+
+# ----------------------------------------------------------------------------- cone projection
+def _proj_reference(x, mu):
+    """Euclidean projection onto {||t|| <= mu n} by brute force: a dense sample of the cone's
+    boundary plus the apex and x itself when feasible."""
+    best, bestd = np.zeros(3), np.linalg.norm(x)
+    if np.hypot(x[0], x[1]) <= mu * x[2]:
+        return x.copy()
+    for n in np.linspace(0.0, 3.0, 601):
+        for a in np.linspace(0.0, 2 * math.pi, 361):
+            y = np.array([mu * n * math.cos(a), mu * n * math.sin(a), n])
+            d = np.linalg.norm(x - y)
+            if d < bestd:
+                best, bestd = y, d
+    return best
+
+
+@pytest.mark.parametrize("mu", [0.0, 0.3, 1.0])
+def test_cone_projection_kkt_and_brute_force(mu):
+    rng = np.random.default_rng(20)
+    for _ in range(8):
+        x = rng.standard_normal(3)
+        y = PA.project_cone(x, 0, [mu])
+        # feasibility, the polar-cone condition and orthogonality (KKT of min ||y - x||, y in K)
+        assert math.hypot(y[0], y[1]) <= mu * y[2] + 1e-12
+        w = x - y                           # must lie in the polar cone  {mu ||t|| <= -n}
+        assert mu * math.hypot(w[0], w[1]) <= -w[2] + 1e-12 or np.linalg.norm(w) < 1e-12
+        assert abs(y @ w) < 1e-12
+        if mu > 0:
+            ref = _proj_reference(x, mu)
+            assert np.linalg.norm(x - y) <= np.linalg.norm(x - ref) + 1e-9
+    # bilateral rows pass through unchanged
+    x = rng.standard_normal(7)
+    np.testing.assert_array_equal(PA.project_cone(x, 4, [0.5])[:4], x[:4])
+
+
+def test_desaxce_operator():
+    v = np.array([1.0, 2.0, 3.0, 4.0, 0.0, -1.0])
+    s = PA.desaxce(v, 0, [0.5, 2.0])
+    np.testing.assert_allclose(s, [0, 0, 0.5 * math.hypot(1, 2), 0, 0, 2.0 * 4.0])
+
+
+# ----------------------------------------------------------------------------- bilateral worlds
+@pytest.mark.parametrize("maker,dt", [(wg.make_fourbar, 1e-3), (wg.make_excavator, 2e-3), (wg.make_stewart, 2e-3)])
+def test_padmm_matches_direct_kkt(maker, dt):
+    """Alg. 1 reaches the unique u+ of the KKT system Eq. 2 (solved directly) on worlds without
+    contacts, including over-constrained loops whose impulses are not unique."""
+    ws = maker(num_worlds=2, seed=3)
+    params = T.SolverParams(eps=1e-12, n_max=20000, rho=0.1)
+    st = T.initial_state(ws)
+    st, _ = T.step(ws, st, wg.actuation(ws, 3, 0), dt, params)      # move off the rest state
+    st, infos = T.step(ws, st, wg.actuation(ws, 3, 1), dt, params)
+    for i in infos:
+        M = np.linalg.inv(i.Minv)
+        u_kkt, _ = A.kkt_direct(i.J, M, M @ i.u_free, i.v_star)
+        scale = max(np.abs(u_kkt).max(), 9.81 * dt)
+        assert np.abs(i.u_plus - u_kkt).max() / scale < 1e-8
+        assert i.converged
+
+
+def test_nesterov_and_preconditioning_do_not_change_the_solution():
+    ws = wg.make_fourbar(num_worlds=2, seed=4)
+    st = T.initial_state(ws)
+    outs = []
+    for nest in (True, False):
+        for pre in (True, False):
+            params = T.SolverParams(eps=1e-12, n_max=50000, rho=0.1, nesterov=nest, precond=pre)
+            _, infos = T.step(ws, st, None, 1e-3, params)
+            outs.append(np.concatenate([i.u_plus for i in infos]))
+    for o in outs[1:]:
+        np.testing.assert_allclose(o, outs[0], atol=1e-9)
+
+
+# ----------------------------------------------------------------------------- contact closed forms
+def test_box_resting_on_plane_carries_its_weight():
+    """A box at rest on the plane: the normal impulses sum to m g dt, no friction, u+ = 0.  The
+    split among the corners is not unique, so only the sum is checked."""
+    m, dt = 1.3, 2e-3
+    ws = wg.make_box(mass=m, mu=0.6)
+    params = T.SolverParams(eps=1e-10, n_max=20000, rho=0.1)
+    st, infos = T.step(ws, T.initial_state(ws), None, dt, params)
+    i = infos[0]
+    assert len(i.contact_ids) == 4                 # the four bottom corners
+    lam = i.lam.reshape(-1, 3)
+    assert abs(lam[:, 2].sum() - m * 9.81 * dt) < 1e-8
+    assert np.abs(lam[:, :2]).max() < 1e-8
+    assert np.abs(i.u_plus).max() < 1e-8
+
+
+def test_sliding_box_decelerates_at_mu_g_and_stops():
+    """Coulomb sliding: v(t) = v0 - mu g t until rest at t = v0 / (mu g), then it stays at rest."""
+    mu, v0, dt = 0.4, 0.5, 1e-3
+    ws = wg.make_box(mass=1.0, mu=mu, v0=(v0, 0.0, 0.0))
+    params = T.SolverParams(eps=1e-10, n_max=20000, rho=0.1)
+    st = T.initial_state(ws)
+    vs = []
+    for k in range(150):
+        st, infos = T.step(ws, st, None, dt, params)
+        vs.append(st.u[0, 0])
+    t = dt * np.arange(1, 151)
+    expect = np.maximum(v0 - mu * 9.81 * t, 0.0)
+    np.testing.assert_allclose(vs, expect, atol=2e-6)
+    assert np.abs(st.u[0, 1:]).max() < 1e-6
+
+
+@pytest.mark.parametrize("angle,mu,sticks", [(0.3, 0.5, True), (0.5, 0.5, False), (0.2, 0.1, False)])
+def test_box_on_incline_sticks_iff_tan_theta_le_mu(angle, mu, sticks):
+    """Tilting gravity by theta is an incline of angle theta: the box sticks iff tan(theta) <= mu,
+    otherwise it accelerates at g (sin theta - mu cos theta) along the slope."""
+    g = 9.81
+    grav = (g * math.sin(angle), 0.0, -g * math.cos(angle))
+    ws = wg.make_box(mass=1.0, mu=mu, gravity=grav)
+    params = T.SolverParams(eps=1e-10, n_max=20000, rho=0.1)
+    st = T.initial_state(ws)
+    dt, n = 1e-3, 50
+    for _ in range(n):
+        st, _ = T.step(ws, st, None, dt, params)
+    a_expect = 0.0 if sticks else g * (math.sin(angle) - mu * math.cos(angle))
+    assert (math.tan(angle) <= mu) == sticks
+    assert abs(st.u[0, 0] - a_expect * n * dt) < 1e-6
+    assert abs(st.u[0, 2]) < 1e-6
+
+
+# ----------------------------------------------------------------------------- brute force
+def _planar_modes(D2, vf2, mu):
+    """All solutions of the planar (1-D friction) De Saxce NCP by enumeration of the contact modes
+    separate / stick / slide+ / slide-.  Each mode fixes two linear equations per contact in
+    (lambda, v = D lambda + v_f); a mode's solution is kept when its inequalities hold."""
+    k = len(mu)
+    sols = []
+    for modes in itertools.product(range(4), repeat=k):
+        A_ = np.zeros((2 * k, 2 * k))
+        b_ = np.zeros(2 * k)
+        for c, mode in enumerate(modes):
+            it, inn = 2 * c, 2 * c + 1
+            rows = []
+            if mode == 0:            # separate: lambda = 0
+                rows = [(np.eye(2 * k)[it], 0.0), (np.eye(2 * k)[inn], 0.0)]
+            elif mode == 1:          # stick: v = 0
+                rows = [(D2[it], -vf2[it]), (D2[inn], -vf2[inn])]
+            else:                    # slide: v_n = 0, lambda_t = -+ mu lambda_n
+                s = 1.0 if mode == 2 else -1.0
+                e = np.zeros(2 * k)
+                e[it] = 1.0
+                e[inn] = s * mu[c]
+                rows = [(D2[inn], -vf2[inn]), (e, 0.0)]
+            for j, (a, bb) in enumerate(rows):
+                A_[it + j] = a
+                b_[it + j] = bb
+        try:
+            lam = np.linalg.solve(A_, b_)
+        except np.linalg.LinAlgError:
+            continue
+        v = D2 @ lam + vf2
+        ok = True
+        for c, mode in enumerate(modes):
+            lt, ln, vt, vn = lam[2 * c], lam[2 * c + 1], v[2 * c], v[2 * c + 1]
+            tol = 1e-9
+            if mode == 0:
+                ok &= vn >= -tol
+            elif mode == 1:
+                ok &= abs(lt) <= mu[c] * ln + tol
+            else:
+                s = 1.0 if mode == 2 else -1.0
+                ok &= ln >= -tol and s * vt >= -tol
+        if ok:
+            sols.append(lam)
+    return sols
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_padmm_solution_is_one_of_the_enumerated_contact_modes(k):
+    """Random planar contact problems with k <= 3 contacts (embedded in 3-D with a decoupled second
+    tangent): the impulses found by Alg. 1 coincide with one of the brute-force mode solutions."""
+    rng = np.random.default_rng(30 + k)
+    for trial in range(6):
+        G = rng.standard_normal((2 * k, 2 * k + 1))
+        D2 = G @ G.T / (2 * k) + 0.05 * np.eye(2 * k)
+        vf2 = rng.standard_normal(2 * k)
+        mu = rng.uniform(0.2, 1.0, size=k)
+        m = 3 * k
+        D = np.eye(m)
+        vf = np.zeros(m)
+        idx = [3 * c for c in range(k)] + [3 * c + 2 for c in range(k)]
+        idx2 = [2 * c for c in range(k)] + [2 * c + 1 for c in range(k)]
+        for a, a2 in zip(idx, idx2):
+            vf[a] = vf2[a2]
+            for b, b2 in zip(idx, idx2):
+                D[a, b] = D2[a2, b2]
+        res = PA.padmm(D, vf, 0, mu, eta=1e-8, rho=0.5, eps=1e-12, n_max=50000)
+        lam2 = np.array([res.y[3 * c + j] for c in range(k) for j in (0, 2)])
+        sols = _planar_modes(D2, vf2, mu)
+        assert sols, "enumeration found no solution"
+        assert min(np.abs(s - lam2).max() for s in sols) < 1e-6
+        assert np.abs(res.y[1::3]).max() < 1e-9
+
+
+def test_biped_step_satisfies_ncp_conditions():
+    """One biped step from the assembled pose (consistent bias, so Alg. 1 can reach a tight
+    tolerance): lambda lies in the friction cones, v + Gamma(v) in the dual cones, they are
+    complementary, sliding contacts have zero normal velocity (Sec. 4), and the natural-map
+    residual is at the solver tolerance."""
+    ws = wg.make_biped(num_worlds=3, seed=5)
+    params = T.SolverParams(eps=1e-10, n_max=20000, rho=0.1)
+    st, infos = T.step(ws, T.initial_state(ws), wg.actuation(ws, 5, 0), 2e-3, params)
+    for i in infos:
+        assert i.converged
+        nb = i.n_bilateral
+        lam = i.lam[nb:].reshape(-1, 3)
+        v = (i.J @ i.u_plus + i.v_star)[nb:].reshape(-1, 3)
+        for (lt1, lt2, ln), (vt1, vt2, vn), mu in zip(lam, v, i.mu):
+            vt = math.hypot(vt1, vt2)
+            assert math.hypot(lt1, lt2) <= mu * ln + 1e-7
+            assert vn + mu * vt >= -1e-6
+            assert abs(lt1 * vt1 + lt2 * vt2 + ln * (vn + mu * vt)) < 1e-6
+            if vt > 1e-4 and ln > 1e-6:
+                assert abs(vn) < 1e-5
+        r_c, r_b = A.ncp_residual(i.J, i.u_plus, i.v_star, i.lam, i.p, nb, i.mu)
+        assert r_c < 1e-6 and r_b < 1e-6
