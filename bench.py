@@ -1,0 +1,351 @@
+#!/usr/bin/env python3
+"""Throughput of the constrained forward-dynamics step: world-steps/s on 4096 closed-loop bipeds.
+
+Workload (one "step" = one kamino_step over the whole batch, the full hot path in one launch):
+4096 synthetic bipeds (31 bodies, 36 revolute joints, 6 loops, 16 foot-corner contact candidates
+on the plane), dt = 2 ms, Gaussian actuation sigma = 5 N m from the counter-based generator,
+Proximal-ADMM to tol 1e-5 with N_max = 200, FP32.  The simulation really advances: K timed
+steps follow W warm-up steps from the standing pose.
+
+Reported: ``value`` = world-steps/s with the state resident in HBM (CUDA events on the launching
+stream, L2 flushed between timed steps); ``e2e`` = the same through the C ABI with the actuation
+uploaded from pinned host memory and the body state downloaded every step; ``roofline`` of the
+step kernel; ``cpu_baseline`` = the FP64 CPU oracle on a bounded sample.  ``--impl reference``
+times the oracle alone (the reference arm of this comparison).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "world-steps/s @4096 closed-loop bipeds, NCP residual<=1e-5; warm vs plain"
+UNIT = "world-steps/s"
+SM_COUNT, FP32_LANES = 152, 128
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=30)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    p.add_argument("--worlds", type=int, default=4096)
+    p.add_argument("--iters", type=int, default=200)
+    p.add_argument("--tol", type=float, default=1e-5)
+    p.add_argument("--dt", type=float, default=2e-3)
+    p.add_argument("--rho", type=float, default=0.1)
+    p.add_argument("--seed", type=int, default=0)
+    p.add_argument("--cpu-sample", type=int, default=128, help="worlds in the CPU-oracle sample")
+    p.add_argument("--no-cpu", action="store_true")
+    return p.parse_args()
+
+
+# ----------------------------------------------------------------------------- CPU oracle (baseline)
+def _oracle_chunk(job):
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    import worldgen as wg
+    from oracle import timestep as T
+    n, seed, worlds, dt, iters, tol, rho = job
+    ws = wg.make_biped(num_worlds=n, seed=seed)
+    tau = wg.actuation(ws, seed, 0)
+    params = T.SolverParams(rho=rho, eps=tol, n_max=iters)
+    t0 = time.perf_counter()
+    T.step(ws, T.initial_state(ws), tau, dt, params, worlds=worlds)
+    return time.perf_counter() - t0
+
+
+def oracle_rate(pool, cores, n_worlds, sample, seed, dt, iters, tol, rho):
+    """World-steps/s of the oracle over `sample` worlds (first step from the standing pose), split
+    over the pool's processes."""
+    worlds = list(range(sample))
+    chunks = [worlds[i::cores] for i in range(cores)]
+    jobs = [(sample, seed, c, dt, iters, tol, rho) for c in chunks if c]
+    t0 = time.perf_counter()
+    pool.map(_oracle_chunk, jobs)
+    wall = time.perf_counter() - t0
+    return sample / wall, wall
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+# ----------------------------------------------------------------------------- reference arm
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    cores = host_cores()
+    ctx = mp.get_context("spawn")
+    sample = max(8, min(args.cpu_sample, args.worlds))
+    with ctx.Pool(cores) as pool:
+        for _ in range(args.warmup):
+            oracle_rate(pool, cores, args.worlds, min(sample, cores), args.seed, args.dt, args.iters, args.tol, args.rho)
+        total, n = 0.0, 0
+        for _ in range(args.steps):
+            _, wall = oracle_rate(pool, cores, args.worlds, sample, args.seed, args.dt, args.iters, args.tol, args.rho)
+            total += wall
+            n += sample
+    value = n / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{args.worlds} closed-loop bipeds (31 bodies, 36 revolute, 6 loops), dt={args.dt}, "
+                                   f"tol={args.tol}, N_max={args.iters}", "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{sample} of {args.worlds} worlds x 1 step per timed step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def algorithmic_flops(rows, iters):
+    """Flops of the method per world-step: dense Cholesky m^3/3, per PADMM iteration a forward and
+    a backward substitution 2 m^2 plus ~20 m elementwise (De Saxce, projection, dual update,
+    Nesterov, residuals), block-sparse Delassus assembly ~ 2 * 12 * m * k (k ~ 8 rows sharing a
+    body)."""
+    m = rows.astype("float64")
+    it = iters.astype("float64")
+    return m ** 3 / 3.0 + it * (2.0 * m * m + 20.0 * m) + 2.0 * 12.0 * m * 8.0
+
+
+def run_gpu(args, rank, world):
+    import numpy as np
+
+    # CPU baseline first (spawned pool, before any CUDA call)
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cores = host_cores()
+        with mp.get_context("spawn").Pool(cores) as pool:
+            rate, wall = oracle_rate(pool, cores, args.worlds, min(args.cpu_sample, args.worlds), args.seed,
+                                     args.dt, args.iters, args.tol, args.rho)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{min(args.cpu_sample, args.worlds)} of {args.worlds} bipeds x 1 step (standing pose), "
+                         f"tol {args.tol}, N_max {args.iters}; {wall:.1f} s wall"}
+
+    import torch
+    import torch.distributed as dist
+    import worldgen as wg
+    import paper_2603_16536_gb300 as pkg
+    from paper_2603_16536_gb300 import kamino as K
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    seed = args.seed + rank
+    ws = wg.make_biped(num_worlds=args.worlds, seed=seed)
+    stream = torch.cuda.current_stream()
+    n_act = ws.n_act_max
+    total_steps = args.warmup + args.steps
+    tau_host = np.stack([wg.actuation(ws, seed, k) for k in range(total_steps)]).astype(np.float32)
+    tau_dev = torch.tensor(tau_host, device=dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)   # > L2 (129 MB)
+
+    def run_variant(warm_mode):
+        model = K.Model(ws, "fp32", K.make_params(rho=args.rho, warm_mode=warm_mode))
+        st = K.State(model, dev)
+        for k in range(args.warmup):
+            st.step(args.dt, args.iters, args.tol, tau_dev[k], stream)
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        ms, rows, its, conv = [], [], [], []
+        for k in range(args.warmup, total_steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st.step(args.dt, args.iters, args.tol, tau_dev[k], stream)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            rep = st.residuals()
+            rows.append(rep["num_rows"].copy())
+            its.append(rep["iterations"].copy())
+            conv.append(float(np.mean(rep["status"] == 0)))
+        torch.cuda.synchronize()
+        barrier()
+        return st, model, ms, np.concatenate(rows), np.concatenate(its), conv
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    st_c, model_c, ms_c, rows_c, its_c, conv_c = run_variant(K.WARM_COLD)
+    st_w, model_w, ms_w, rows_w, its_w, conv_w = run_variant(K.WARM_CACHED)
+    clocks = sampler.stop()
+
+    def reduce_max(v):
+        if world == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    t_cold = reduce_max(sum(ms_c) / 1e3)
+    t_warm = reduce_max(sum(ms_w) / 1e3)
+    units = args.worlds * args.steps * world
+    v_cold, v_warm = units / t_cold, units / t_warm
+
+    # ---- end to end through the C ABI: pinned host actuation in, body state out, every step
+    B = int(ws.world_body_offset[-1])
+    tau_pin = torch.tensor(tau_host).pin_memory()
+    q_out = torch.empty((B, 7), dtype=torch.float32).pin_memory()
+    u_out = torch.empty((B, 6), dtype=torch.float32).pin_memory()
+    lib = K.load_library()
+    import ctypes as C
+    tau_dev_ptr = C.c_void_p(st_w.tau.data_ptr())
+    sptr = C.c_void_p(stream.cuda_stream)
+    for k in range(args.warmup):
+        K._check(lib.kamino_state_upload(st_w.handle, K.BUF_TAU, C.c_void_p(tau_pin[k].data_ptr()), ws.num_worlds * n_act, sptr))
+        K._check(lib.kamino_step(st_w.handle, args.dt, args.iters, args.tol, tau_dev_ptr, sptr))
+    torch.cuda.synchronize()
+    barrier()
+    e_ms = []
+    for k in range(args.warmup, total_steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        K._check(lib.kamino_state_upload(st_w.handle, K.BUF_TAU, C.c_void_p(tau_pin[k].data_ptr()),
+                                         ws.num_worlds * n_act, sptr))
+        K._check(lib.kamino_step(st_w.handle, args.dt, args.iters, args.tol, tau_dev_ptr, sptr))
+        K._check(lib.kamino_state_download(st_w.handle, K.BUF_BODY_Q, C.c_void_p(q_out.data_ptr()), B * 7, sptr))
+        K._check(lib.kamino_state_download(st_w.handle, K.BUF_BODY_U, C.c_void_p(u_out.data_ptr()), B * 6, sptr))
+        e1.record(stream)
+        e1.synchronize()
+        e_ms.append(e0.elapsed_time(e1))
+    barrier()
+    t_e2e = reduce_max(sum(e_ms) / 1e3)
+    v_e2e = units / t_e2e
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    # ---- roofline of the step kernel (one launch = the whole batch) for the headline variant
+    peaks = measured_peaks()
+    smax = clocks.get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
+    alu_peak = SM_COUNT * FP32_LANES * 2 * smax * 1e6 / 1e12       # FP32 FMA lanes x clock, TFLOP/s
+    flops_w = float(algorithmic_flops(rows_w, its_w).sum()) / 1e12
+    achieved = flops_w / (sum(ms_w) / 1e3)
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tpath):
+        try:
+            traffic = json.load(open(tpath)).get("step_kernel_bytes_per_launch")
+        except Exception:
+            traffic = None
+    line = {
+        "metric": METRIC, "value": v_warm, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_warm / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{args.worlds} closed-loop bipeds per GPU (31 bodies, 36 revolute joints, 6 loops, "
+                               f"16 foot contact candidates, plane), dt={args.dt}, Gaussian actuation sigma=5, "
+                               f"PADMM tol={args.tol}, N_max={args.iters}, rho={args.rho}, cached warm start",
+                   "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}"},
+        "variants": {"cached_warm_fp32": {"value": v_warm, "mean_iterations": float(its_w.mean()),
+                                          "converged_fraction": float(np.mean(conv_w))},
+                     "plain_fp32_cold": {"value": v_cold, "mean_iterations": float(its_c.mean()),
+                                         "converged_fraction": float(np.mean(conv_c))},
+                     "warm_over_plain": v_warm / v_cold},
+        "mean_rows": float(rows_w.mean()),
+        "gpu_launches": args.steps,
+        "e2e": {"value": v_e2e, "unit": UNIT, "h2d_bytes_per_step": ws.num_worlds * n_act * 4,
+                "d2h_bytes_per_step": B * 13 * 4},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                     "frac": achieved / alu_peak, "traffic": traffic,
+                     "peak_note": f"FP32 FMA peak = {SM_COUNT} SMs x {FP32_LANES} lanes x 2 x {smax:.0f} MHz (derived)"},
+        "clocks": clocks,
+    }
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_gpu(args, rank, world)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

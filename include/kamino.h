@@ -1,0 +1,204 @@
+/*
+ * kamino.h -- C ABI of the GB300 (sm_103a) constrained forward-dynamics step.
+ *
+ * The library advances many independent "worlds" of rigid bodies in maximal coordinates by one
+ * time step each (Kamino, arXiv 2603.16536):
+ *   - body kinematics and the block-diagonal mass matrix             (Sec. 3, Eq. 1)
+ *   - joint constraints f(q) = 0, incl. loop closures, and frictional contacts with a Baumgarte
+ *     bias v*, assembled into the constraint Jacobian J              (Sec. 3, Eq. 2)
+ *   - the Delassus matrix D = J M^-1 J^T and free velocity v_f       (Sec. 4, Eq. 4)
+ *   - Jacobi preconditioning, a regularised factorisation of D + (eta + rho) I computed once per
+ *     step, and the Proximal-ADMM iteration with De Saxce correction, friction-cone projection
+ *     and Nesterov acceleration with adaptive restart                (Sec. 4, Alg. 1, Sec. 4.1)
+ *   - semi-implicit Euler with the SO(3) exponential map             (Sec. 3)
+ * Every stage runs in this library's own CUDA kernels.  There is no CPU fallback: every entry
+ * point that needs the GPU returns KAMINO_E_CUDA when no usable device is present.
+ *
+ * Conventions shared by every buffer:
+ *   - gravity is a model parameter; the ground plane is z = 0 with normal +z;
+ *   - a body's frame is its centre of mass and principal frame (diagonal inertia);
+ *   - pose q = (r[3], quat[4] stored x,y,z,w); twist u = (v[3], omega[3]), omega in the world frame;
+ *   - a joint frame is (pos[3], quat[4]) in its body's frame.  Revolute: hinge about the frame's
+ *     e3.  Prismatic: slide along e3.  Universal: free about e1 of the parent frame and e2 of the
+ *     child frame.  Spherical: point.  Fixed: weld.  joint_parent = -1 attaches to the world;
+ *   - constraint rows of a world: the joints' rows in joint order (revolute 5, prismatic 5,
+ *     universal 4, spherical 3, fixed 6), then one (t1, t2, n) triple per active contact in
+ *     candidate order.  A contact candidate is active when its signed distance is below
+ *     params.margin.
+ *
+ * Ownership: all host pointers passed in are read during the call only; the caller keeps them.
+ * Device memory of a model is allocated by the library (cudaMalloc) and freed by
+ * kamino_model_destroy.  State memory is either a caller-provided device buffer (e.g. from the
+ * PyTorch caching allocator) that must outlive the state, or allocated by the library when the
+ * buffer pointer is NULL.  Calls that take a stream are asynchronous on that stream (NULL = the
+ * legacy default stream); host-detectable errors are returned before anything is enqueued.
+ * Errors never cross the ABI as exceptions; kamino_last_error() gives a message for the calling
+ * thread's last failed call.
+ */
+#ifndef KAMINO_H
+#define KAMINO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    KAMINO_OK = 0,
+    KAMINO_E_INVALID_ARG = 1,   /* a NULL pointer, a size out of range, a bad parameter       */
+    KAMINO_E_TOPOLOGY = 2,      /* inconsistent world description (indices, offsets, masses)   */
+    KAMINO_E_NOMEM = 3,         /* device allocation failed or caller buffer too small        */
+    KAMINO_E_CUDA = 4,          /* a CUDA runtime call failed (also: no device present)       */
+    KAMINO_E_NONFINITE = 5,     /* reserved for per-world status words (see kamino_residual)   */
+    KAMINO_E_TIMEOUT = 6,       /* reserved: every device loop of this library is bounded     */
+    KAMINO_E_UNSUPPORTED = 7    /* a size this build does not support (e.g. too many rows)     */
+} kamino_status;
+
+enum { KAMINO_JOINT_REVOLUTE = 0, KAMINO_JOINT_PRISMATIC = 1, KAMINO_JOINT_UNIVERSAL = 2,
+       KAMINO_JOINT_SPHERICAL = 3, KAMINO_JOINT_FIXED = 4 };
+enum { KAMINO_TERRAIN_NONE = 0, KAMINO_TERRAIN_PLANE = 1, KAMINO_TERRAIN_HEIGHTFIELD = 2 };
+enum { KAMINO_FP32 = 0, KAMINO_FP64 = 1 };
+/* warm start of Alg. 1 (Sec. 4.1): zero, the impulses cached by the previous step, or impulses
+ * supplied by the caller through KAMINO_BUF_WARM (e.g. a learned predictor). */
+enum { KAMINO_WARM_COLD = 0, KAMINO_WARM_CACHED = 1, KAMINO_WARM_EXTERNAL = 2 };
+
+/* per-world status bits in kamino_residual.status */
+enum { KAMINO_WORLD_NOT_CONVERGED = 1, KAMINO_WORLD_NONFINITE = 2 };
+
+typedef struct {
+    double eta;        /* proximal regularisation, Alg. 1 (scaled units), >= 0              */
+    double rho;        /* augmented-Lagrangian penalty, Alg. 1 (scaled units), > 0          */
+    double beta;       /* Baumgarte factor of the bias v* (Sec. 3), in [0, 1]               */
+    double margin;     /* contact activation distance in metres, >= 0                       */
+    int32_t nesterov;  /* 1: Nesterov acceleration with adaptive restart (Sec. 4.1)         */
+    int32_t precond;   /* 1: Jacobi preconditioning P = diag(D)^-1/2 (Sec. 4.1)              */
+    int32_t warm_mode; /* KAMINO_WARM_*                                                       */
+    int32_t reserved;
+} kamino_solver_params;
+
+/* World description, sum-allocated over worlds: world w owns bodies
+ * [world_body_offset[w], world_body_offset[w+1]) and likewise joints and contact candidates.
+ * Body indices inside joint_parent / joint_child / contact_body are LOCAL to the world. */
+typedef struct {
+    int32_t num_worlds;
+    int32_t precision;                  /* KAMINO_FP32 or KAMINO_FP64 (storage and arithmetic) */
+    const int32_t *world_body_offset;   /* [W+1] */
+    const int32_t *world_joint_offset;  /* [W+1] */
+    const int32_t *world_contact_offset;/* [W+1] */
+    const int32_t *world_num_actuators; /* [W]   length of the world's actuation vector        */
+    const double  *world_mu;            /* [W]   Coulomb friction coefficient, >= 0            */
+    const double  *body_mass;           /* [B]   kg, > 0                                       */
+    const double  *body_inertia;        /* [B*3] principal moments, kg m^2, > 0                */
+    const int32_t *joint_type;          /* [J]   KAMINO_JOINT_*                                */
+    const int32_t *joint_parent;        /* [J]   local body index or -1 (world)                */
+    const int32_t *joint_child;         /* [J]   local body index                              */
+    const int32_t *joint_actuator;      /* [J]   slot in the actuation vector or -1            */
+    const double  *joint_frame_parent;  /* [J*7] pos(3) + quat xyzw(4) in the parent frame    */
+    const double  *joint_frame_child;   /* [J*7] pos(3) + quat xyzw(4) in the child frame      */
+    const int32_t *contact_body;        /* [C]   local body index                              */
+    const double  *contact_point;       /* [C*3] point in the body frame                       */
+    double gravity[3];
+    int32_t terrain_kind;               /* KAMINO_TERRAIN_*                                     */
+    int32_t hf_nx, hf_ny;               /* heightfield vertex counts (>= 2 each)                */
+    double hf_origin[2];                /* world (x, y) of vertex (0, 0)                        */
+    double hf_cell;                     /* vertex spacing, > 0                                  */
+    const double *hf_heights;           /* [ny*nx] heights, vertex (i, j) at [j*nx + i]         */
+    const double *body_q0;              /* [B*7] initial poses (NULL: origin, identity)         */
+    const double *body_u0;              /* [B*6] initial twists (NULL: zero)                    */
+    kamino_solver_params params;
+} kamino_model_desc;
+
+typedef struct {
+    int32_t num_worlds;
+    int32_t num_bodies;        /* B, all worlds                                              */
+    int32_t max_bodies;        /* max bodies of one world                                    */
+    int32_t max_rows;          /* max constraint rows of one world (all candidates active)   */
+    int32_t n_act_max;         /* row length of the actuation input [W][n_act_max]           */
+    int32_t cache_len;         /* length of the impulse cache / external warm-start buffer  */
+    int32_t precision;
+    int32_t threads_per_world; /* CTA size of the step kernel                                */
+    int64_t smem_bytes;        /* dynamic shared memory of one world's CTA                   */
+} kamino_model_info;
+
+/* Per-world solver report (8 words), written by kamino_step (Sec. 4.1, convergence budget). */
+typedef struct {
+    int32_t iterations;        /* PADMM iterations run                                       */
+    int32_t status;            /* KAMINO_WORLD_* bits, 0 = converged and finite              */
+    int32_t num_rows;          /* constraint rows this step                                  */
+    int32_t num_contacts;      /* active contacts this step                                  */
+    float r_primal;            /* ||x - y||_inf   (scaled units)                              */
+    float r_dual;              /* ||eta (x - x_prev) + rho (y - y_hat_prev)||_inf             */
+    float r_compl;             /* max over contacts |y_k . z_k|                               */
+    float reserved;
+} kamino_residual;
+
+/* Buffers of a state, for zero-copy access (kamino_state_get). Element type is float for
+ * KAMINO_FP32 models and double for KAMINO_FP64 models, except RESIDUAL (kamino_residual). */
+typedef enum {
+    KAMINO_BUF_BODY_Q = 0,     /* [B*7]  poses                                               */
+    KAMINO_BUF_BODY_U = 1,     /* [B*6]  twists                                              */
+    KAMINO_BUF_CACHE = 2,      /* [cache_len] impulses lambda* of the last step, physical units:
+                                  world w's joint rows, then 3 per contact CANDIDATE (zero for
+                                  candidates that were not active)                          */
+    KAMINO_BUF_WARM = 3,       /* [cache_len] caller-supplied initial impulses (warm_mode 2)  */
+    KAMINO_BUF_RESIDUAL = 4,   /* [W] kamino_residual                                         */
+    KAMINO_BUF_TAU = 5         /* [W*n_act_max] actuation staging buffer: fill it (upload or
+                                  zero-copy) and pass its device pointer to kamino_step        */
+} kamino_buffer;
+
+typedef struct kamino_model_s *kamino_model_t;
+typedef struct kamino_state_s *kamino_state_t;
+
+/* Validate a world description and copy it to the device.  Host-side checks (offsets monotone,
+ * indices in range, parent != child, positive masses and inertias, unit-normalisable frame
+ * quaternions, supported sizes, valid parameters) run first and return KAMINO_E_TOPOLOGY,
+ * KAMINO_E_INVALID_ARG or KAMINO_E_UNSUPPORTED without touching the GPU. */
+kamino_status kamino_model_create(const kamino_model_desc *desc, kamino_model_t *out);
+kamino_status kamino_model_destroy(kamino_model_t model);
+kamino_status kamino_model_get_info(kamino_model_t model, kamino_model_info *out);
+/* Replace the solver parameters of a model (host-side only, takes effect at the next step). */
+kamino_status kamino_model_set_params(kamino_model_t model, const kamino_solver_params *params);
+
+/* Bytes of device memory a state of this model needs (256-byte aligned sub-buffers). */
+kamino_status kamino_state_bytes(kamino_model_t model, size_t *bytes);
+/* Create a state over `device_buffer` (>= kamino_state_bytes bytes, 256-byte aligned, owned by the
+ * caller) or, when `device_buffer` is NULL, over memory the library allocates and later frees.
+ * The state starts at the description's initial poses and twists with zero impulse caches
+ * (synchronous: the state is ready when the call returns). */
+kamino_status kamino_state_alloc(kamino_model_t model, void *device_buffer, size_t bytes,
+                                 kamino_state_t *out);
+kamino_status kamino_state_free(kamino_state_t state);
+/* Device pointer and element count of one buffer of the state (zero-copy view). */
+kamino_status kamino_state_get(kamino_state_t state, kamino_buffer which, void **dev_ptr,
+                               int64_t *count);
+/* Copy `count` elements (the state's element type, or kamino_residual) from / to host memory;
+ * asynchronous on `stream` (pinned host memory makes it truly asynchronous). */
+kamino_status kamino_state_upload(kamino_state_t state, kamino_buffer which, const void *host,
+                                  int64_t count, void *stream);
+kamino_status kamino_state_download(kamino_state_t state, kamino_buffer which, void *host,
+                                    int64_t count, void *stream);
+
+/* One time step of every world of the state (the whole hot path, one kernel launch).
+ *   dt      time step in seconds, > 0
+ *   iters   N_max of Alg. 1, >= 1
+ *   tol     epsilon of the convergence test of Alg. 1 / Sec. 4.1, >= 0 (0 = run N_max)
+ *   tau_dev device pointer to the actuation [W][n_act_max] (torques about revolute hinges, forces
+ *           along prismatic axes, the state's element type) or NULL for none
+ *   stream  cudaStream_t to launch on (NULL = legacy default stream)
+ * Per-world failures (not converged within iters, non-finite result) are reported in the
+ * RESIDUAL buffer; the return value covers argument and launch errors only. */
+kamino_status kamino_step(kamino_state_t state, double dt, int32_t iters, double tol,
+                          const void *tau_dev, void *stream);
+
+/* Copy the per-world reports into `out_dev` (device memory, [W] kamino_residual) on `stream`. */
+kamino_status kamino_residuals(kamino_state_t state, kamino_residual *out_dev, void *stream);
+
+/* Message of the calling thread's last failed call ("" if none). */
+const char *kamino_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KAMINO_H */

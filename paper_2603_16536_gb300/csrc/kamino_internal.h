@@ -1,0 +1,112 @@
+// Internal declarations shared by the host API (kamino_api.cu) and the step kernel
+// (kamino_step.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "kamino.h"
+
+namespace kamino {
+
+constexpr int kThreads = 256;        // CTA size of the per-world step kernel (8 warps)
+constexpr int kWarps = kThreads / 32;
+constexpr int kMaxRowsPad = 288;     // largest padded row count the step kernel supports
+constexpr int kMaxChunks = kMaxRowsPad / 32;
+constexpr int kMaxCandidates = 64;   // contact candidates per world
+
+// Device-side view of a model (all pointers are device pointers; T = float or double).
+template <typename T>
+struct ModelView {
+    int num_worlds;
+    int n_act_max;
+    const int4 *world_a;       // (body_offset, joint_offset, contact_offset, cache_offset)
+    const int4 *world_b;       // (num_bodies, num_joints, num_candidates, num_bilateral_rows)
+    const T *world_mu;         // [W]
+    const T *body_mass;        // [B]
+    const T *body_inertia;     // [B*3]
+    const int4 *joint_meta;    // (type, parent, child, actuator)
+    const int *joint_row;      // first row of the joint inside its world
+    const T *joint_frames;     // [J*14]: parent pos3 quat4, child pos3 quat4
+    const int *contact_body;   // [C]
+    const T *contact_point;    // [C*3]
+    int terrain_kind, hf_nx, hf_ny;
+    T hf_x0, hf_y0, hf_cell;
+    const T *hf_heights;       // [ny*nx]
+    T gx, gy, gz;
+};
+
+template <typename T>
+struct StepArgs {
+    ModelView<T> m;
+    T *body_q;                 // [B*7]
+    T *body_u;                 // [B*6]
+    T *cache;                  // [cache_len]
+    const T *warm;             // [cache_len] (external warm start) or nullptr
+    kamino_residual *res;      // [W]
+    const T *tau;              // [W*n_act_max] or nullptr
+    const int *world_order;    // optional permutation of worlds (nullptr = identity)
+    T dt, tol, eta, rho, beta, margin;
+    int iters, nesterov, precond, warm_mode;
+    // shared-memory layout bounds (maxima over the launched worlds)
+    int nb_max, nj_max, nc_max, mp_max;
+};
+
+// Byte offsets of the per-world shared-memory working set.
+struct Layout {
+    size_t bq, bu, bR, bI, bIinv, bminv, bufree, jwr, cid, cslot, rbody, rJ, rvs;
+    size_t vf, p, x, xn, y, z, yh, zh, b, mut, X, A, red, misc, total;
+};
+
+__host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+template <typename T>
+__host__ __device__ inline Layout make_layout(int nb, int nj, int nc, int mp, int nb_panel) {
+    Layout L{};
+    size_t o = 0;
+    auto take = [&](size_t &field, size_t bytes) { field = o; o = align_up(o + bytes, 16); };
+    const size_t s = sizeof(T);
+    take(L.bq, nb * 7 * s);
+    take(L.bu, nb * 6 * s);
+    take(L.bR, nb * 9 * s);
+    take(L.bI, nb * 3 * s);
+    take(L.bIinv, nb * 6 * s);
+    take(L.bminv, nb * s);
+    take(L.bufree, nb * 6 * s);
+    take(L.jwr, nj * 12 * s);
+    take(L.cid, nc * sizeof(int));
+    take(L.cslot, nc * sizeof(int));
+    take(L.rbody, mp * 2 * sizeof(int));
+    take(L.rJ, mp * 12 * s);
+    take(L.rvs, mp * s);
+    take(L.vf, mp * s);
+    take(L.p, mp * s);
+    take(L.x, mp * s);
+    take(L.xn, mp * s);
+    take(L.y, mp * s);
+    take(L.z, mp * s);
+    take(L.yh, mp * s);
+    take(L.zh, mp * s);
+    take(L.b, mp * s);
+    take(L.mut, (nc > 0 ? nc : 1) * s);
+    size_t xs = (size_t)mp * 12;
+    size_t sweep = (size_t)2 * mp * nb_panel + (size_t)nb_panel * nb_panel;
+    if (sweep > xs) xs = sweep;
+    if ((size_t)kWarps * mp > xs) xs = (size_t)kWarps * mp;
+    take(L.X, xs * s);
+    take(L.A, (size_t)mp * (mp + 1) / 2 * s);
+    take(L.red, 2 * 4 * kWarps * s);
+    take(L.misc, 16 * sizeof(int));
+    L.total = o;
+    return L;
+}
+
+// Launchers (kamino_step.cu).  Return the launch error (cudaSuccess on success).
+template <typename T>
+cudaError_t launch_step(const StepArgs<T> &args, int num_worlds, int nb_panel, size_t smem,
+                        cudaStream_t stream);
+template <typename T>
+cudaError_t prepare_step(int nb_panel, size_t smem);
+
+}  // namespace kamino

@@ -1,0 +1,848 @@
+// Fused per-world constrained forward-dynamics step for sm_103a (Kamino, arXiv 2603.16536).
+//
+// One CTA (256 threads) owns one world for the whole step and keeps its working set in shared
+// memory; nothing but the state, the inputs and the impulse cache touches HBM.
+//
+//   1  body kinematics: R(q), world inverse inertia, M^-1 (Sec. 3, Eq. 1)
+//   2  joint rows (incl. loop closures) with Baumgarte bias; actuation as J_d^T tau (Sec. 3)
+//   3  contacts against the terrain, compacted in candidate order, rows (t1, t2, n) (Sec. 3)
+//   4  u_free = u + dt M^-1 h (gyroscopic + gravity + actuation); v_f = J u_free + v* (Eq. 4)
+//   5  D = J M^-1 J^T from the two 1x6 blocks of every row (block-sparse), Jacobi scaling
+//      P = diag(D)^-1/2 with a shared tangential scale per contact (Sec. 4.1), packed lower
+//      storage of A = P D P + (eta + rho) I
+//   6  warm start (cached or external impulses)                          (Sec. 4.1)
+//   7  regularised factorisation, computed once per step (Sec. 4: A is constant across the
+//      iterations).  The paper factorises with block-Cholesky and runs a backward-forward
+//      pass every iteration; here A^-1 is formed once by a blocked symmetric sweep
+//      (Gauss-Jordan on the SPD matrix, panels of NB columns, register-tiled rank-NB updates),
+//      so every iteration's solve is one fully parallel symmetric matrix-vector product instead
+//      of two length-m dependency chains.  The iterates are the same up to rounding.
+//   8  Proximal-ADMM (Alg. 1): De Saxce correction, solve, cone projection, dual update,
+//      Nesterov with adaptive restart, infinity-norm residuals, early exit
+//   9  lambda = P y; u+ = u_free + M^-1 J^T lambda; r+ = r + dt v+, q+ = exp(dt w+) q (Sec. 3);
+//      impulse cache (warm start of the next step) and the per-world report.
+//
+// Every loop is bounded (N_max iterations at most); there are no inter-CTA waits.
+
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "kamino_internal.h"
+
+namespace kamino {
+namespace {
+
+// ----------------------------------------------------------------------------- small math
+template <typename T> __device__ __forceinline__ T rsq(T x);
+template <> __device__ __forceinline__ float rsq<float>(float x) { return rsqrtf(x); }
+template <> __device__ __forceinline__ double rsq<double>(double x) { return rsqrt(x); }
+
+template <typename T>
+__device__ __forceinline__ void cross3(const T *a, const T *b, T *c) {
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+template <typename T>
+__device__ __forceinline__ T dot3(const T *a, const T *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+// rotation matrix (row-major) of the unit quaternion (x, y, z, w)
+template <typename T>
+__device__ __forceinline__ void quat_rot(const T *q, T *R) {
+    const T x = q[0], y = q[1], z = q[2], w = q[3];
+    R[0] = T(1) - T(2) * (y * y + z * z); R[1] = T(2) * (x * y - z * w); R[2] = T(2) * (x * z + y * w);
+    R[3] = T(2) * (x * y + z * w); R[4] = T(1) - T(2) * (x * x + z * z); R[5] = T(2) * (y * z - x * w);
+    R[6] = T(2) * (x * z - y * w); R[7] = T(2) * (y * z + x * w); R[8] = T(1) - T(2) * (x * x + y * y);
+}
+template <typename T>
+__device__ __forceinline__ void matvec3(const T *R, const T *v, T *o) {
+    o[0] = R[0] * v[0] + R[1] * v[1] + R[2] * v[2];
+    o[1] = R[3] * v[0] + R[4] * v[1] + R[5] * v[2];
+    o[2] = R[6] * v[0] + R[7] * v[1] + R[8] * v[2];
+}
+template <typename T>
+__device__ __forceinline__ void matTvec3(const T *R, const T *v, T *o) {
+    o[0] = R[0] * v[0] + R[3] * v[1] + R[6] * v[2];
+    o[1] = R[1] * v[0] + R[4] * v[1] + R[7] * v[2];
+    o[2] = R[2] * v[0] + R[5] * v[1] + R[8] * v[2];
+}
+template <typename T>
+__device__ __forceinline__ void matmul3(const T *A, const T *B, T *C) {
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            C[3 * i + j] = A[3 * i] * B[j] + A[3 * i + 1] * B[3 + j] + A[3 * i + 2] * B[6 + j];
+}
+// symmetric 3x3 stored (xx, yy, zz, xy, xz, yz) times v
+template <typename T>
+__device__ __forceinline__ void symvec3(const T *S, const T *v, T *o) {
+    o[0] = S[0] * v[0] + S[3] * v[1] + S[4] * v[2];
+    o[1] = S[3] * v[0] + S[1] * v[1] + S[5] * v[2];
+    o[2] = S[4] * v[0] + S[5] * v[1] + S[2] * v[2];
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+template <typename T>
+__device__ __forceinline__ T warp_max(T v) {
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// packed lower-triangular, column-major storage of a symmetric mp x mp matrix
+__device__ __forceinline__ int col_start(int j, int mp) { return j * mp - (j * (j - 1)) / 2; }
+__device__ __forceinline__ int pidx(int i, int j, int mp) {  // requires i >= j
+    return col_start(j, mp) + (i - j);
+}
+__device__ __forceinline__ int sidx(int i, int j, int mp) { return i >= j ? pidx(i, j, mp) : pidx(j, i, mp); }
+
+// Duff et al. 2017 branchless orthonormal basis: (t1, t2, n) right-handed
+template <typename T>
+__device__ __forceinline__ void onb(const T *n, T *t1, T *t2) {
+    const T sign = n[2] >= T(0) ? T(1) : T(-1);
+    const T a = T(-1) / (sign + n[2]);
+    const T b = n[0] * n[1] * a;
+    t1[0] = T(1) + sign * n[0] * n[0] * a; t1[1] = sign * b; t1[2] = -sign * n[0];
+    t2[0] = b; t2[1] = sign + n[1] * n[1] * a; t2[2] = -n[1];
+}
+
+// Signed distance of p to the terrain and the terrain normal there.  Plane: z = 0.  Heightfield:
+// cells split along the (i, j)-(i+1, j+1) diagonal; (x, y) clamped into the grid.
+template <typename T>
+__device__ __forceinline__ T terrain(const ModelView<T> &m, const T *p, T *n) {
+    if (m.terrain_kind == KAMINO_TERRAIN_PLANE) {
+        n[0] = T(0); n[1] = T(0); n[2] = T(1);
+        return p[2];
+    }
+    const T h = m.hf_cell;
+    T gx = (p[0] - m.hf_x0) / h, gy = (p[1] - m.hf_y0) / h;
+    gx = fmin(fmax(gx, T(0)), T(m.hf_nx - 1));
+    gy = fmin(fmax(gy, T(0)), T(m.hf_ny - 1));
+    int i = min((int)floor(gx), m.hf_nx - 2);
+    int j = min((int)floor(gy), m.hf_ny - 2);
+    const T fx = gx - T(i), fy = gy - T(j);
+    const T *H = m.hf_heights;
+    const T h00 = H[j * m.hf_nx + i], h11 = H[(j + 1) * m.hf_nx + i + 1];
+    T e1[3], e2[3];
+    if (fx >= fy) {   // vertices (i,j), (i+1,j), (i+1,j+1)
+        const T h10 = H[j * m.hf_nx + i + 1];
+        e1[0] = h; e1[1] = T(0); e1[2] = h10 - h00;
+        e2[0] = h; e2[1] = h; e2[2] = h11 - h00;
+    } else {          // vertices (i,j), (i+1,j+1), (i,j+1)
+        const T h01 = H[(j + 1) * m.hf_nx + i];
+        e1[0] = h; e1[1] = h; e1[2] = h11 - h00;
+        e2[0] = T(0); e2[1] = h; e2[2] = h01 - h00;
+    }
+    cross3(e1, e2, n);
+    const T inv = rsq(dot3(n, n));
+    n[0] *= inv; n[1] *= inv; n[2] *= inv;
+    const T q[3] = {gx * h - T(i) * h, gy * h - T(j) * h, p[2] - h00};
+    return dot3(q, n);
+}
+
+template <typename T>
+__device__ __forceinline__ void put_row(int *rbody, T *rJ, T *rvs, int row, int ba, int bb, const T *Ja, const T *Jb,
+                                        T vstar) {
+    rbody[2 * row] = ba;
+    rbody[2 * row + 1] = bb;
+    T *J = rJ + 12 * row;
+    for (int k = 0; k < 6; ++k) { J[k] = Ja[k]; J[6 + k] = Jb[k]; }
+    rvs[row] = vstar;
+}
+
+// Joint rows of one joint (Sec. 3): positional rows along world axes, angular rows along the
+// parent frame's axes; returns the actuation wrench (J_d^T value) for parent and child.
+template <typename T>
+__device__ void joint_rows(int type, int par, int ch, const T *fr, const T *bq, const T *bR, int row0, T kbias,
+                           int *rbody, T *rJ, T *rvs, bool actuated, T value, T *wr) {
+    T rA[3] = {T(0), T(0), T(0)}, RA[9] = {T(1), T(0), T(0), T(0), T(1), T(0), T(0), T(0), T(1)};
+    if (par >= 0) {
+        for (int k = 0; k < 3; ++k) rA[k] = bq[7 * par + k];
+        for (int k = 0; k < 9; ++k) RA[k] = bR[9 * par + k];
+    }
+    const T *rB = bq + 7 * ch;
+    const T *RB = bR + 9 * ch;
+    T cA[3], cB[3], pA[3], pB[3], QA[9], QB[9], FA[9], FB[9];
+    matvec3(RA, fr, cA);
+    matvec3(RB, fr + 7, cB);
+    for (int k = 0; k < 3; ++k) { pA[k] = rA[k] + cA[k]; pB[k] = rB[k] + cB[k]; }
+    quat_rot(fr + 3, QA);
+    quat_rot(fr + 10, QB);
+    matmul3(RA, QA, FA);
+    matmul3(RB, QB, FB);
+    T a[3][3], b[3][3];   // a[k] = k-th axis of the parent-side frame (column k)
+    for (int k = 0; k < 3; ++k)
+        for (int r = 0; r < 3; ++r) { a[k][r] = FA[3 * r + k]; b[k][r] = FB[3 * r + k]; }
+    T dp[3] = {pB[0] - pA[0], pB[1] - pA[1], pB[2] - pA[2]};
+    T Ja[6], Jb[6], t[3];
+    int row = row0;
+    const bool positional = (type == KAMINO_JOINT_REVOLUTE || type == KAMINO_JOINT_UNIVERSAL ||
+                             type == KAMINO_JOINT_SPHERICAL || type == KAMINO_JOINT_FIXED);
+    if (positional) {
+        for (int k = 0; k < 3; ++k) {
+            T e[3] = {T(k == 0), T(k == 1), T(k == 2)};
+            cross3(cA, e, t);
+            Ja[0] = -e[0]; Ja[1] = -e[1]; Ja[2] = -e[2]; Ja[3] = -t[0]; Ja[4] = -t[1]; Ja[5] = -t[2];
+            cross3(cB, e, t);
+            Jb[0] = e[0]; Jb[1] = e[1]; Jb[2] = e[2]; Jb[3] = t[0]; Jb[4] = t[1]; Jb[5] = t[2];
+            put_row(rbody, rJ, rvs, row++, par, ch, Ja, Jb, kbias * dp[k]);
+        }
+    }
+    if (type == KAMINO_JOINT_REVOLUTE) {
+        T err[3];
+        cross3(a[2], b[2], err);
+        for (int k = 0; k < 2; ++k) {
+            for (int r = 0; r < 3; ++r) { Ja[r] = T(0); Jb[r] = T(0); Ja[3 + r] = -a[k][r]; Jb[3 + r] = a[k][r]; }
+            put_row(rbody, rJ, rvs, row++, par, ch, Ja, Jb, kbias * dot3(a[k], err));
+        }
+    } else if (type == KAMINO_JOINT_PRISMATIC) {
+        T lever[3] = {pB[0] - rA[0], pB[1] - rA[1], pB[2] - rA[2]};
+        for (int k = 0; k < 2; ++k) {
+            cross3(lever, a[k], t);
+            Ja[0] = -a[k][0]; Ja[1] = -a[k][1]; Ja[2] = -a[k][2]; Ja[3] = -t[0]; Ja[4] = -t[1]; Ja[5] = -t[2];
+            cross3(cB, a[k], t);
+            Jb[0] = a[k][0]; Jb[1] = a[k][1]; Jb[2] = a[k][2]; Jb[3] = t[0]; Jb[4] = t[1]; Jb[5] = t[2];
+            put_row(rbody, rJ, rvs, row++, par, ch, Ja, Jb, kbias * dot3(a[k], dp));
+        }
+    }
+    if (type == KAMINO_JOINT_PRISMATIC || type == KAMINO_JOINT_FIXED) {
+        T err[3] = {T(0), T(0), T(0)};
+        for (int i = 0; i < 3; ++i) {
+            cross3(a[i], b[i], t);
+            err[0] += T(0.5) * t[0]; err[1] += T(0.5) * t[1]; err[2] += T(0.5) * t[2];
+        }
+        for (int k = 0; k < 3; ++k) {
+            for (int r = 0; r < 3; ++r) { Ja[r] = T(0); Jb[r] = T(0); Ja[3 + r] = -a[k][r]; Jb[3 + r] = a[k][r]; }
+            put_row(rbody, rJ, rvs, row++, par, ch, Ja, Jb, kbias * dot3(a[k], err));
+        }
+    }
+    if (type == KAMINO_JOINT_UNIVERSAL) {
+        T n[3];
+        cross3(a[0], b[1], n);
+        for (int r = 0; r < 3; ++r) { Ja[r] = T(0); Jb[r] = T(0); Ja[3 + r] = n[r]; Jb[3 + r] = -n[r]; }
+        put_row(rbody, rJ, rvs, row++, par, ch, Ja, Jb, kbias * dot3(a[0], b[1]));
+    }
+    for (int k = 0; k < 12; ++k) wr[k] = T(0);
+    if (actuated) {
+        if (type == KAMINO_JOINT_REVOLUTE) {
+            for (int r = 0; r < 3; ++r) { wr[3 + r] = -value * a[2][r]; wr[9 + r] = value * a[2][r]; }
+        } else if (type == KAMINO_JOINT_PRISMATIC) {
+            T lever[3] = {pB[0] - rA[0], pB[1] - rA[1], pB[2] - rA[2]};
+            cross3(lever, a[2], t);
+            for (int r = 0; r < 3; ++r) { wr[r] = -value * a[2][r]; wr[3 + r] = -value * t[r]; }
+            cross3(cB, a[2], t);
+            for (int r = 0; r < 3; ++r) { wr[6 + r] = value * a[2][r]; wr[9 + r] = value * t[r]; }
+        }
+    }
+}
+
+// Block-wide reductions of (max, max, max, sum); every thread gets the results.  The scratch is
+// double-buffered by `phase` so consecutive calls need only the one barrier inside.
+template <typename T>
+__device__ __forceinline__ void block_reduce4(T &a, T &b, T &c, T &d, T *red, int phase) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    a = warp_max(a); b = warp_max(b); c = warp_max(c); d = warp_sum(d);
+    T *r = red + phase * 4 * kWarps;
+    if (lane == 0) { r[warp] = a; r[kWarps + warp] = b; r[2 * kWarps + warp] = c; r[3 * kWarps + warp] = d; }
+    __syncthreads();
+    a = r[0]; b = r[kWarps]; c = r[2 * kWarps]; d = r[3 * kWarps];
+    for (int k = 1; k < kWarps; ++k) {
+        a = fmax(a, r[k]); b = fmax(b, r[kWarps + k]); c = fmax(c, r[2 * kWarps + k]); d += r[3 * kWarps + k];
+    }
+}
+
+// y = S x for a symmetric S in packed lower column-major storage (mp x mp).  Warp w walks the
+// columns j = w, w + 8, ...; each element S(i, j), i >= j, is read once from shared memory and
+// used twice: y_i += S_ij x_j (accumulated per lane in registers) and y_j += S_ij x_i (a warp
+// reduction per column).  The per-warp partial sums meet in `partial` ([kWarps][mp]).
+template <typename T>
+__device__ void symv_packed(const T *S, int mp, const T *x, T *y, T *partial) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    T part[kMaxChunks], xr[kMaxChunks];
+#pragma unroll
+    for (int c = 0; c < kMaxChunks; ++c) {
+        const int i = lane + 32 * c;
+        part[c] = T(0);
+        xr[c] = i < mp ? x[i] : T(0);
+    }
+    for (int j = warp; j < mp; j += kWarps) {
+        const T *col = S + col_start(j, mp) - j;   // col[i] = S(i, j) for i >= j
+        const T xj = x[j];
+        T dot = T(0);
+#pragma unroll
+        for (int c = 0; c < kMaxChunks; ++c) {
+            if (32 * c + 31 < j || 32 * c >= mp) continue;   // warp-uniform
+            const int i = lane + 32 * c;
+            if (i >= j && i < mp) {
+                const T s = col[i];
+                part[c] = fma(s, xj, part[c]);
+                if (i > j) dot = fma(s, xr[c], dot);
+            }
+        }
+        dot = warp_sum(dot);
+        if (lane == 0) y[j] = dot;
+    }
+#pragma unroll
+    for (int c = 0; c < kMaxChunks; ++c) {
+        const int i = lane + 32 * c;
+        if (i < mp) partial[warp * mp + i] = part[c];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < mp; i += kThreads) {
+        T acc = y[i];
+        for (int w = 0; w < kWarps; ++w) acc += partial[w * mp + i];
+        y[i] = acc;
+    }
+    __syncthreads();
+}
+
+// In-place blocked sweep of a symmetric positive definite matrix in packed lower storage:
+// sweeping every pivot turns A into -A^-1.  Panels of NB columns: invert the NB x NB pivot block,
+// T = A(:,K) A_KK^-1, rank-NB update A(i,j) -= T(i,:) A(j,K)^T for i, j outside K (4x4 register
+// tiles), then A(:,K) = T and A_KK = -A_KK^-1.  `P`, `Tm`, `Dm` live in the X scratch.
+template <typename T, int NB>
+__device__ void sweep_inverse(T *A, int mp, T *X) {
+    T *P = X;                    // [mp][NB] old panel
+    T *Tm = X + mp * NB;         // [mp][NB]
+    T *Dm = X + 2 * mp * NB;     // [NB][NB]
+    const int tid = threadIdx.x;
+    for (int k0 = 0; k0 < mp; k0 += NB) {
+        for (int e = tid; e < mp * NB; e += kThreads) {
+            const int i = e / NB, t = e - i * NB;
+            P[e] = A[sidx(i, k0 + t, mp)];
+        }
+        __syncthreads();
+        // -- pivot block inverse by an unblocked sweep on one warp (result negated at the end)
+        if (tid < 32) {
+            for (int e = tid; e < NB * NB; e += 32) Dm[e] = P[(k0 + e / NB) * NB + (e % NB)];
+            __syncwarp();
+            for (int p = 0; p < NB; ++p) {
+                const T d = T(1) / Dm[p * NB + p];
+                T nv[(NB * NB + 31) / 32];
+#pragma unroll
+                for (int q = 0; q < (NB * NB + 31) / 32; ++q) {
+                    const int e = tid + 32 * q;
+                    if (e < NB * NB) {
+                        const int i = e / NB, j = e % NB;
+                        const T aij = Dm[e], aip = Dm[i * NB + p], apj = Dm[p * NB + j];
+                        if (i == p && j == p) nv[q] = -d;
+                        else if (i == p) nv[q] = apj * d;
+                        else if (j == p) nv[q] = aip * d;
+                        else nv[q] = aij - aip * apj * d;
+                    }
+                }
+                __syncwarp();
+#pragma unroll
+                for (int q = 0; q < (NB * NB + 31) / 32; ++q) {
+                    const int e = tid + 32 * q;
+                    if (e < NB * NB) Dm[e] = nv[q];
+                }
+                __syncwarp();
+            }
+            for (int e = tid; e < NB * NB; e += 32) Dm[e] = -Dm[e];   // = A_KK^-1
+        }
+        __syncthreads();
+        // -- T = A(:,K) A_KK^-1 for rows outside K
+        for (int e = tid; e < mp * NB; e += kThreads) {
+            const int i = e / NB, t = e - i * NB;
+            if (i >= k0 && i < k0 + NB) continue;
+            T acc = T(0);
+#pragma unroll
+            for (int u = 0; u < NB; ++u) acc = fma(P[i * NB + u], Dm[u * NB + t], acc);
+            Tm[e] = acc;
+        }
+        __syncthreads();
+        // -- rank-NB update of the lower triangle outside K, 4x4 tiles
+        const int nt = mp / 4;
+        const int ntiles = nt * (nt + 1) / 2;
+        const int kb0 = k0 / 4, kb1 = (k0 + NB) / 4;
+        for (int tile = tid; tile < ntiles; tile += kThreads) {
+            int ti = (int)((sqrtf(8.0f * (float)tile + 1.0f) - 1.0f) * 0.5f);
+            while (ti * (ti + 1) / 2 > tile) --ti;
+            while ((ti + 1) * (ti + 2) / 2 <= tile) ++ti;
+            const int tj = tile - ti * (ti + 1) / 2;
+            if ((ti >= kb0 && ti < kb1) || (tj >= kb0 && tj < kb1)) continue;
+            T acc[4][4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+            const T *Ti = Tm + (4 * ti) * NB;
+            const T *Pj = P + (4 * tj) * NB;
+#pragma unroll 4
+            for (int u = 0; u < NB; ++u) {
+                T tv[4], pv[4];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) { tv[a] = Ti[a * NB + u]; pv[a] = Pj[a * NB + u]; }
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) acc[a][b] = fma(tv[a], pv[b], acc[a][b]);
+            }
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const int j = 4 * tj + b;
+                T *colj = A + col_start(j, mp) - j;
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    const int i = 4 * ti + a;
+                    if (i >= j) colj[i] -= acc[a][b];
+                }
+            }
+        }
+        __syncthreads();
+        // -- write back the swept panel
+        for (int e = tid; e < mp * NB; e += kThreads) {
+            const int i = e / NB, t = e - i * NB;
+            const int j = k0 + t;
+            if (i >= k0 && i < k0 + NB) {
+                if (i >= j) A[pidx(i, j, mp)] = -Dm[(i - k0) * NB + t];
+            } else {
+                A[sidx(i, j, mp)] = Tm[e];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ----------------------------------------------------------------------------- the step kernel
+template <typename T, int NB>
+__global__ void __launch_bounds__(kThreads, 1) step_kernel(const StepArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int w = a.world_order ? a.world_order[blockIdx.x] : (int)blockIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const ModelView<T> &M = a.m;
+    const int4 wa = M.world_a[w], wb = M.world_b[w];
+    const int b0 = wa.x, j0 = wa.y, c0 = wa.z, k0 = wa.w;
+    const int nb = wb.x, nj = wb.y, nc = wb.z, nbil = wb.w;
+    const Layout L = make_layout<T>(a.nb_max, a.nj_max, a.nc_max, a.mp_max, NB);
+    T *bq = (T *)(smem + L.bq), *bu = (T *)(smem + L.bu), *bR = (T *)(smem + L.bR), *bI = (T *)(smem + L.bI);
+    T *bIinv = (T *)(smem + L.bIinv), *bminv = (T *)(smem + L.bminv), *bufree = (T *)(smem + L.bufree);
+    T *jwr = (T *)(smem + L.jwr);
+    int *cid = (int *)(smem + L.cid), *cslot = (int *)(smem + L.cslot), *rbody = (int *)(smem + L.rbody);
+    T *rJ = (T *)(smem + L.rJ), *rvs = (T *)(smem + L.rvs);
+    T *vf = (T *)(smem + L.vf), *p = (T *)(smem + L.p), *x = (T *)(smem + L.x), *xn = (T *)(smem + L.xn);
+    T *y = (T *)(smem + L.y), *z = (T *)(smem + L.z), *yh = (T *)(smem + L.yh), *zh = (T *)(smem + L.zh);
+    T *bb = (T *)(smem + L.b), *mut = (T *)(smem + L.mut), *X = (T *)(smem + L.X), *A = (T *)(smem + L.A);
+    T *red = (T *)(smem + L.red);
+    int *misc = (int *)(smem + L.misc);
+    const T dt = a.dt, kbias = a.beta / a.dt;
+
+    // ---- 1. body kinematics
+    for (int i = tid; i < nb; i += kThreads) {
+        const T *gq = a.body_q + 7 * (size_t)(b0 + i);
+        const T *gu = a.body_u + 6 * (size_t)(b0 + i);
+        T q[7];
+        for (int k = 0; k < 7; ++k) q[k] = gq[k];
+        const T qn = rsq(q[3] * q[3] + q[4] * q[4] + q[5] * q[5] + q[6] * q[6]);
+        for (int k = 3; k < 7; ++k) q[k] *= qn;
+        for (int k = 0; k < 7; ++k) bq[7 * i + k] = q[k];
+        for (int k = 0; k < 6; ++k) bu[6 * i + k] = gu[k];
+        T R[9];
+        quat_rot(q + 3, R);
+        for (int k = 0; k < 9; ++k) bR[9 * i + k] = R[k];
+        const T m = M.body_mass[b0 + i];
+        T inv[3];
+        for (int k = 0; k < 3; ++k) {
+            const T Ik = M.body_inertia[3 * (size_t)(b0 + i) + k];
+            bI[3 * i + k] = Ik;
+            inv[k] = T(1) / Ik;
+        }
+        // R diag(1/I) R^T, symmetric (xx, yy, zz, xy, xz, yz)
+        T *S = bIinv + 6 * i;
+        const int rr[6] = {0, 1, 2, 0, 0, 1}, cc[6] = {0, 1, 2, 1, 2, 2};
+        for (int k = 0; k < 6; ++k) {
+            const int r = rr[k], c = cc[k];
+            S[k] = R[3 * r] * inv[0] * R[3 * c] + R[3 * r + 1] * inv[1] * R[3 * c + 1] + R[3 * r + 2] * inv[2] * R[3 * c + 2];
+        }
+        bminv[i] = T(1) / m;
+    }
+    __syncthreads();
+
+    // ---- 2. joint rows and actuation wrenches (thread per joint); 3. contacts (last warp)
+    for (int j = tid; j < nj; j += kThreads) {
+        const int4 meta = M.joint_meta[j0 + j];
+        const bool act = meta.w >= 0 && a.tau != nullptr;
+        const T val = act ? a.tau[(size_t)w * M.n_act_max + meta.w] : T(0);
+        joint_rows(meta.x, meta.y, meta.z, M.joint_frames + 14 * (size_t)(j0 + j), bq, bR, M.joint_row[j0 + j], kbias,
+                   rbody, rJ, rvs, act, val, jwr + 12 * j);
+    }
+    if (warp == kWarps - 1) {
+        int count = 0;
+        for (int cb = 0; cb < nc; cb += 32) {
+            const int c = cb + lane;
+            bool active = false;
+            T pw[3], n[3], phi = T(0), rb[3];
+            int body = 0;
+            if (c < nc && M.terrain_kind != KAMINO_TERRAIN_NONE) {
+                body = M.contact_body[c0 + c];
+                const T *cp = M.contact_point + 3 * (size_t)(c0 + c);
+                T lc[3] = {cp[0], cp[1], cp[2]}, wc[3];
+                matvec3(bR + 9 * body, lc, wc);
+                for (int k = 0; k < 3; ++k) { rb[k] = bq[7 * body + k]; pw[k] = rb[k] + wc[k]; }
+                phi = terrain(M, pw, n);
+                active = phi < a.margin;
+            }
+            const unsigned mask = __ballot_sync(0xffffffffu, active);
+            const int rank = count + __popc(mask & ((1u << lane) - 1u));
+            if (c < nc) cslot[c] = active ? rank : -1;
+            if (active) {
+                cid[rank] = c;
+                T t1[3], t2[3], lev[3], Ja[6] = {T(0), T(0), T(0), T(0), T(0), T(0)}, Jb[6], cr[3];
+                onb(n, t1, t2);
+                for (int k = 0; k < 3; ++k) lev[k] = pw[k] - rb[k];
+                const T *dirs[3] = {t1, t2, n};
+                const int row0 = nbil + 3 * rank;
+                for (int d = 0; d < 3; ++d) {
+                    cross3(lev, dirs[d], cr);
+                    for (int k = 0; k < 3; ++k) { Jb[k] = dirs[d][k]; Jb[3 + k] = cr[k]; }
+                    const T vs = d < 2 ? T(0) : (phi > T(0) ? phi / dt : kbias * phi);
+                    put_row(rbody, rJ, rvs, row0 + d, -1, body, Ja, Jb, vs);
+                }
+            }
+            count += __popc(mask);
+        }
+        if (lane == 0) misc[0] = count;
+    }
+    __syncthreads();
+    const int nact = misc[0];
+    const int m = nbil + 3 * nact;
+    const int mp = ((m + NB - 1) / NB) * NB;
+    const int nunits = nbil + nact;
+
+    // ---- 4. u_free = u + dt M^-1 h
+    for (int i = tid; i < nb; i += kThreads) {
+        T f[3] = {M.gx * (T(1) / bminv[i]), M.gy * (T(1) / bminv[i]), M.gz * (T(1) / bminv[i])};
+        T tq[3] = {T(0), T(0), T(0)};
+        for (int j = 0; j < nj; ++j) {
+            const int4 meta = M.joint_meta[j0 + j];
+            if (meta.w < 0 || a.tau == nullptr) continue;
+            const T *wr = jwr + 12 * j;
+            if (meta.y == i) for (int k = 0; k < 3; ++k) { f[k] += wr[k]; tq[k] += wr[3 + k]; }
+            if (meta.z == i) for (int k = 0; k < 3; ++k) { f[k] += wr[6 + k]; tq[k] += wr[9 + k]; }
+        }
+        // gyroscopic: -w x (I_w w), I_w w = R (I o (R^T w))
+        const T *om = bu + 6 * i + 3;
+        T wbody[3], Iw[3], Iww[3], gy[3];
+        matTvec3(bR + 9 * i, om, wbody);
+        for (int k = 0; k < 3; ++k) Iw[k] = bI[3 * i + k] * wbody[k];
+        matvec3(bR + 9 * i, Iw, Iww);
+        cross3(om, Iww, gy);
+        for (int k = 0; k < 3; ++k) tq[k] -= gy[k];
+        T dw[3];
+        symvec3(bIinv + 6 * i, tq, dw);
+        for (int k = 0; k < 3; ++k) {
+            bufree[6 * i + k] = bu[6 * i + k] + dt * bminv[i] * f[k];
+            bufree[6 * i + 3 + k] = bu[6 * i + 3 + k] + dt * dw[k];
+        }
+    }
+    __syncthreads();
+
+    // ---- 5a. per row: M^-1 J^T blocks (into X), diag(D), v_f
+    T *MJ = X;
+    for (int r = tid; r < m; r += kThreads) {
+        const int ba = rbody[2 * r], bbd = rbody[2 * r + 1];
+        const T *J = rJ + 12 * r;
+        T d = T(0), v = rvs[r];
+        for (int s = 0; s < 2; ++s) {
+            const int body = s == 0 ? ba : bbd;
+            T *o = MJ + 12 * r + 6 * s;
+            if (body < 0) { for (int k = 0; k < 6; ++k) o[k] = T(0); continue; }
+            const T *Js = J + 6 * s;
+            for (int k = 0; k < 3; ++k) o[k] = bminv[body] * Js[k];
+            symvec3(bIinv + 6 * body, Js + 3, o + 3);
+            for (int k = 0; k < 6; ++k) { d += Js[k] * o[k]; v += Js[k] * bufree[6 * body + k]; }
+        }
+        x[r] = d;      // diag(D), temporarily
+        vf[r] = v;
+    }
+    __syncthreads();
+    // ---- 5b. Jacobi scaling (tangent rows of a contact share one scale), scaled mu, scaled v_f
+    for (int r = tid; r < mp; r += kThreads) {
+        T pr = T(1);
+        if (r < m && a.precond) {
+            if (r < nbil) {
+                pr = rsq(x[r]);
+            } else {
+                const int k = (r - nbil) / 3, t = (r - nbil) % 3;
+                const int rt = nbil + 3 * k;
+                pr = t < 2 ? rsq(T(0.5) * (x[rt] + x[rt + 1])) : rsq(x[r]);
+            }
+        }
+        p[r] = pr;
+    }
+    __syncthreads();
+    for (int r = tid; r < mp; r += kThreads) {
+        vf[r] = r < m ? p[r] * vf[r] : T(0);
+        bb[r] = T(0);
+    }
+    for (int k = tid; k < nact; k += kThreads) {
+        const int rt = nbil + 3 * k;
+        mut[k] = M.world_mu[w] * p[rt + 2] / p[rt];
+    }
+    // ---- 5c. A = P D P + (eta + rho) I in packed storage (identity on the padding rows)
+    const T shift = a.eta + a.rho;
+    for (int j = warp; j < mp; j += kWarps) {
+        T *col = A + col_start(j, mp) - j;
+        const int ja = j < m ? rbody[2 * j] : -2, jb = j < m ? rbody[2 * j + 1] : -2;
+        for (int i = j + lane; i < mp; i += 32) {
+            T v;
+            if (i >= m || j >= m) {
+                v = i == j ? T(1) : T(0);
+            } else {
+                const int ia = rbody[2 * i], ib = rbody[2 * i + 1];
+                const T *Ji = rJ + 12 * i;
+                const T *Mj = MJ + 12 * j;
+                T s = T(0);
+                if (ia >= 0 && ia == ja) for (int k = 0; k < 6; ++k) s += Ji[k] * Mj[k];
+                if (ia >= 0 && ia == jb) for (int k = 0; k < 6; ++k) s += Ji[k] * Mj[6 + k];
+                if (ib == ja) for (int k = 0; k < 6; ++k) s += Ji[6 + k] * Mj[k];
+                if (ib == jb) for (int k = 0; k < 6; ++k) s += Ji[6 + k] * Mj[6 + k];
+                v = p[i] * p[j] * s + (i == j ? shift : T(0));
+            }
+            col[i] = v;
+        }
+    }
+    __syncthreads();
+
+    // ---- 6. warm start: x0 = y0 = P^-1 lambda0, z0 = v0 + Gamma(v0), v0 = D~ x0 + v~_f
+    const bool warm = a.warm_mode != KAMINO_WARM_COLD;
+    for (int r = tid; r < mp; r += kThreads) {
+        T l0 = T(0);
+        if (warm && r < m) {
+            const T *src = a.warm_mode == KAMINO_WARM_EXTERNAL ? a.warm : a.cache;
+            if (src) {
+                if (r < nbil) l0 = src[k0 + r];
+                else {
+                    const int k = (r - nbil) / 3, t = (r - nbil) % 3;
+                    l0 = src[k0 + nbil + 3 * cid[k] + t];
+                }
+            }
+        }
+        x[r] = l0 / p[r];
+    }
+    __syncthreads();
+    if (warm) {
+        symv_packed(A, mp, x, xn, X);          // xn = A x0 = D~ x0 + (eta + rho) x0
+        for (int u = tid; u < nunits; u += kThreads) {
+            if (u < nbil) {
+                const T v0 = xn[u] - shift * x[u] + vf[u];
+                z[u] = v0;
+            } else {
+                const int r0 = nbil + 3 * (u - nbil);
+                T v0[3];
+                for (int t = 0; t < 3; ++t) v0[t] = xn[r0 + t] - shift * x[r0 + t] + vf[r0 + t];
+                z[r0] = v0[0]; z[r0 + 1] = v0[1];
+                z[r0 + 2] = v0[2] + mut[u - nbil] * sqrt(v0[0] * v0[0] + v0[1] * v0[1]);
+            }
+        }
+    }
+    for (int r = tid; r < mp; r += kThreads) {
+        if (!warm || r >= m) z[r] = T(0);
+        y[r] = x[r]; yh[r] = x[r]; zh[r] = z[r];
+    }
+    __syncthreads();
+
+    // ---- 7. A <- -A^-1 (blocked sweep)
+    sweep_inverse<T, NB>(A, mp, X);
+
+    // ---- 8. Proximal-ADMM (Alg. 1)
+    const T eta = a.eta, rho = a.rho, irho = T(1) / a.rho;
+    T acc_a = T(1), c_prev = T(INFINITY);
+    T rp = T(INFINITY), rd = T(INFINITY), rc = T(INFINITY);
+    int it = 0;
+    bool converged = false;
+    for (it = 1; it <= a.iters; ++it) {
+        // s = Gamma(z^), b = v_f + s - eta x - rho y^ - z^
+        for (int u = tid; u < nunits; u += kThreads) {
+            if (u < nbil) {
+                bb[u] = vf[u] - eta * x[u] - rho * yh[u] - zh[u];
+            } else {
+                const int r0 = nbil + 3 * (u - nbil);
+                const T s = mut[u - nbil] * sqrt(zh[r0] * zh[r0] + zh[r0 + 1] * zh[r0 + 1]);
+                for (int t = 0; t < 3; ++t)
+                    bb[r0 + t] = vf[r0 + t] + (t == 2 ? s : T(0)) - eta * x[r0 + t] - rho * yh[r0 + t] - zh[r0 + t];
+            }
+        }
+        __syncthreads();
+        // x^i = -(D~ + (eta + rho) I)^-1 b = A b   (A holds -A_orig^-1)
+        symv_packed(A, mp, bb, xn, X);
+        // y^i = Pi_K(x^i - z^/rho), z^i = z^ - rho (x^i - y^i), residual terms
+        T lrp = T(0), lrd = T(0), lrc = T(0), lc = T(0);
+        T ynew[2][3], znew[2][3];   // per owned unit: a thread owns units tid and tid + kThreads
+#pragma unroll
+        for (int sl = 0; sl < 2; ++sl) {
+            const int u = tid + sl * kThreads;
+            if (u >= nunits) continue;
+            if (u < nbil) {
+                const T xv = xn[u];
+                const T yv = xv - zh[u] * irho;
+                const T zv = zh[u] - rho * (xv - yv);
+                lrp = fmax(lrp, fabs(xv - yv));
+                lrd = fmax(lrd, fabs(eta * (xv - x[u]) + rho * (yv - yh[u])));
+                lc += (zv - zh[u]) * (zv - zh[u]) * irho + rho * (yv - yh[u]) * (yv - yh[u]);
+                ynew[sl][0] = yv; znew[sl][0] = zv;
+            } else {
+                const int k = u - nbil, r0 = nbil + 3 * k;
+                const T mu = mut[k];
+                T v[3], yv[3];
+#pragma unroll
+                for (int t = 0; t < 3; ++t) v[t] = xn[r0 + t] - zh[r0 + t] * irho;
+                const T tn = sqrt(v[0] * v[0] + v[1] * v[1]);
+                if (tn <= mu * v[2]) {
+                    yv[0] = v[0]; yv[1] = v[1]; yv[2] = v[2];
+                } else if (mu * tn <= -v[2]) {
+                    yv[0] = yv[1] = yv[2] = T(0);
+                } else {
+                    const T nn = (mu * tn + v[2]) / (T(1) + mu * mu);
+                    const T sc = mu * nn / tn;
+                    yv[0] = sc * v[0]; yv[1] = sc * v[1]; yv[2] = nn;
+                }
+                T ydz = T(0);
+#pragma unroll
+                for (int t = 0; t < 3; ++t) {
+                    const T xv = xn[r0 + t];
+                    const T zv = zh[r0 + t] - rho * (xv - yv[t]);
+                    lrp = fmax(lrp, fabs(xv - yv[t]));
+                    lrd = fmax(lrd, fabs(eta * (xv - x[r0 + t]) + rho * (yv[t] - yh[r0 + t])));
+                    lc += (zv - zh[r0 + t]) * (zv - zh[r0 + t]) * irho + rho * (yv[t] - yh[r0 + t]) * (yv[t] - yh[r0 + t]);
+                    ydz += yv[t] * zv;
+                    ynew[sl][t] = yv[t]; znew[sl][t] = zv;
+                }
+                lrc = fmax(lrc, fabs(ydz));
+            }
+        }
+        block_reduce4(lrp, lrd, lrc, lc, red, it & 1);
+        rp = lrp; rd = lrd; rc = lrc;
+        // Nesterov with adaptive restart (uniform decision), then commit the iterates
+        T beta_n = T(0);
+        bool restart = false;
+        if (a.nesterov) {
+            if (lc < T(0.999) * c_prev) {
+                const T an = T(0.5) * (T(1) + sqrt(T(1) + T(4) * acc_a * acc_a));
+                beta_n = (acc_a - T(1)) / an;
+                acc_a = an;
+                c_prev = lc;
+            } else {
+                restart = true;
+                acc_a = T(1);
+                c_prev = c_prev / T(0.999);
+            }
+        }
+#pragma unroll
+        for (int sl = 0; sl < 2; ++sl) {
+            const int u = tid + sl * kThreads;
+            if (u >= nunits) continue;
+            const int r0 = u < nbil ? u : nbil + 3 * (u - nbil);
+            const int cnt = u < nbil ? 1 : 3;
+#pragma unroll
+            for (int t = 0; t < 3; ++t) {
+                if (t >= cnt) break;
+                const int r = r0 + t;
+                const T yv = ynew[sl][t], zv = znew[sl][t];
+                if (!a.nesterov) { yh[r] = yv; zh[r] = zv; }
+                else if (restart) { yh[r] = y[r]; zh[r] = z[r]; }
+                else { yh[r] = yv + beta_n * (yv - y[r]); zh[r] = zv + beta_n * (zv - z[r]); }
+                y[r] = yv; z[r] = zv; x[r] = xn[r];
+            }
+        }
+        if (rp < a.tol && rd < a.tol && rc < a.tol) { converged = true; break; }
+    }
+    if (it > a.iters) it = a.iters;
+    __syncthreads();
+
+    // ---- 9. lambda = P y; u+ = u_free + M^-1 J^T lambda; integrate; cache; report
+    for (int r = tid; r < m; r += kThreads) xn[r] = p[r] * y[r];
+    __syncthreads();
+    bool bad = false;
+    for (int i = tid; i < nb; i += kThreads) {
+        T f[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+        for (int r = 0; r < m; ++r) {
+            const T l = xn[r];
+            const T *J = rJ + 12 * r;
+            if (rbody[2 * r] == i) for (int k = 0; k < 6; ++k) f[k] += J[k] * l;
+            if (rbody[2 * r + 1] == i) for (int k = 0; k < 6; ++k) f[k] += J[6 + k] * l;
+        }
+        T up[6], dw[3];
+        symvec3(bIinv + 6 * i, f + 3, dw);
+        for (int k = 0; k < 3; ++k) {
+            up[k] = bufree[6 * i + k] + bminv[i] * f[k];
+            up[3 + k] = bufree[6 * i + 3 + k] + dw[k];
+        }
+        const T *q = bq + 7 * i;
+        T th[3] = {dt * up[3], dt * up[4], dt * up[5]};
+        const T ang = sqrt(dot3(th, th));
+        T dq[4];
+        if (ang > T(0)) {
+            const T s = sin(T(0.5) * ang) / ang;
+            dq[0] = s * th[0]; dq[1] = s * th[1]; dq[2] = s * th[2]; dq[3] = cos(T(0.5) * ang);
+        } else {
+            dq[0] = dq[1] = dq[2] = T(0); dq[3] = T(1);
+        }
+        const T qx = q[3], qy = q[4], qz = q[5], qw = q[6];
+        T qn[4] = {dq[3] * qx + dq[0] * qw + dq[1] * qz - dq[2] * qy,
+                   dq[3] * qy - dq[0] * qz + dq[1] * qw + dq[2] * qx,
+                   dq[3] * qz + dq[0] * qy - dq[1] * qx + dq[2] * qw,
+                   dq[3] * qw - dq[0] * qx - dq[1] * qy - dq[2] * qz};
+        const T nrm = rsq(qn[0] * qn[0] + qn[1] * qn[1] + qn[2] * qn[2] + qn[3] * qn[3]);
+        T *gq = a.body_q + 7 * (size_t)(b0 + i);
+        T *gu = a.body_u + 6 * (size_t)(b0 + i);
+        for (int k = 0; k < 3; ++k) gq[k] = q[k] + dt * up[k];
+        for (int k = 0; k < 4; ++k) gq[3 + k] = qn[k] * nrm;
+        for (int k = 0; k < 6; ++k) {
+            gu[k] = up[k];
+            bad |= !isfinite(up[k]);
+        }
+    }
+    // impulse cache: joint rows, then 3 per candidate (zero when inactive)
+    for (int r = tid; r < nbil; r += kThreads) a.cache[k0 + r] = xn[r];
+    for (int e = tid; e < 3 * nc; e += kThreads) {
+        const int c = e / 3, t = e % 3;
+        const int s = cslot[c];
+        a.cache[k0 + nbil + e] = s >= 0 ? xn[nbil + 3 * s + t] : T(0);
+    }
+    const int any_bad = __syncthreads_or(bad);
+    if (tid == 0) {
+        kamino_residual rep;
+        rep.iterations = it;
+        rep.status = (converged ? 0 : KAMINO_WORLD_NOT_CONVERGED) | (any_bad ? KAMINO_WORLD_NONFINITE : 0);
+        rep.num_rows = m;
+        rep.num_contacts = nact;
+        rep.r_primal = (float)rp;
+        rep.r_dual = (float)rd;
+        rep.r_compl = (float)rc;
+        rep.reserved = 0.0f;
+        a.res[w] = rep;
+    }
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t prepare_step(int nb_panel, size_t smem) {
+    cudaError_t e;
+    if (nb_panel == 16)
+        e = cudaFuncSetAttribute(step_kernel<T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    else
+        e = cudaFuncSetAttribute(step_kernel<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return e;
+}
+
+template <typename T>
+cudaError_t launch_step(const StepArgs<T> &args, int num_worlds, int nb_panel, size_t smem, cudaStream_t stream) {
+    if (num_worlds <= 0) return cudaSuccess;
+    if (nb_panel == 16)
+        step_kernel<T, 16><<<num_worlds, kThreads, smem, stream>>>(args);
+    else
+        step_kernel<T, 8><<<num_worlds, kThreads, smem, stream>>>(args);
+    return cudaGetLastError();
+}
+
+template cudaError_t prepare_step<float>(int, size_t);
+template cudaError_t prepare_step<double>(int, size_t);
+template cudaError_t launch_step<float>(const StepArgs<float> &, int, int, size_t, cudaStream_t);
+template cudaError_t launch_step<double>(const StepArgs<double> &, int, int, size_t, cudaStream_t);
+
+}  // namespace kamino

@@ -1,0 +1,248 @@
+"""Python binding of the kamino C ABI (``include/kamino.h``): argument marshalling only.
+
+Every computation of the step runs in the library's CUDA kernels.  PyTorch provides the device
+memory of the state (one ``uint8`` buffer, carved by the library) and the CUDA stream; the views
+returned here are zero-copy tensors over that buffer.  There is no CPU fallback: loading fails
+loudly when the shared library has not been built, and stepping fails when no GPU is present.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+FP32, FP64 = 0, 1
+WARM_COLD, WARM_CACHED, WARM_EXTERNAL = 0, 1, 2
+BUF_BODY_Q, BUF_BODY_U, BUF_CACHE, BUF_WARM, BUF_RESIDUAL, BUF_TAU = 0, 1, 2, 3, 4, 5
+WORLD_NOT_CONVERGED, WORLD_NONFINITE = 1, 2
+STATUS = {0: "KAMINO_OK", 1: "KAMINO_E_INVALID_ARG", 2: "KAMINO_E_TOPOLOGY", 3: "KAMINO_E_NOMEM",
+          4: "KAMINO_E_CUDA", 5: "KAMINO_E_NONFINITE", 6: "KAMINO_E_TIMEOUT", 7: "KAMINO_E_UNSUPPORTED"}
+
+
+class KaminoError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class SolverParams(C.Structure):
+    _fields_ = [("eta", C.c_double), ("rho", C.c_double), ("beta", C.c_double), ("margin", C.c_double),
+                ("nesterov", C.c_int32), ("precond", C.c_int32), ("warm_mode", C.c_int32), ("reserved", C.c_int32)]
+
+
+def make_params(eta=1e-6, rho=0.1, beta=0.2, margin=0.005, nesterov=True, precond=True, warm_mode=WARM_COLD):
+    return SolverParams(eta, rho, beta, margin, int(nesterov), int(precond), int(warm_mode), 0)
+
+
+_P = C.c_void_p
+
+
+class ModelDesc(C.Structure):
+    _fields_ = [("num_worlds", C.c_int32), ("precision", C.c_int32),
+                ("world_body_offset", _P), ("world_joint_offset", _P), ("world_contact_offset", _P),
+                ("world_num_actuators", _P), ("world_mu", _P), ("body_mass", _P), ("body_inertia", _P),
+                ("joint_type", _P), ("joint_parent", _P), ("joint_child", _P), ("joint_actuator", _P),
+                ("joint_frame_parent", _P), ("joint_frame_child", _P), ("contact_body", _P),
+                ("contact_point", _P), ("gravity", C.c_double * 3), ("terrain_kind", C.c_int32),
+                ("hf_nx", C.c_int32), ("hf_ny", C.c_int32), ("hf_origin", C.c_double * 2), ("hf_cell", C.c_double),
+                ("hf_heights", _P), ("body_q0", _P), ("body_u0", _P), ("params", SolverParams)]
+
+
+class ModelInfo(C.Structure):
+    _fields_ = [("num_worlds", C.c_int32), ("num_bodies", C.c_int32), ("max_bodies", C.c_int32),
+                ("max_rows", C.c_int32), ("n_act_max", C.c_int32), ("cache_len", C.c_int32),
+                ("precision", C.c_int32), ("threads_per_world", C.c_int32), ("smem_bytes", C.c_int64)]
+
+
+RESIDUAL_DTYPE = np.dtype([("iterations", np.int32), ("status", np.int32), ("num_rows", np.int32),
+                           ("num_contacts", np.int32), ("r_primal", np.float32), ("r_dual", np.float32),
+                           ("r_compl", np.float32), ("reserved", np.float32)])
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load_library(path: str | None = None):
+    """Load the shared library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"kamino CUDA library not built ({path} missing); run paper_2603_16536_gb300.build.build()")
+    lib = C.CDLL(path)
+    vp, i32, i64, dbl, sz = C.c_void_p, C.c_int32, C.c_int64, C.c_double, C.c_size_t
+    sig = {
+        "kamino_model_create": ([C.POINTER(ModelDesc), C.POINTER(vp)], i32),
+        "kamino_model_destroy": ([vp], i32),
+        "kamino_model_get_info": ([vp, C.POINTER(ModelInfo)], i32),
+        "kamino_model_set_params": ([vp, C.POINTER(SolverParams)], i32),
+        "kamino_state_bytes": ([vp, C.POINTER(sz)], i32),
+        "kamino_state_alloc": ([vp, vp, sz, C.POINTER(vp)], i32),
+        "kamino_state_free": ([vp], i32),
+        "kamino_state_get": ([vp, i32, C.POINTER(vp), C.POINTER(i64)], i32),
+        "kamino_state_upload": ([vp, i32, vp, i64, vp], i32),
+        "kamino_state_download": ([vp, i32, vp, i64, vp], i32),
+        "kamino_step": ([vp, dbl, i32, dbl, vp, vp], i32),
+        "kamino_residuals": ([vp, vp, vp], i32),
+        "kamino_last_error": ([], C.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def header_functions(header: str | None = None) -> list[str]:
+    """Names of the functions declared in include/kamino.h."""
+    header = header or os.path.join(_build.ROOT, "include", "kamino.h")
+    text = open(header).read()
+    return sorted(set(re.findall(r"\b(kamino_[a-z_0-9]+)\s*\(", text)))
+
+
+def _check(status):
+    if status != 0:
+        msg = load_library().kamino_last_error().decode()
+        raise KaminoError(status, msg)
+
+
+def _ptr(a):
+    return a.ctypes.data_as(C.c_void_p) if a is not None and a.size else None
+
+
+class Model:
+    """A set of worlds on the device (kamino_model_create)."""
+
+    def __init__(self, ws, precision: str = "fp32", params: SolverParams | None = None):
+        lib = load_library()
+        self.precision = FP64 if precision in ("fp64", FP64) else FP32
+        self.ws = ws
+        keep = {
+            "bo": np.ascontiguousarray(ws.world_body_offset, np.int32),
+            "jo": np.ascontiguousarray(ws.world_joint_offset, np.int32),
+            "co": np.ascontiguousarray(ws.world_contact_offset, np.int32),
+            "na": np.ascontiguousarray(ws.world_num_actuators, np.int32),
+            "mu": np.ascontiguousarray(ws.world_mu, np.float64),
+            "mass": np.ascontiguousarray(ws.body_mass, np.float64),
+            "inert": np.ascontiguousarray(ws.body_inertia, np.float64).reshape(-1),
+            "jt": np.ascontiguousarray(ws.joint_type, np.int32),
+            "jp": np.ascontiguousarray(ws.joint_parent, np.int32),
+            "jc": np.ascontiguousarray(ws.joint_child, np.int32),
+            "ja": np.ascontiguousarray(ws.joint_actuator, np.int32),
+            "fp": np.ascontiguousarray(ws.joint_frame_parent, np.float64).reshape(-1),
+            "fc": np.ascontiguousarray(ws.joint_frame_child, np.float64).reshape(-1),
+            "cb": np.ascontiguousarray(ws.contact_body, np.int32),
+            "cp": np.ascontiguousarray(ws.contact_point, np.float64).reshape(-1),
+            "hh": np.ascontiguousarray(ws.hf_heights, np.float64).reshape(-1),
+            "q0": np.ascontiguousarray(ws.body_q0, np.float64).reshape(-1),
+            "u0": np.ascontiguousarray(ws.body_u0, np.float64).reshape(-1),
+        }
+        d = ModelDesc()
+        d.num_worlds = ws.num_worlds
+        d.precision = self.precision
+        d.world_body_offset, d.world_joint_offset = _ptr(keep["bo"]), _ptr(keep["jo"])
+        d.world_contact_offset, d.world_num_actuators = _ptr(keep["co"]), _ptr(keep["na"])
+        d.world_mu, d.body_mass, d.body_inertia = _ptr(keep["mu"]), _ptr(keep["mass"]), _ptr(keep["inert"])
+        d.joint_type, d.joint_parent, d.joint_child = _ptr(keep["jt"]), _ptr(keep["jp"]), _ptr(keep["jc"])
+        d.joint_actuator, d.joint_frame_parent, d.joint_frame_child = _ptr(keep["ja"]), _ptr(keep["fp"]), _ptr(keep["fc"])
+        d.contact_body, d.contact_point = _ptr(keep["cb"]), _ptr(keep["cp"])
+        d.gravity = (C.c_double * 3)(*[float(g) for g in ws.gravity])
+        d.terrain_kind = int(ws.terrain_kind)
+        d.hf_nx, d.hf_ny = int(ws.hf_nx), int(ws.hf_ny)
+        d.hf_origin = (C.c_double * 2)(*[float(v) for v in ws.hf_origin])
+        d.hf_cell = float(ws.hf_cell)
+        d.hf_heights = _ptr(keep["hh"])
+        d.body_q0, d.body_u0 = _ptr(keep["q0"]), _ptr(keep["u0"])
+        d.params = params if params is not None else make_params()
+        self.handle = C.c_void_p()
+        _check(lib.kamino_model_create(C.byref(d), C.byref(self.handle)))
+        info = ModelInfo()
+        _check(lib.kamino_model_get_info(self.handle, C.byref(info)))
+        self.info = info
+        self.params = d.params
+
+    def set_params(self, params: SolverParams):
+        _check(load_library().kamino_model_set_params(self.handle, C.byref(params)))
+        self.params = params
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.kamino_model_destroy(self.handle)
+            self.handle = None
+
+
+class State:
+    """Device state of a model over one PyTorch-allocated buffer (kamino_state_alloc)."""
+
+    def __init__(self, model: Model, device="cuda"):
+        import torch
+        lib = load_library()
+        self.model = model
+        nbytes = C.c_size_t()
+        _check(lib.kamino_state_bytes(model.handle, C.byref(nbytes)))
+        self._raw = torch.empty(nbytes.value + 256, dtype=torch.uint8, device=device)
+        base = self._raw.data_ptr()
+        self._off = (-base) % 256
+        self.handle = C.c_void_p()
+        _check(lib.kamino_state_alloc(model.handle, C.c_void_p(base + self._off), nbytes.value, C.byref(self.handle)))
+        self.dtype = torch.float64 if model.precision == FP64 else torch.float32
+        self.body_q = self._view(BUF_BODY_Q, self.dtype).view(-1, 7)
+        self.body_u = self._view(BUF_BODY_U, self.dtype).view(-1, 6)
+        self.cache = self._view(BUF_CACHE, self.dtype)
+        self.warm = self._view(BUF_WARM, self.dtype)
+        self.residual_raw = self._view(BUF_RESIDUAL, torch.int32).view(-1, 8)
+        self.tau = self._view(BUF_TAU, self.dtype)
+
+    def _view(self, which, dtype):
+        import torch
+        ptr, count = C.c_void_p(), C.c_int64()
+        _check(load_library().kamino_state_get(self.handle, which, C.byref(ptr), C.byref(count)))
+        esz = torch.empty(0, dtype=dtype).element_size() if which != BUF_RESIDUAL else 4
+        n = count.value * (8 if which == BUF_RESIDUAL else 1)
+        start = (ptr.value or 0) - self._raw.data_ptr()
+        return self._raw[start:start + n * esz].view(dtype)
+
+    def step(self, dt: float, iters: int, tol: float, tau=None, stream=None):
+        """One step of every world (kamino_step).  ``tau``: device tensor [W, n_act_max] or None."""
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        tptr = None
+        if tau is not None:
+            assert tau.is_cuda and tau.dtype == self.dtype and tau.is_contiguous()
+            assert tau.numel() >= self.model.ws.num_worlds * max(self.model.info.n_act_max, 0)
+            tptr = C.c_void_p(tau.data_ptr())
+        _check(load_library().kamino_step(self.handle, float(dt), int(iters), float(tol), tptr,
+                                          C.c_void_p(stream.cuda_stream)))
+
+    def upload(self, which, host: np.ndarray, stream=None):
+        import torch
+        s = (stream or torch.cuda.current_stream()).cuda_stream
+        _check(load_library().kamino_state_upload(self.handle, which, host.ctypes.data_as(C.c_void_p), host.size,
+                                                  C.c_void_p(s)))
+
+    def download(self, which, host: np.ndarray, stream=None):
+        import torch
+        s = (stream or torch.cuda.current_stream()).cuda_stream
+        _check(load_library().kamino_state_download(self.handle, which, host.ctypes.data_as(C.c_void_p), host.size,
+                                                    C.c_void_p(s)))
+
+    def residuals(self) -> np.ndarray:
+        """Per-world reports as a numpy structured array (synchronises the current stream)."""
+        raw = self.residual_raw.cpu().numpy()
+        return raw.view(RESIDUAL_DTYPE).reshape(-1)
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.kamino_state_free(self.handle)
+            self.handle = None

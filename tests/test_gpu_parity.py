@@ -1,0 +1,217 @@
+"""GPU parity: the CUDA step (through the C ABI) against the FP64 CPU oracle, one step at a time
+from identical states.  Compared on generalised velocities and pose increments (impulses are not
+unique on over-constrained loops), with the per-world reports checked against the oracle's
+active-set sizes.
+
+Metric (per set of worlds): err_u = max|u_gpu - u_oracle| / max(max|u_oracle|, g dt),
+err_q = max|(q+_gpu - q-) - (q+_oracle - q-)| / max(max|q+_oracle - q-|, g dt^2).
+Bars: FP64 <= 1e-9, FP32 <= 1e-4."""
+import math
+
+import numpy as np
+import pytest
+
+import worldgen as wg
+from oracle import timestep as T
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+G = 9.81
+
+
+@pytest.fixture(scope="module")
+def K():
+    import __graft_entry__ as ge
+    from paper_2603_16536_gb300 import kamino
+    import os
+    from paper_2603_16536_gb300 import build as B
+    if not os.path.exists(B.LIB):
+        ge.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return kamino
+
+
+def gpu_step(K, ws, q, u, tau, dt, iters, tol, precision="fp32", rho=0.1, warm=0, cache=None, model=None):
+    """One GPU step from host state (q, u); returns (q+, u+, residual report, cache)."""
+    if model is None:
+        model = K.Model(ws, precision, K.make_params(rho=rho, warm_mode=warm))
+    st = K.State(model)
+    dtype = st.dtype
+    st.body_q.copy_(torch.tensor(q.reshape(-1, 7), dtype=dtype))
+    st.body_u.copy_(torch.tensor(u.reshape(-1, 6), dtype=dtype))
+    if cache is not None:
+        st.cache.copy_(torch.tensor(cache, dtype=dtype))
+    tau_d = None if tau is None else torch.tensor(tau, dtype=dtype, device="cuda").contiguous()
+    st.step(dt, iters, tol, tau_d)
+    torch.cuda.synchronize()
+    return (st.body_q.double().cpu().numpy(), st.body_u.double().cpu().numpy(), st.residuals(),
+            st.cache.double().cpu().numpy())
+
+
+def errors(q0, q_gpu, u_gpu, q_ref, u_ref, dt):
+    eu = np.abs(u_gpu - u_ref).max() / max(np.abs(u_ref).max(), G * dt)
+    dq_ref = q_ref - q0
+    eq = np.abs((q_gpu - q0) - dq_ref).max() / max(np.abs(dq_ref).max(), G * dt * dt)
+    return eu, eq
+
+
+def oracle_step(ws, q, u, tau, dt, rho=0.1, eps=1e-11, n_max=50000, warm="cold", cache=None):
+    st = T.WorldState(q=q.copy(), u=u.copy(), cache=cache or [None] * ws.num_worlds)
+    params = T.SolverParams(rho=rho, eps=eps, n_max=n_max, warm=warm)
+    return T.step(ws, st, tau, dt, params)
+
+
+def check_report(rep, infos):
+    assert np.all(rep["num_rows"] == np.array([i.m for i in infos]))
+    assert np.all(rep["num_contacts"] == np.array([len(i.contact_ids) for i in infos]))
+
+
+# ----------------------------------------------------------------------------- four-bar, FP64 and FP32
+@pytest.mark.parametrize("precision,bar,tol", [("fp64", 1e-9, 1e-12), ("fp32", 1e-4, 1e-6)])
+def test_fourbar_parity_over_steps(K, precision, bar, tol):
+    """64 four-bars (1 ms): every step of a 20-step run starts the oracle from the GPU state."""
+    ws = wg.make_fourbar(num_worlds=64, seed=0)
+    dt = 1e-3
+    q, u = ws.body_q0.copy(), ws.body_u0.copy()
+    model = K.Model(ws, precision, K.make_params(rho=0.1))
+    worst = (0.0, 0.0)
+    for k in range(20):
+        qg, ug, rep, _ = gpu_step(K, ws, q, u, None, dt, 20000, tol, precision, model=model)
+        ref, infos = oracle_step(ws, q, u, None, dt, eps=1e-12)
+        eu, eq = errors(q, qg, ug, ref.q, ref.u, dt)
+        worst = (max(worst[0], eu), max(worst[1], eq))
+        check_report(rep, infos)
+        assert np.all(rep["status"] & 2 == 0)
+        q, u = qg, ug
+    assert worst[0] <= bar and worst[1] <= bar, worst
+
+
+# ----------------------------------------------------------------------------- biped with contacts
+def _biped_case(n, seed, steps_before=0, z_lift=0.0):
+    ws = wg.make_biped(num_worlds=n, seed=seed, z_lift=z_lift)
+    st = T.initial_state(ws)
+    params = T.SolverParams(rho=0.1, eps=1e-9, n_max=20000)
+    for k in range(steps_before):
+        st, _ = T.step(ws, st, wg.actuation(ws, seed, k), 2e-3, params)
+    return ws, st.q, st.u
+
+
+def _margin_clear(infos_ws, ws, q, margin=0.005, gap=1e-5):
+    """True when no contact candidate is within `gap` of the activation threshold (the active set is
+    then decided identically in FP32 and FP64)."""
+    from oracle import constraints as Cn, rigid
+    for w in range(ws.num_worlds):
+        bs = ws.bodies(w)
+        r = q[bs, :3]
+        R = np.array([rigid.quat_to_rot(qq) for qq in q[bs, 3:]])
+        for _, _, _, _, phi in Cn.contacts(ws, w, r, R):
+            if abs(phi - margin) < gap:
+                return False
+    return True
+
+
+@pytest.mark.parametrize("steps_before", [0, 3])
+def test_biped_parity_fp32(K, steps_before):
+    """8 closed-loop bipeds standing on the plane (8 active contacts each), one FP32 step."""
+    ws, q, u = _biped_case(8, seed=2, steps_before=steps_before)
+    assert _margin_clear(None, ws, q)
+    tau = wg.actuation(ws, 2, steps_before)
+    dt = 2e-3
+    qg, ug, rep, _ = gpu_step(K, ws, q, u, tau, dt, 5000, 1e-6)
+    ref, infos = oracle_step(ws, q, u, tau, dt, eps=1e-10)
+    check_report(rep, infos)
+    eu, eq = errors(q, qg, ug, ref.q, ref.u, dt)
+    assert eu <= 1e-4 and eq <= 1e-4, (eu, eq, rep["iterations"], rep["status"])
+
+
+def test_biped_in_the_air_has_no_contacts(K):
+    """Edge case: every candidate above the margin -> m = bilateral rows only."""
+    ws, q, u = _biped_case(4, seed=3, z_lift=0.2)
+    tau = wg.actuation(ws, 3, 0)
+    qg, ug, rep, _ = gpu_step(K, ws, q, u, tau, 2e-3, 5000, 1e-6)
+    ref, infos = oracle_step(ws, q, u, tau, 2e-3)
+    check_report(rep, infos)
+    assert np.all(rep["num_contacts"] == 0)
+    eu, eq = errors(q, qg, ug, ref.q, ref.u, 2e-3)
+    assert eu <= 1e-4 and eq <= 1e-4
+
+
+def test_heterogeneous_worlds_one_launch(K):
+    """Four world types with 20 to 228 rows, ragged sizes, one launch."""
+    sets = [wg.make_fourbar(3, seed=4), wg.make_stewart(3, seed=4), wg.make_excavator(3, seed=4),
+            wg.make_biped(3, seed=4)]
+    ws = wg.concat(sets)
+    q, u = ws.body_q0.copy(), ws.body_u0.copy()
+    tau = wg.actuation(ws, 4, 0)
+    dt = 2e-3
+    qg, ug, rep, _ = gpu_step(K, ws, q, u, tau, dt, 20000, 1e-6)
+    ref, infos = oracle_step(ws, q, u, tau, dt, eps=1e-10)
+    check_report(rep, infos)
+    for w0 in range(0, 12, 3):
+        bs = slice(int(ws.world_body_offset[w0]), int(ws.world_body_offset[w0 + 3]))
+        eu, eq = errors(q[bs], qg[bs], ug[bs], ref.q[bs], ref.u[bs], dt)
+        assert eu <= 1e-4 and eq <= 1e-4, (w0, eu, eq)
+
+
+def test_box_at_rest_carries_its_weight_on_gpu(K):
+    """Closed form on the GPU path: the cached normal impulses of a resting box sum to m g dt."""
+    m, dt = 1.3, 2e-3
+    ws = wg.make_box(mass=m, mu=0.6, num_worlds=5)
+    qg, ug, rep, cache = gpu_step(K, ws, ws.body_q0, ws.body_u0, None, dt, 5000, 1e-7)
+    lam = cache.reshape(5, 8, 3)
+    np.testing.assert_allclose(lam[:, :, 2].sum(axis=1), m * 9.81 * dt, rtol=1e-4)
+    assert np.abs(ug).max() < 1e-5
+    assert np.all(rep["num_contacts"] == 4)
+
+
+def test_cached_warm_start_matches_oracle(K):
+    """Two steps with the cached warm start: the second step starts Alg. 1 from the first step's
+    impulses on both sides."""
+    ws, q, u = _biped_case(4, seed=5)
+    dt = 2e-3
+    model = K.Model(ws, "fp32", K.make_params(rho=0.1, warm_mode=K.WARM_CACHED))
+    qg1, ug1, _, cache1 = gpu_step(K, ws, q, u, wg.actuation(ws, 5, 0), dt, 5000, 1e-7, model=model)
+    ref1, _ = oracle_step(ws, q, u, wg.actuation(ws, 5, 0), dt, warm="cached")
+    # second step from the GPU state, both warm-started from their own first-step caches
+    qg2, ug2, rep2, _ = gpu_step(K, ws, qg1, ug1, wg.actuation(ws, 5, 1), dt, 5000, 1e-7, model=model,
+                                 cache=cache1)
+    ref2, infos2 = oracle_step(ws, qg1, ug1, wg.actuation(ws, 5, 1), dt, warm="cached", cache=ref1.cache)
+    check_report(rep2, infos2)
+    eu, eq = errors(qg1, qg2, ug2, ref2.q, ref2.u, dt)
+    assert eu <= 1e-4 and eq <= 1e-4
+
+
+def test_iteration_cap_and_report(K):
+    """tol = 0 runs exactly N_max iterations and reports 'not converged'; results stay finite."""
+    ws = wg.make_fourbar(num_worlds=8, seed=6)
+    _, ug, rep, _ = gpu_step(K, ws, ws.body_q0, ws.body_u0, None, 1e-3, 7, 0.0)
+    assert np.all(rep["iterations"] == 7)
+    assert np.all(rep["status"] == 1)
+    assert np.isfinite(ug).all()
+
+
+def test_full_size_bipeds_sampled_parity(K):
+    """4096 bipeds, the benchmark's launch (FP32, tol 1e-5): sampled worlds against the oracle run
+    to the same tolerance, plus whole-batch properties (finite, reports consistent)."""
+    ws = wg.make_biped(num_worlds=4096, seed=0)
+    dt = 2e-3
+    tau = wg.actuation(ws, 0, 0)
+    qg, ug, rep, _ = gpu_step(K, ws, ws.body_q0, ws.body_u0, tau, dt, 200, 1e-5)
+    assert np.isfinite(qg).all() and np.isfinite(ug).all()
+    assert np.all(rep["status"] & 2 == 0)
+    assert np.all(rep["iterations"] >= 1) and np.all(rep["iterations"] <= 200)
+    conv = rep["status"] == 0
+    assert np.all(rep["iterations"][~conv] == 200)
+    sample = [0, 1, 777, 2048, 4095]
+    sub = wg.make_biped(num_worlds=4096, seed=0)
+    for w in sample:
+        bs = ws.bodies(w)
+        ref_st, infos = T.step(ws, T.initial_state(ws), tau, dt, T.SolverParams(rho=0.1, eps=1e-10, n_max=20000),
+                               worlds=[w])
+        assert rep["num_rows"][w] == infos[0].m
+        if rep["status"][w] == 0:
+            eu, eq = errors(ws.body_q0[bs], qg[bs], ug[bs], ref_st.q[bs], ref_st.u[bs], dt)
+            # tol 1e-5 on the GPU side bounds the velocity error at a few 1e-4 of the step scale
+            assert eu <= 1e-2 and eq <= 1e-2, (w, eu, eq)
