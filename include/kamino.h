@@ -195,6 +195,48 @@ kamino_status kamino_step(kamino_state_t state, double dt, int32_t iters, double
 /* Copy the per-world reports into `out_dev` (device memory, [W] kamino_residual) on `stream`. */
 kamino_status kamino_residuals(kamino_state_t state, kamino_residual *out_dev, void *stream);
 
+/* ---- Heterogeneous worlds (Sec. 5.2: worlds with different body and constraint counts in one
+ * batch).  The model groups its worlds into size buckets by padded row count.  Two launch plans:
+ *   KAMINO_LAUNCH_SINGLE      one CTA of 256 threads per world, shared memory sized for the
+ *                             largest world (default; best for homogeneous batches)
+ *   KAMINO_LAUNCH_PERSISTENT  one persistent launch per bucket (grid = SMs x resident CTAs); each
+ *                             CTA is split into groups of 32/64/128/256 threads, one world per
+ *                             group, each group pulling worlds from an atomic counter; buckets run
+ *                             concurrently on forked streams.  Group size and panel width per
+ *                             bucket come from kamino_autotune or from a size heuristic. */
+enum { KAMINO_LAUNCH_SINGLE = 0, KAMINO_LAUNCH_PERSISTENT = 1 };
+
+typedef struct {
+    int32_t rows_pad;          /* padded row bound of the bucket (multiple of 32)             */
+    int32_t num_worlds;        /* worlds in the bucket                                         */
+    int32_t group_threads;     /* threads per world (32, 64, 128, 256)                         */
+    int32_t panel;             /* sweep panel width (8 or 16)                                  */
+    int32_t grid;              /* persistent CTAs launched for the bucket                      */
+    int32_t worlds_per_cta;    /* concurrent worlds per CTA (= 256 / group_threads)           */
+    float tuned_ms;            /* autotuner time of the chosen configuration (0 = heuristic)  */
+    float reserved;
+} kamino_bucket_info;
+
+/* Current plan: up to `capacity` bucket records, their count and the launch mode. */
+kamino_status kamino_plan_get(kamino_model_t model, kamino_bucket_info *out, int32_t capacity,
+                              int32_t *count, int32_t *mode);
+/* Select KAMINO_LAUNCH_SINGLE or KAMINO_LAUNCH_PERSISTENT for subsequent steps and graphs. */
+kamino_status kamino_plan_set_mode(kamino_model_t model, int32_t mode);
+/* Autotuner: for every bucket, time each feasible (group size, panel width) on the state's own
+ * worlds (the state is snapshotted and restored around every trial, so it is left unchanged),
+ * keep the fastest, and switch the model to KAMINO_LAUNCH_PERSISTENT.  Synchronous. */
+kamino_status kamino_autotune(kamino_state_t state, double dt, int32_t iters, double tol,
+                              const void *tau_dev, void *stream);
+
+/* ---- CUDA graph of one step (Sec. 5.2: the solver loop captured and replayed each step).  The
+ * graph bakes in dt, iters, tol, the actuation pointer and the current plan; refill the actuation
+ * buffer between launches.  Launch it on any stream; destroy before the state. */
+typedef struct kamino_graph_s *kamino_graph_t;
+kamino_status kamino_graph_create(kamino_state_t state, double dt, int32_t iters, double tol,
+                                  const void *tau_dev, void *stream, kamino_graph_t *out);
+kamino_status kamino_graph_launch(kamino_graph_t graph, void *stream);
+kamino_status kamino_graph_destroy(kamino_graph_t graph);
+
 /* Message of the calling thread's last failed call ("" if none). */
 const char *kamino_last_error(void);
 

@@ -60,6 +60,17 @@ kamino_status check_params(const kamino_solver_params &p) {
 
 }  // namespace
 
+struct Bucket {
+    int rows_pad = 0, count = 0;           // padded row bound, worlds
+    int nb = 0, nj = 0, nc = 0, rows = 0;  // layout maxima over the bucket
+    int units = 0;                         // max PADMM units (joint rows + contacts)
+    int group = 256, panel = 16, grid = 0, per_cta = 1;
+    size_t slice = 0, smem = 0;
+    float tuned_ms = 0.0f;
+    int *d_worlds = nullptr;
+    std::vector<int> worlds;
+};
+
 struct kamino_model_s {
     int precision = KAMINO_FP32;
     int W = 0, B = 0, J = 0, C = 0;
@@ -76,17 +87,33 @@ struct kamino_model_s {
     void *contact_point = nullptr, *hf_heights = nullptr, *q0 = nullptr, *u0 = nullptr;
     int terrain_kind = 0, hf_nx = 0, hf_ny = 0;
     double hf_x0 = 0, hf_y0 = 0, hf_cell = 0, g[3] = {0, 0, 0};
+    // heterogeneous plan
+    std::vector<Bucket> buckets;
+    int launch_mode = KAMINO_LAUNCH_SINGLE;
+    bool plan_ready = false;
+    int sm_count = 0;
+    std::vector<cudaStream_t> side;
+    std::vector<cudaEvent_t> join;
+    cudaEvent_t fork = nullptr;
 
     ~kamino_model_s() {
         for (void *p : allocs) cudaFree(p);
+        for (cudaStream_t st : side) cudaStreamDestroy(st);
+        for (cudaEvent_t e : join) cudaEventDestroy(e);
+        if (fork) cudaEventDestroy(fork);
     }
+};
+
+struct kamino_graph_s {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
 };
 
 struct kamino_state_s {
     kamino_model_t model = nullptr;
     char *base = nullptr;
     bool owned = false;
-    size_t off_q = 0, off_u = 0, off_cache = 0, off_warm = 0, off_res = 0, off_tau = 0, bytes = 0;
+    size_t off_q = 0, off_u = 0, off_cache = 0, off_warm = 0, off_res = 0, off_tau = 0, off_cnt = 0, bytes = 0;
     void *ptr(size_t off) const { return base + off; }
 };
 
@@ -176,14 +203,82 @@ ModelView<T> view(const kamino_model_s *m) {
     return v;
 }
 
+size_t esize(const kamino_model_s *m) { return m->precision == KAMINO_FP64 ? sizeof(double) : sizeof(float); }
+
+// Shared memory of a persistent CTA for bucket b with `group` threads per world and panel `nbp`;
+// 0 when the configuration does not fit.
+size_t persistent_smem(const kamino_model_s *m, const Bucket &b, int group, int nbp, size_t *slice) {
+    if (b.units > kSlots * group) return 0;
+    const int mp = std::max(((b.rows + nbp - 1) / nbp) * nbp, nbp);
+    if (mp > kMaxRowsPad) return 0;
+    const Layout L = esize(m) == sizeof(double) ? make_layout<double>(b.nb, b.nj, b.nc, mp, nbp)
+                                                : make_layout<float>(b.nb, b.nj, b.nc, mp, nbp);
+    const size_t sl = align_up(L.total, 16);
+    const int per = kThreads / group;
+    const size_t total = per * sl + align_up(per * sizeof(int), 16);
+    if (total > kMaxSmem) return 0;
+    if (slice) *slice = sl;
+    return total;
+}
+
+bool set_config(const kamino_model_s *m, Bucket &b, int group, int nbp) {
+    size_t slice = 0;
+    const size_t smem = persistent_smem(m, b, group, nbp, &slice);
+    if (!smem) return false;
+    b.group = group;
+    b.panel = nbp;
+    b.slice = slice;
+    b.smem = smem;
+    b.per_cta = kThreads / group;
+    return true;
+}
+
+// Size heuristic: one warp per world up to 32 rows, two warps up to 96, four up to 160, else the
+// whole CTA; larger groups when the PADMM units or the shared memory demand it.
+bool choose_default(const kamino_model_s *m, Bucket &b) {
+    const int pref = b.rows_pad <= 32 ? 32 : b.rows_pad <= 96 ? 64 : b.rows_pad <= 160 ? 128 : 256;
+    for (int g = pref; g <= kThreads; g *= 2)
+        for (int nbp : {16, 8})
+            if (set_config(m, b, g, nbp)) return true;
+    return false;
+}
+
 template <typename T>
-kamino_status do_step(kamino_state_s *st, double dt, int iters, double tol, const void *tau, cudaStream_t stream) {
-    kamino_model_s *m = st->model;
-    if (!m->prepared) {
-        cudaError_t e = prepare_step<T>(m->nb_panel, m->smem);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute (step kernel shared memory)");
-        m->prepared = true;
+kamino_status ensure_plan_ready(kamino_model_s *m) {
+    if (m->plan_ready) return KAMINO_OK;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&m->sm_count, cudaDevAttrMultiProcessorCount, dev);
+    for (int nbp : {16, 8})
+        if (e == cudaSuccess) e = prepare_persistent<T>(nbp, kMaxSmem);
+    if (e != cudaSuccess) return cuda_fail(e, "persistent launch set-up");
+    while (m->side.size() < m->buckets.size()) {
+        cudaStream_t st;
+        cudaEvent_t ev;
+        if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess) return cuda_fail(e, "stream");
+        if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return cuda_fail(e, "event");
+        m->side.push_back(st);
+        m->join.push_back(ev);
     }
+    if (!m->fork && (e = cudaEventCreateWithFlags(&m->fork, cudaEventDisableTiming)) != cudaSuccess)
+        return cuda_fail(e, "event");
+    m->plan_ready = true;
+    return KAMINO_OK;
+}
+
+template <typename T>
+kamino_status grid_of(kamino_model_s *m, Bucket &b) {
+    int per_sm = 0;
+    cudaError_t e = occupancy_persistent<T>(b.panel, b.smem, &per_sm);
+    if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
+    const int need = (b.count + b.per_cta - 1) / b.per_cta;
+    b.grid = std::max(1, std::min(need, std::max(per_sm, 1) * m->sm_count));
+    return KAMINO_OK;
+}
+
+template <typename T>
+StepArgs<T> make_args(kamino_state_s *st, double dt, int iters, double tol, const void *tau) {
+    kamino_model_s *m = st->model;
     StepArgs<T> a{};
     a.m = view<T>(m);
     a.body_q = (T *)st->ptr(st->off_q);
@@ -207,8 +302,122 @@ kamino_status do_step(kamino_state_s *st, double dt, int iters, double tol, cons
     a.nj_max = m->nj_max;
     a.nc_max = m->nc_max;
     a.mp_max = m->mp_max;
-    cudaError_t e = launch_step<T>(a, m->W, m->nb_panel, m->smem, stream);
-    if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
+    return a;
+}
+
+// Persistent launch of one bucket on `stream` (its counter must be zero).
+template <typename T>
+kamino_status launch_bucket(kamino_state_s *st, const StepArgs<T> &base, int bi, cudaStream_t stream) {
+    kamino_model_s *m = st->model;
+    Bucket &b = m->buckets[bi];
+    if (b.grid == 0) {
+        kamino_status s = grid_of<T>(m, b);
+        if (s) return s;
+    }
+    StepArgs<T> a = base;
+    a.nb_max = b.nb;
+    a.nj_max = b.nj;
+    a.nc_max = b.nc;
+    a.mp_max = std::max(((b.rows + b.panel - 1) / b.panel) * b.panel, b.panel);
+    PersistentArgs p{};
+    p.worlds = b.d_worlds;
+    p.count = b.count;
+    p.counter = (int *)st->ptr(st->off_cnt) + bi;
+    p.group = b.group;
+    p.slice_bytes = b.slice;
+    cudaError_t e = launch_persistent<T>(a, p, b.panel, b.grid, b.smem, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "persistent step launch");
+    return KAMINO_OK;
+}
+
+template <typename T>
+kamino_status do_step(kamino_state_s *st, double dt, int iters, double tol, const void *tau, cudaStream_t stream) {
+    kamino_model_s *m = st->model;
+    const StepArgs<T> a = make_args<T>(st, dt, iters, tol, tau);
+    if (m->launch_mode == KAMINO_LAUNCH_SINGLE) {
+        if (!m->prepared) {
+            cudaError_t e = prepare_step<T>(m->nb_panel, kMaxSmem);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute (step kernel shared memory)");
+            m->prepared = true;
+        }
+        cudaError_t e = launch_step<T>(a, m->W, m->nb_panel, m->smem, stream);
+        if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
+        return KAMINO_OK;
+    }
+    kamino_status s = ensure_plan_ready<T>(m);
+    if (s) return s;
+    const int nbk = (int)m->buckets.size();
+    cudaError_t e = cudaMemsetAsync(st->ptr(st->off_cnt), 0, nbk * sizeof(int), stream);
+    if (e != cudaSuccess) return cuda_fail(e, "counter reset");
+    if (nbk > 1) {
+        if ((e = cudaEventRecord(m->fork, stream)) != cudaSuccess) return cuda_fail(e, "fork");
+        for (int b = 1; b < nbk; ++b)
+            if ((e = cudaStreamWaitEvent(m->side[b], m->fork, 0)) != cudaSuccess) return cuda_fail(e, "fork wait");
+    }
+    for (int b = 0; b < nbk; ++b) {
+        s = launch_bucket<T>(st, a, b, b == 0 ? stream : m->side[b]);
+        if (s) return s;
+    }
+    for (int b = 1; b < nbk; ++b) {
+        if ((e = cudaEventRecord(m->join[b], m->side[b])) != cudaSuccess) return cuda_fail(e, "join");
+        if ((e = cudaStreamWaitEvent(stream, m->join[b], 0)) != cudaSuccess) return cuda_fail(e, "join wait");
+    }
+    return KAMINO_OK;
+}
+
+// Autotuner: time every feasible configuration of every bucket on the state's worlds.
+template <typename T>
+kamino_status autotune(kamino_state_s *st, double dt, int iters, double tol, const void *tau, cudaStream_t stream) {
+    kamino_model_s *m = st->model;
+    kamino_status s = ensure_plan_ready<T>(m);
+    if (s) return s;
+    const StepArgs<T> a = make_args<T>(st, dt, iters, tol, tau);
+    char *snap = nullptr;
+    cudaError_t e = cudaMalloc(&snap, st->bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "autotune snapshot");
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    e = cudaMemcpyAsync(snap, st->base, st->bytes, cudaMemcpyDeviceToDevice, stream);
+    for (size_t bi = 0; bi < m->buckets.size() && e == cudaSuccess && !s; ++bi) {
+        Bucket &b = m->buckets[bi];
+        const Bucket keep = b;
+        float best = 1e30f;
+        int best_g = b.group, best_nb = b.panel;
+        for (int g : {32, 64, 128, 256}) {
+            for (int nbp : {16, 8}) {
+                if (!set_config(m, b, g, nbp)) continue;
+                b.grid = 0;
+                float t = 1e30f;
+                for (int rep = 0; rep < 3 && !s; ++rep) {
+                    cudaMemcpyAsync(st->base, snap, st->bytes, cudaMemcpyDeviceToDevice, stream);
+                    cudaMemsetAsync(st->ptr(st->off_cnt), 0, m->buckets.size() * sizeof(int), stream);
+                    cudaEventRecord(e0, stream);
+                    s = launch_bucket<T>(st, a, (int)bi, stream);
+                    cudaEventRecord(e1, stream);
+                    if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+                    float ms = 0.0f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    t = std::min(t, ms);
+                }
+                if (s || e != cudaSuccess) break;
+                if (t < best) { best = t; best_g = g; best_nb = nbp; }
+            }
+            if (s || e != cudaSuccess) break;
+        }
+        if (s || e != cudaSuccess) { b = keep; break; }
+        set_config(m, b, best_g, best_nb);
+        b.grid = 0;
+        b.tuned_ms = best;
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(st->base, snap, st->bytes, cudaMemcpyDeviceToDevice, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(snap);
+    if (s) return s;
+    if (e != cudaSuccess) return cuda_fail(e, "autotune");
+    m->launch_mode = KAMINO_LAUNCH_PERSISTENT;
     return KAMINO_OK;
 }
 
@@ -327,6 +536,21 @@ kamino_status kamino_model_create(const kamino_model_desc *d, kamino_model_t *ou
         }
         wa[w] = make_int4(b0, j0, c0, cache);
         wb[w] = make_int4(nb, nj, nc, row);
+        {
+            const int rows = row + 3 * nc;
+            const int rp = std::max(32, ((rows + 31) / 32) * 32);
+            Bucket *bk = nullptr;
+            for (auto &b : m->buckets)
+                if (b.rows_pad == rp) bk = &b;
+            if (!bk) { m->buckets.emplace_back(); bk = &m->buckets.back(); bk->rows_pad = rp; }
+            bk->worlds.push_back(w);
+            bk->count++;
+            bk->nb = std::max(bk->nb, nb);
+            bk->nj = std::max(bk->nj, nj);
+            bk->nc = std::max(bk->nc, nc);
+            bk->rows = std::max(bk->rows, rows);
+            bk->units = std::max(bk->units, row + nc);
+        }
         cache += row + 3 * nc;
         m->nb_max = std::max(m->nb_max, nb);
         m->nj_max = std::max(m->nj_max, nj);
@@ -356,6 +580,15 @@ kamino_status kamino_model_create(const kamino_model_desc *d, kamino_model_t *ou
                     "a world needs %d constraint rows; the shared-memory working set exceeds %zu bytes "
                     "(max %d padded rows)", rows, kMaxSmem, kMaxRowsPad);
     }
+    std::sort(m->buckets.begin(), m->buckets.end(),
+              [](const Bucket &a, const Bucket &b) { return a.rows_pad > b.rows_pad; });
+    for (auto &b : m->buckets) {
+        if (!choose_default(m, b)) {
+            const int rp = b.rows_pad;
+            delete m;
+            return fail(KAMINO_E_UNSUPPORTED, "no persistent configuration fits the bucket of %d rows", rp);
+        }
+    }
     std::vector<double> q0(7 * (size_t)B, 0.0);
     for (int b = 0; b < B; ++b) {
         if (d->body_q0) {
@@ -367,6 +600,12 @@ kamino_status kamino_model_create(const kamino_model_desc *d, kamino_model_t *ou
     kamino_status st = d->precision == KAMINO_FP64 ? build_device<double>(m, d, wa, wb, jm, jrow, frames, q0)
                                                    : build_device<float>(m, d, wa, wb, jm, jrow, frames, q0);
     if (st) { delete m; return st; }
+    for (auto &b : m->buckets) {
+        if ((st = upload<float>(m, (void **)&b.d_worlds, b.worlds.data(), b.worlds.size() * sizeof(int)))) {
+            delete m;
+            return st;
+        }
+    }
     *out = m;
     return KAMINO_OK;
 }
@@ -408,6 +647,7 @@ static void state_layout(kamino_model_t m, kamino_state_s *s) {
     take(s->off_warm, (size_t)m->cache_len * esz);
     take(s->off_res, (size_t)m->W * sizeof(kamino_residual));
     take(s->off_tau, (size_t)m->W * std::max(m->n_act_max, 1) * esz);
+    take(s->off_cnt, std::max<size_t>(m->buckets.size(), 1) * sizeof(int));
     s->bytes = o;
 }
 
@@ -518,6 +758,91 @@ kamino_status kamino_residuals(kamino_state_t s, kamino_residual *out_dev, void 
     cudaError_t e = cudaMemcpyAsync(out_dev, s->ptr(s->off_res), (size_t)s->model->W * sizeof(kamino_residual),
                                     cudaMemcpyDeviceToDevice, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "residual copy");
+    return KAMINO_OK;
+}
+
+kamino_status kamino_plan_get(kamino_model_t m, kamino_bucket_info *out, int32_t capacity, int32_t *count,
+                              int32_t *mode) {
+    if (!m || !count || !mode || (capacity > 0 && !out))
+        return fail(KAMINO_E_INVALID_ARG, "model, count and mode must not be NULL");
+    *count = (int32_t)m->buckets.size();
+    *mode = m->launch_mode;
+    for (int i = 0; i < capacity && i < (int)m->buckets.size(); ++i) {
+        const Bucket &b = m->buckets[i];
+        out[i].rows_pad = b.rows_pad;
+        out[i].num_worlds = b.count;
+        out[i].group_threads = b.group;
+        out[i].panel = b.panel;
+        out[i].grid = b.grid;
+        out[i].worlds_per_cta = b.per_cta;
+        out[i].tuned_ms = b.tuned_ms;
+        out[i].reserved = 0.0f;
+    }
+    return KAMINO_OK;
+}
+
+kamino_status kamino_plan_set_mode(kamino_model_t m, int32_t mode) {
+    if (!m) return fail(KAMINO_E_INVALID_ARG, "model must not be NULL");
+    if (mode != KAMINO_LAUNCH_SINGLE && mode != KAMINO_LAUNCH_PERSISTENT)
+        return fail(KAMINO_E_INVALID_ARG, "mode %d is not a KAMINO_LAUNCH_* value", mode);
+    m->launch_mode = mode;
+    return KAMINO_OK;
+}
+
+kamino_status kamino_autotune(kamino_state_t s, double dt, int32_t iters, double tol, const void *tau_dev,
+                              void *stream) {
+    if (!s) return fail(KAMINO_E_INVALID_ARG, "state must not be NULL");
+    if (!(dt > 0.0) || iters < 1 || !(tol >= 0.0)) return fail(KAMINO_E_INVALID_ARG, "bad dt / iters / tol");
+    return s->model->precision == KAMINO_FP64 ? autotune<double>(s, dt, iters, tol, tau_dev, (cudaStream_t)stream)
+                                              : autotune<float>(s, dt, iters, tol, tau_dev, (cudaStream_t)stream);
+}
+
+kamino_status kamino_graph_create(kamino_state_t s, double dt, int32_t iters, double tol, const void *tau_dev,
+                                  void *stream, kamino_graph_t *out) {
+    if (!s || !out) return fail(KAMINO_E_INVALID_ARG, "state and out must not be NULL");
+    *out = nullptr;
+    if (!stream) return fail(KAMINO_E_INVALID_ARG, "graph capture needs a non-default stream");
+    if (!(dt > 0.0) || iters < 1 || !(tol >= 0.0)) return fail(KAMINO_E_INVALID_ARG, "bad dt / iters / tol");
+    kamino_model_s *m = s->model;
+    kamino_status st;
+    // everything that is not a stream operation happens before the capture
+    if (m->precision == KAMINO_FP64) {
+        if ((st = ensure_plan_ready<double>(m))) return st;
+        for (auto &b : m->buckets)
+            if (!b.grid && (st = grid_of<double>(m, b))) return st;
+        if (!m->prepared) { prepare_step<double>(m->nb_panel, kMaxSmem); m->prepared = true; }
+    } else {
+        if ((st = ensure_plan_ready<float>(m))) return st;
+        for (auto &b : m->buckets)
+            if (!b.grid && (st = grid_of<float>(m, b))) return st;
+        if (!m->prepared) { prepare_step<float>(m->nb_panel, kMaxSmem); m->prepared = true; }
+    }
+    auto *g = new kamino_graph_s();
+    cudaStream_t cs = (cudaStream_t)stream;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) { delete g; return cuda_fail(e, "begin capture"); }
+    st = kamino_step(s, dt, iters, tol, tau_dev, stream);
+    e = cudaStreamEndCapture(cs, &g->graph);
+    if (st) { if (g->graph) cudaGraphDestroy(g->graph); delete g; return st; }
+    if (e != cudaSuccess) { delete g; return cuda_fail(e, "end capture"); }
+    e = cudaGraphInstantiate(&g->exec, g->graph, 0);
+    if (e != cudaSuccess) { cudaGraphDestroy(g->graph); delete g; return cuda_fail(e, "graph instantiate"); }
+    *out = g;
+    return KAMINO_OK;
+}
+
+kamino_status kamino_graph_launch(kamino_graph_t g, void *stream) {
+    if (!g) return fail(KAMINO_E_INVALID_ARG, "graph must not be NULL");
+    cudaError_t e = cudaGraphLaunch(g->exec, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "graph launch");
+    return KAMINO_OK;
+}
+
+kamino_status kamino_graph_destroy(kamino_graph_t g) {
+    if (!g) return KAMINO_OK;
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    delete g;
     return KAMINO_OK;
 }
 

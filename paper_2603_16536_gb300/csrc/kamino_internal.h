@@ -15,6 +15,7 @@ constexpr int kWarps = kThreads / 32;
 constexpr int kMaxRowsPad = 288;     // largest padded row count the step kernel supports
 constexpr int kMaxChunks = kMaxRowsPad / 32;
 constexpr int kMaxCandidates = 64;   // contact candidates per world
+constexpr int kSlots = 4;            // PADMM units (joint rows / contacts) per thread: units <= kSlots * group
 
 // Device-side view of a model (all pointers are device pointers; T = float or double).
 template <typename T>
@@ -51,6 +52,15 @@ struct StepArgs {
     int iters, nesterov, precond, warm_mode;
     // shared-memory layout bounds (maxima over the launched worlds)
     int nb_max, nj_max, nc_max, mp_max;
+};
+
+// Persistent launch over one bucket of worlds (see step_persistent).
+struct PersistentArgs {
+    const int *worlds;         // [count] world ids of the bucket
+    int count;
+    int *counter;              // device work counter, zero before the launch
+    int group;                 // threads per world: 32, 64, 128 or 256
+    size_t slice_bytes;        // shared memory per group (multiple of 16)
 };
 
 // Byte offsets of the per-world shared-memory working set.
@@ -108,5 +118,12 @@ cudaError_t launch_step(const StepArgs<T> &args, int num_worlds, int nb_panel, s
                         cudaStream_t stream);
 template <typename T>
 cudaError_t prepare_step(int nb_panel, size_t smem);
+template <typename T>
+cudaError_t launch_persistent(const StepArgs<T> &args, const PersistentArgs &p, int nb_panel, int grid, size_t smem,
+                              cudaStream_t stream);
+template <typename T>
+cudaError_t prepare_persistent(int nb_panel, size_t smem);
+template <typename T>
+cudaError_t occupancy_persistent(int nb_panel, size_t smem, int *blocks_per_sm);
 
 }  // namespace kamino

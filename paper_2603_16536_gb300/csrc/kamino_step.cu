@@ -91,6 +91,19 @@ __device__ __forceinline__ T warp_max(T v) {
     return v;
 }
 
+// A group of `size` threads (a multiple of 32) that owns one world.  `bar` is the named barrier it
+// synchronises on: 0 with size == blockDim.x is the CTA barrier; groups inside a CTA use ids 1..8.
+struct Group {
+    int tid, size, bar;
+    __device__ __forceinline__ int lane() const { return tid & 31; }
+    __device__ __forceinline__ int warp() const { return tid >> 5; }
+    __device__ __forceinline__ int warps() const { return size >> 5; }
+    __device__ __forceinline__ void sync() const {
+        if (size == 32) __syncwarp();
+        else asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(size) : "memory");
+    }
+};
+
 // packed lower-triangular, column-major storage of a symmetric mp x mp matrix
 __device__ __forceinline__ int col_start(int j, int mp) { return j * mp - (j * (j - 1)) / 2; }
 __device__ __forceinline__ int pidx(int i, int j, int mp) {  // requires i >= j
@@ -238,17 +251,17 @@ __device__ void joint_rows(int type, int par, int ch, const T *fr, const T *bq, 
     }
 }
 
-// Block-wide reductions of (max, max, max, sum); every thread gets the results.  The scratch is
+// Group-wide reductions of (max, max, max, sum); every thread gets the results.  The scratch is
 // double-buffered by `phase` so consecutive calls need only the one barrier inside.
 template <typename T>
-__device__ __forceinline__ void block_reduce4(T &a, T &b, T &c, T &d, T *red, int phase) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+__device__ __forceinline__ void group_reduce4(T &a, T &b, T &c, T &d, T *red, int phase, const Group &g) {
+    const int lane = g.lane(), warp = g.warp(), nw = g.warps();
     a = warp_max(a); b = warp_max(b); c = warp_max(c); d = warp_sum(d);
     T *r = red + phase * 4 * kWarps;
     if (lane == 0) { r[warp] = a; r[kWarps + warp] = b; r[2 * kWarps + warp] = c; r[3 * kWarps + warp] = d; }
-    __syncthreads();
+    g.sync();
     a = r[0]; b = r[kWarps]; c = r[2 * kWarps]; d = r[3 * kWarps];
-    for (int k = 1; k < kWarps; ++k) {
+    for (int k = 1; k < nw; ++k) {
         a = fmax(a, r[k]); b = fmax(b, r[kWarps + k]); c = fmax(c, r[2 * kWarps + k]); d += r[3 * kWarps + k];
     }
 }
@@ -256,10 +269,10 @@ __device__ __forceinline__ void block_reduce4(T &a, T &b, T &c, T &d, T *red, in
 // y = S x for a symmetric S in packed lower column-major storage (mp x mp).  Warp w walks the
 // columns j = w, w + 8, ...; each element S(i, j), i >= j, is read once from shared memory and
 // used twice: y_i += S_ij x_j (accumulated per lane in registers) and y_j += S_ij x_i (a warp
-// reduction per column).  The per-warp partial sums meet in `partial` ([kWarps][mp]).
+// reduction per column).  The per-warp partial sums meet in `partial` ([warps][mp]).
 template <typename T>
-__device__ void symv_packed(const T *S, int mp, const T *x, T *y, T *partial) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+__device__ void symv_packed(const T *S, int mp, const T *x, T *y, T *partial, const Group &g) {
+    const int lane = g.lane(), warp = g.warp(), nw = g.warps();
     T part[kMaxChunks], xr[kMaxChunks];
 #pragma unroll
     for (int c = 0; c < kMaxChunks; ++c) {
@@ -267,7 +280,7 @@ __device__ void symv_packed(const T *S, int mp, const T *x, T *y, T *partial) {
         part[c] = T(0);
         xr[c] = i < mp ? x[i] : T(0);
     }
-    for (int j = warp; j < mp; j += kWarps) {
+    for (int j = warp; j < mp; j += nw) {
         const T *col = S + col_start(j, mp) - j;   // col[i] = S(i, j) for i >= j
         const T xj = x[j];
         T dot = T(0);
@@ -289,13 +302,13 @@ __device__ void symv_packed(const T *S, int mp, const T *x, T *y, T *partial) {
         const int i = lane + 32 * c;
         if (i < mp) partial[warp * mp + i] = part[c];
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < mp; i += kThreads) {
+    g.sync();
+    for (int i = g.tid; i < mp; i += g.size) {
         T acc = y[i];
-        for (int w = 0; w < kWarps; ++w) acc += partial[w * mp + i];
+        for (int w = 0; w < nw; ++w) acc += partial[w * mp + i];
         y[i] = acc;
     }
-    __syncthreads();
+    g.sync();
 }
 
 // In-place blocked sweep of a symmetric positive definite matrix in packed lower storage:
@@ -303,17 +316,17 @@ __device__ void symv_packed(const T *S, int mp, const T *x, T *y, T *partial) {
 // T = A(:,K) A_KK^-1, rank-NB update A(i,j) -= T(i,:) A(j,K)^T for i, j outside K (4x4 register
 // tiles), then A(:,K) = T and A_KK = -A_KK^-1.  `P`, `Tm`, `Dm` live in the X scratch.
 template <typename T, int NB>
-__device__ void sweep_inverse(T *A, int mp, T *X) {
+__device__ void sweep_inverse(T *A, int mp, T *X, const Group &g) {
     T *P = X;                    // [mp][NB] old panel
     T *Tm = X + mp * NB;         // [mp][NB]
     T *Dm = X + 2 * mp * NB;     // [NB][NB]
-    const int tid = threadIdx.x;
+    const int tid = g.tid, nthr = g.size;
     for (int k0 = 0; k0 < mp; k0 += NB) {
-        for (int e = tid; e < mp * NB; e += kThreads) {
+        for (int e = tid; e < mp * NB; e += nthr) {
             const int i = e / NB, t = e - i * NB;
             P[e] = A[sidx(i, k0 + t, mp)];
         }
-        __syncthreads();
+        g.sync();
         // -- pivot block inverse by an unblocked sweep on one warp (result negated at the end)
         if (tid < 32) {
             for (int e = tid; e < NB * NB; e += 32) Dm[e] = P[(k0 + e / NB) * NB + (e % NB)];
@@ -343,9 +356,9 @@ __device__ void sweep_inverse(T *A, int mp, T *X) {
             }
             for (int e = tid; e < NB * NB; e += 32) Dm[e] = -Dm[e];   // = A_KK^-1
         }
-        __syncthreads();
+        g.sync();
         // -- T = A(:,K) A_KK^-1 for rows outside K
-        for (int e = tid; e < mp * NB; e += kThreads) {
+        for (int e = tid; e < mp * NB; e += nthr) {
             const int i = e / NB, t = e - i * NB;
             if (i >= k0 && i < k0 + NB) continue;
             T acc = T(0);
@@ -353,12 +366,12 @@ __device__ void sweep_inverse(T *A, int mp, T *X) {
             for (int u = 0; u < NB; ++u) acc = fma(P[i * NB + u], Dm[u * NB + t], acc);
             Tm[e] = acc;
         }
-        __syncthreads();
+        g.sync();
         // -- rank-NB update of the lower triangle outside K, 4x4 tiles
         const int nt = mp / 4;
         const int ntiles = nt * (nt + 1) / 2;
         const int kb0 = k0 / 4, kb1 = (k0 + NB) / 4;
-        for (int tile = tid; tile < ntiles; tile += kThreads) {
+        for (int tile = tid; tile < ntiles; tile += nthr) {
             int ti = (int)((sqrtf(8.0f * (float)tile + 1.0f) - 1.0f) * 0.5f);
             while (ti * (ti + 1) / 2 > tile) --ti;
             while ((ti + 1) * (ti + 2) / 2 <= tile) ++ti;
@@ -392,9 +405,9 @@ __device__ void sweep_inverse(T *A, int mp, T *X) {
                 }
             }
         }
-        __syncthreads();
+        g.sync();
         // -- write back the swept panel
-        for (int e = tid; e < mp * NB; e += kThreads) {
+        for (int e = tid; e < mp * NB; e += nthr) {
             const int i = e / NB, t = e - i * NB;
             const int j = k0 + t;
             if (i >= k0 && i < k0 + NB) {
@@ -403,16 +416,14 @@ __device__ void sweep_inverse(T *A, int mp, T *X) {
                 A[sidx(i, j, mp)] = Tm[e];
             }
         }
-        __syncthreads();
+        g.sync();
     }
 }
 
 // ----------------------------------------------------------------------------- the step kernel
 template <typename T, int NB>
-__global__ void __launch_bounds__(kThreads, 1) step_kernel(const StepArgs<T> a) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int w = a.world_order ? a.world_order[blockIdx.x] : (int)blockIdx.x;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+__device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, const Group &g) {
+    const int tid = g.tid, lane = g.lane(), warp = g.warp(), nthr = g.size, nwarps = g.warps();
     const ModelView<T> &M = a.m;
     const int4 wa = M.world_a[w], wb = M.world_b[w];
     const int b0 = wa.x, j0 = wa.y, c0 = wa.z, k0 = wa.w;
@@ -429,9 +440,10 @@ __global__ void __launch_bounds__(kThreads, 1) step_kernel(const StepArgs<T> a) 
     T *red = (T *)(smem + L.red);
     int *misc = (int *)(smem + L.misc);
     const T dt = a.dt, kbias = a.beta / a.dt;
+    if (tid == 0) misc[1] = 0;   // non-finite flag of this world
 
     // ---- 1. body kinematics
-    for (int i = tid; i < nb; i += kThreads) {
+    for (int i = tid; i < nb; i += nthr) {
         const T *gq = a.body_q + 7 * (size_t)(b0 + i);
         const T *gu = a.body_u + 6 * (size_t)(b0 + i);
         T q[7];
@@ -459,17 +471,17 @@ __global__ void __launch_bounds__(kThreads, 1) step_kernel(const StepArgs<T> a) 
         }
         bminv[i] = T(1) / m;
     }
-    __syncthreads();
+    g.sync();
 
     // ---- 2. joint rows and actuation wrenches (thread per joint); 3. contacts (last warp)
-    for (int j = tid; j < nj; j += kThreads) {
+    for (int j = tid; j < nj; j += nthr) {
         const int4 meta = M.joint_meta[j0 + j];
         const bool act = meta.w >= 0 && a.tau != nullptr;
         const T val = act ? a.tau[(size_t)w * M.n_act_max + meta.w] : T(0);
         joint_rows(meta.x, meta.y, meta.z, M.joint_frames + 14 * (size_t)(j0 + j), bq, bR, M.joint_row[j0 + j], kbias,
                    rbody, rJ, rvs, act, val, jwr + 12 * j);
     }
-    if (warp == kWarps - 1) {
+    if (warp == nwarps - 1) {
         int count = 0;
         for (int cb = 0; cb < nc; cb += 32) {
             const int c = cb + lane;
@@ -506,14 +518,14 @@ __global__ void __launch_bounds__(kThreads, 1) step_kernel(const StepArgs<T> a) 
         }
         if (lane == 0) misc[0] = count;
     }
-    __syncthreads();
+    g.sync();
     const int nact = misc[0];
     const int m = nbil + 3 * nact;
     const int mp = ((m + NB - 1) / NB) * NB;
     const int nunits = nbil + nact;
 
     // ---- 4. u_free = u + dt M^-1 h
-    for (int i = tid; i < nb; i += kThreads) {
+    for (int i = tid; i < nb; i += nthr) {
         T f[3] = {M.gx * (T(1) / bminv[i]), M.gy * (T(1) / bminv[i]), M.gz * (T(1) / bminv[i])};
         T tq[3] = {T(0), T(0), T(0)};
         for (int j = 0; j < nj; ++j) {
@@ -538,11 +550,11 @@ __global__ void __launch_bounds__(kThreads, 1) step_kernel(const StepArgs<T> a) 
             bufree[6 * i + 3 + k] = bu[6 * i + 3 + k] + dt * dw[k];
         }
     }
-    __syncthreads();
+    g.sync();
 
     // ---- 5a. per row: M^-1 J^T blocks (into X), diag(D), v_f
     T *MJ = X;
-    for (int r = tid; r < m; r += kThreads) {
+    for (int r = tid; r < m; r += nthr) {
         const int ba = rbody[2 * r], bbd = rbody[2 * r + 1];
         const T *J = rJ + 12 * r;
         T d = T(0), v = rvs[r];
@@ -558,9 +570,9 @@ __global__ void __launch_bounds__(kThreads, 1) step_kernel(const StepArgs<T> a) 
         x[r] = d;      // diag(D), temporarily
         vf[r] = v;
     }
-    __syncthreads();
+    g.sync();
     // ---- 5b. Jacobi scaling (tangent rows of a contact share one scale), scaled mu, scaled v_f
-    for (int r = tid; r < mp; r += kThreads) {
+    for (int r = tid; r < mp; r += nthr) {
         T pr = T(1);
         if (r < m && a.precond) {
             if (r < nbil) {
@@ -573,18 +585,18 @@ __global__ void __launch_bounds__(kThreads, 1) step_kernel(const StepArgs<T> a) 
         }
         p[r] = pr;
     }
-    __syncthreads();
-    for (int r = tid; r < mp; r += kThreads) {
+    g.sync();
+    for (int r = tid; r < mp; r += nthr) {
         vf[r] = r < m ? p[r] * vf[r] : T(0);
         bb[r] = T(0);
     }
-    for (int k = tid; k < nact; k += kThreads) {
+    for (int k = tid; k < nact; k += nthr) {
         const int rt = nbil + 3 * k;
         mut[k] = M.world_mu[w] * p[rt + 2] / p[rt];
     }
     // ---- 5c. A = P D P + (eta + rho) I in packed storage (identity on the padding rows)
     const T shift = a.eta + a.rho;
-    for (int j = warp; j < mp; j += kWarps) {
+    for (int j = warp; j < mp; j += nwarps) {
         T *col = A + col_start(j, mp) - j;
         const int ja = j < m ? rbody[2 * j] : -2, jb = j < m ? rbody[2 * j + 1] : -2;
         for (int i = j + lane; i < mp; i += 32) {
@@ -605,11 +617,11 @@ __global__ void __launch_bounds__(kThreads, 1) step_kernel(const StepArgs<T> a) 
             col[i] = v;
         }
     }
-    __syncthreads();
+    g.sync();
 
     // ---- 6. warm start: x0 = y0 = P^-1 lambda0, z0 = v0 + Gamma(v0), v0 = D~ x0 + v~_f
     const bool warm = a.warm_mode != KAMINO_WARM_COLD;
-    for (int r = tid; r < mp; r += kThreads) {
+    for (int r = tid; r < mp; r += nthr) {
         T l0 = T(0);
         if (warm && r < m) {
             const T *src = a.warm_mode == KAMINO_WARM_EXTERNAL ? a.warm : a.cache;
@@ -623,10 +635,10 @@ __global__ void __launch_bounds__(kThreads, 1) step_kernel(const StepArgs<T> a) 
         }
         x[r] = l0 / p[r];
     }
-    __syncthreads();
+    g.sync();
     if (warm) {
-        symv_packed(A, mp, x, xn, X);          // xn = A x0 = D~ x0 + (eta + rho) x0
-        for (int u = tid; u < nunits; u += kThreads) {
+        symv_packed(A, mp, x, xn, X, g);          // xn = A x0 = D~ x0 + (eta + rho) x0
+        for (int u = tid; u < nunits; u += nthr) {
             if (u < nbil) {
                 const T v0 = xn[u] - shift * x[u] + vf[u];
                 z[u] = v0;
@@ -639,14 +651,14 @@ __global__ void __launch_bounds__(kThreads, 1) step_kernel(const StepArgs<T> a) 
             }
         }
     }
-    for (int r = tid; r < mp; r += kThreads) {
+    for (int r = tid; r < mp; r += nthr) {
         if (!warm || r >= m) z[r] = T(0);
         y[r] = x[r]; yh[r] = x[r]; zh[r] = z[r];
     }
-    __syncthreads();
+    g.sync();
 
     // ---- 7. A <- -A^-1 (blocked sweep)
-    sweep_inverse<T, NB>(A, mp, X);
+    sweep_inverse<T, NB>(A, mp, X, g);
 
     // ---- 8. Proximal-ADMM (Alg. 1)
     const T eta = a.eta, rho = a.rho, irho = T(1) / a.rho;
@@ -656,7 +668,7 @@ __global__ void __launch_bounds__(kThreads, 1) step_kernel(const StepArgs<T> a) 
     bool converged = false;
     for (it = 1; it <= a.iters; ++it) {
         // s = Gamma(z^), b = v_f + s - eta x - rho y^ - z^
-        for (int u = tid; u < nunits; u += kThreads) {
+        for (int u = tid; u < nunits; u += nthr) {
             if (u < nbil) {
                 bb[u] = vf[u] - eta * x[u] - rho * yh[u] - zh[u];
             } else {
@@ -666,15 +678,15 @@ __global__ void __launch_bounds__(kThreads, 1) step_kernel(const StepArgs<T> a) 
                     bb[r0 + t] = vf[r0 + t] + (t == 2 ? s : T(0)) - eta * x[r0 + t] - rho * yh[r0 + t] - zh[r0 + t];
             }
         }
-        __syncthreads();
+        g.sync();
         // x^i = -(D~ + (eta + rho) I)^-1 b = A b   (A holds -A_orig^-1)
-        symv_packed(A, mp, bb, xn, X);
+        symv_packed(A, mp, bb, xn, X, g);
         // y^i = Pi_K(x^i - z^/rho), z^i = z^ - rho (x^i - y^i), residual terms
         T lrp = T(0), lrd = T(0), lrc = T(0), lc = T(0);
-        T ynew[2][3], znew[2][3];   // per owned unit: a thread owns units tid and tid + kThreads
+        T ynew[kSlots][3], znew[kSlots][3];   // a thread owns units tid + s * group size, s < kSlots
 #pragma unroll
-        for (int sl = 0; sl < 2; ++sl) {
-            const int u = tid + sl * kThreads;
+        for (int sl = 0; sl < kSlots; ++sl) {
+            const int u = tid + sl * nthr;
             if (u >= nunits) continue;
             if (u < nbil) {
                 const T xv = xn[u];
@@ -714,7 +726,7 @@ __global__ void __launch_bounds__(kThreads, 1) step_kernel(const StepArgs<T> a) 
                 lrc = fmax(lrc, fabs(ydz));
             }
         }
-        block_reduce4(lrp, lrd, lrc, lc, red, it & 1);
+        group_reduce4(lrp, lrd, lrc, lc, red, it & 1, g);
         rp = lrp; rd = lrd; rc = lrc;
         // Nesterov with adaptive restart (uniform decision), then commit the iterates
         T beta_n = T(0);
@@ -732,8 +744,8 @@ __global__ void __launch_bounds__(kThreads, 1) step_kernel(const StepArgs<T> a) 
             }
         }
 #pragma unroll
-        for (int sl = 0; sl < 2; ++sl) {
-            const int u = tid + sl * kThreads;
+        for (int sl = 0; sl < kSlots; ++sl) {
+            const int u = tid + sl * nthr;
             if (u >= nunits) continue;
             const int r0 = u < nbil ? u : nbil + 3 * (u - nbil);
             const int cnt = u < nbil ? 1 : 3;
@@ -751,13 +763,13 @@ __global__ void __launch_bounds__(kThreads, 1) step_kernel(const StepArgs<T> a) 
         if (rp < a.tol && rd < a.tol && rc < a.tol) { converged = true; break; }
     }
     if (it > a.iters) it = a.iters;
-    __syncthreads();
+    g.sync();
 
     // ---- 9. lambda = P y; u+ = u_free + M^-1 J^T lambda; integrate; cache; report
-    for (int r = tid; r < m; r += kThreads) xn[r] = p[r] * y[r];
-    __syncthreads();
+    for (int r = tid; r < m; r += nthr) xn[r] = p[r] * y[r];
+    g.sync();
     bool bad = false;
-    for (int i = tid; i < nb; i += kThreads) {
+    for (int i = tid; i < nb; i += nthr) {
         T f[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
         for (int r = 0; r < m; ++r) {
             const T l = xn[r];
@@ -797,13 +809,15 @@ __global__ void __launch_bounds__(kThreads, 1) step_kernel(const StepArgs<T> a) 
         }
     }
     // impulse cache: joint rows, then 3 per candidate (zero when inactive)
-    for (int r = tid; r < nbil; r += kThreads) a.cache[k0 + r] = xn[r];
-    for (int e = tid; e < 3 * nc; e += kThreads) {
+    for (int r = tid; r < nbil; r += nthr) a.cache[k0 + r] = xn[r];
+    for (int e = tid; e < 3 * nc; e += nthr) {
         const int c = e / 3, t = e % 3;
         const int s = cslot[c];
         a.cache[k0 + nbil + e] = s >= 0 ? xn[nbil + 3 * s + t] : T(0);
     }
-    const int any_bad = __syncthreads_or(bad);
+    if (bad) atomicOr(misc + 1, 1);
+    g.sync();
+    const int any_bad = misc[1];
     if (tid == 0) {
         kamino_residual rep;
         rep.iterations = it;
@@ -818,16 +832,45 @@ __global__ void __launch_bounds__(kThreads, 1) step_kernel(const StepArgs<T> a) 
     }
 }
 
+
+// One world per CTA (256 threads), grid = number of worlds (or of entries in a.world_order).
+template <typename T, int NB>
+__global__ void __launch_bounds__(kThreads, 1) step_kernel(const StepArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int w = a.world_order ? a.world_order[blockIdx.x] : (int)blockIdx.x;
+    const Group g{(int)threadIdx.x, kThreads, 0};
+    world_step<T, NB>(a, w, smem, g);
+}
+
+// Persistent launch over a list of worlds: the CTA is split into groups of `group` threads, each
+// with its own slice of shared memory; every group pulls the next world from an atomic counter
+// until the list is exhausted (dynamic load balance across worlds whose iteration counts differ).
+template <typename T, int NB>
+__global__ void __launch_bounds__(kThreads, 1) step_persistent(const StepArgs<T> a, PersistentArgs p) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int gi = threadIdx.x / p.group;
+    const int ngroups = kThreads / p.group;
+    const Group g{(int)threadIdx.x - gi * p.group, p.group, ngroups > 1 ? 1 + gi : 0};
+    unsigned char *slice = smem + (size_t)gi * p.slice_bytes;
+    int *slot = (int *)(smem + (size_t)ngroups * p.slice_bytes) + gi;
+    for (int round = 0; round < p.count; ++round) {   // bounded: at most one world per round
+        if (g.tid == 0) *slot = atomicAdd(p.counter, 1);
+        g.sync();
+        const int idx = *slot;
+        g.sync();
+        if (idx >= p.count) break;
+        world_step<T, NB>(a, p.worlds[idx], slice, g);
+        g.sync();
+    }
+}
+
 }  // namespace
 
 template <typename T>
 cudaError_t prepare_step(int nb_panel, size_t smem) {
-    cudaError_t e;
     if (nb_panel == 16)
-        e = cudaFuncSetAttribute(step_kernel<T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    else
-        e = cudaFuncSetAttribute(step_kernel<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    return e;
+        return cudaFuncSetAttribute(step_kernel<T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return cudaFuncSetAttribute(step_kernel<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
 template <typename T>
@@ -840,9 +883,42 @@ cudaError_t launch_step(const StepArgs<T> &args, int num_worlds, int nb_panel, s
     return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t prepare_persistent(int nb_panel, size_t smem) {
+    if (nb_panel == 16)
+        return cudaFuncSetAttribute(step_persistent<T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return cudaFuncSetAttribute(step_persistent<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+template <typename T>
+cudaError_t occupancy_persistent(int nb_panel, size_t smem, int *blocks_per_sm) {
+    if (nb_panel == 16)
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, step_persistent<T, 16>, kThreads, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, step_persistent<T, 8>, kThreads, smem);
+}
+
+template <typename T>
+cudaError_t launch_persistent(const StepArgs<T> &args, const PersistentArgs &p, int nb_panel, int grid, size_t smem,
+                              cudaStream_t stream) {
+    if (p.count <= 0 || grid <= 0) return cudaSuccess;
+    if (nb_panel == 16)
+        step_persistent<T, 16><<<grid, kThreads, smem, stream>>>(args, p);
+    else
+        step_persistent<T, 8><<<grid, kThreads, smem, stream>>>(args, p);
+    return cudaGetLastError();
+}
+
 template cudaError_t prepare_step<float>(int, size_t);
 template cudaError_t prepare_step<double>(int, size_t);
 template cudaError_t launch_step<float>(const StepArgs<float> &, int, int, size_t, cudaStream_t);
 template cudaError_t launch_step<double>(const StepArgs<double> &, int, int, size_t, cudaStream_t);
+template cudaError_t prepare_persistent<float>(int, size_t);
+template cudaError_t prepare_persistent<double>(int, size_t);
+template cudaError_t occupancy_persistent<float>(int, size_t, int *);
+template cudaError_t occupancy_persistent<double>(int, size_t, int *);
+template cudaError_t launch_persistent<float>(const StepArgs<float> &, const PersistentArgs &, int, int, size_t,
+                                              cudaStream_t);
+template cudaError_t launch_persistent<double>(const StepArgs<double> &, const PersistentArgs &, int, int, size_t,
+                                               cudaStream_t);
 
 }  // namespace kamino

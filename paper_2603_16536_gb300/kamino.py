@@ -59,6 +59,15 @@ class ModelInfo(C.Structure):
                 ("precision", C.c_int32), ("threads_per_world", C.c_int32), ("smem_bytes", C.c_int64)]
 
 
+LAUNCH_SINGLE, LAUNCH_PERSISTENT = 0, 1
+
+
+class BucketInfo(C.Structure):
+    _fields_ = [("rows_pad", C.c_int32), ("num_worlds", C.c_int32), ("group_threads", C.c_int32),
+                ("panel", C.c_int32), ("grid", C.c_int32), ("worlds_per_cta", C.c_int32),
+                ("tuned_ms", C.c_float), ("reserved", C.c_float)]
+
+
 RESIDUAL_DTYPE = np.dtype([("iterations", np.int32), ("status", np.int32), ("num_rows", np.int32),
                            ("num_contacts", np.int32), ("r_primal", np.float32), ("r_dual", np.float32),
                            ("r_compl", np.float32), ("reserved", np.float32)])
@@ -94,6 +103,12 @@ def load_library(path: str | None = None):
         "kamino_step": ([vp, dbl, i32, dbl, vp, vp], i32),
         "kamino_residuals": ([vp, vp, vp], i32),
         "kamino_last_error": ([], C.c_char_p),
+        "kamino_plan_get": ([vp, C.POINTER(BucketInfo), i32, C.POINTER(i32), C.POINTER(i32)], i32),
+        "kamino_plan_set_mode": ([vp, i32], i32),
+        "kamino_autotune": ([vp, dbl, i32, dbl, vp, vp], i32),
+        "kamino_graph_create": ([vp, dbl, i32, dbl, vp, vp, C.POINTER(vp)], i32),
+        "kamino_graph_launch": ([vp, vp], i32),
+        "kamino_graph_destroy": ([vp], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -175,6 +190,18 @@ class Model:
         _check(load_library().kamino_model_set_params(self.handle, C.byref(params)))
         self.params = params
 
+    def plan(self):
+        """(mode, [bucket dicts]) of the current launch plan."""
+        cap = 64
+        arr = (BucketInfo * cap)()
+        n, mode = C.c_int32(), C.c_int32()
+        _check(load_library().kamino_plan_get(self.handle, arr, cap, C.byref(n), C.byref(mode)))
+        out = [{f: getattr(arr[i], f) for f, _ in BucketInfo._fields_ if f != "reserved"} for i in range(n.value)]
+        return mode.value, out
+
+    def set_launch_mode(self, mode: int):
+        _check(load_library().kamino_plan_set_mode(self.handle, int(mode)))
+
     def __del__(self):
         if getattr(self, "handle", None) and _lib is not None:
             _lib.kamino_model_destroy(self.handle)
@@ -225,6 +252,24 @@ class State:
         _check(load_library().kamino_step(self.handle, float(dt), int(iters), float(tol), tptr,
                                           C.c_void_p(stream.cuda_stream)))
 
+    def autotune(self, dt: float, iters: int, tol: float, tau=None, stream=None):
+        """Time every feasible per-bucket configuration on this state's worlds (state unchanged)."""
+        import torch
+        stream = stream or torch.cuda.current_stream()
+        tptr = None if tau is None else C.c_void_p(tau.data_ptr())
+        _check(load_library().kamino_autotune(self.handle, float(dt), int(iters), float(tol), tptr,
+                                              C.c_void_p(stream.cuda_stream)))
+
+    def graph(self, dt: float, iters: int, tol: float, tau=None, stream=None):
+        """Capture one step into a CUDA graph (returns a StepGraph)."""
+        import torch
+        stream = stream or torch.cuda.current_stream()
+        tptr = None if tau is None else C.c_void_p(tau.data_ptr())
+        h = C.c_void_p()
+        _check(load_library().kamino_graph_create(self.handle, float(dt), int(iters), float(tol), tptr,
+                                                  C.c_void_p(stream.cuda_stream), C.byref(h)))
+        return StepGraph(h, self)
+
     def upload(self, which, host: np.ndarray, stream=None):
         import torch
         s = (stream or torch.cuda.current_stream()).cuda_stream
@@ -245,4 +290,22 @@ class State:
     def __del__(self):
         if getattr(self, "handle", None) and _lib is not None:
             _lib.kamino_state_free(self.handle)
+            self.handle = None
+
+
+class StepGraph:
+    """A captured step (kamino_graph_create); launch() replays it on a stream."""
+
+    def __init__(self, handle, state):
+        self.handle = handle
+        self.state = state     # keeps the state alive while the graph exists
+
+    def launch(self, stream=None):
+        import torch
+        stream = stream or torch.cuda.current_stream()
+        _check(load_library().kamino_graph_launch(self.handle, C.c_void_p(stream.cuda_stream)))
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.kamino_graph_destroy(self.handle)
             self.handle = None

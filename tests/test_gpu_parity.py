@@ -215,3 +215,81 @@ def test_full_size_bipeds_sampled_parity(K):
             eu, eq = errors(ws.body_q0[bs], qg[bs], ug[bs], ref_st.q[bs], ref_st.u[bs], dt)
             # tol 1e-5 on the GPU side bounds the velocity error at a few 1e-4 of the step scale
             assert eu <= 1e-2 and eq <= 1e-2, (w, eu, eq)
+
+
+# ----------------------------------------------------------------------------- heterogeneous plan
+def _hetero(n=4, seed=7):
+    return wg.concat([wg.make_fourbar(n, seed=seed), wg.make_stewart(n, seed=seed),
+                      wg.make_excavator(n, seed=seed), wg.make_biped(n, seed=seed)])
+
+
+def test_persistent_plan_matches_single_launch(K):
+    """The bucketed persistent launch (groups of 32..256 threads per world) gives the same result
+    as one CTA per world, and both match the oracle."""
+    ws = _hetero()
+    tau = wg.actuation(ws, 7, 0)
+    dt = 2e-3
+    model = K.Model(ws, "fp32", K.make_params(rho=0.1))
+    mode, buckets = model.plan()
+    assert mode == K.LAUNCH_SINGLE and len(buckets) == 4
+    assert sorted(b["group_threads"] for b in buckets) == [32, 64, 64, 256]
+    q1, u1, rep1, _ = gpu_step(K, ws, ws.body_q0, ws.body_u0, tau, dt, 20000, 1e-6, model=model)
+    model.set_launch_mode(K.LAUNCH_PERSISTENT)
+    q2, u2, rep2, _ = gpu_step(K, ws, ws.body_q0, ws.body_u0, tau, dt, 20000, 1e-6, model=model)
+    np.testing.assert_array_equal(rep1["num_rows"], rep2["num_rows"])
+    np.testing.assert_allclose(u2, u1, atol=1e-5 * max(1.0, np.abs(u1).max()))
+    ref, infos = oracle_step(ws, ws.body_q0, ws.body_u0, tau, dt, eps=1e-10)
+    check_report(rep2, infos)
+    eu, eq = errors(ws.body_q0, q2, u2, ref.q, ref.u, dt)
+    assert eu <= 1e-4 and eq <= 1e-4
+
+
+def test_autotune_and_graph_replay(K):
+    """Autotune picks a configuration per bucket without changing the state; a captured graph
+    replays the step exactly like an eager step."""
+    ws = _hetero(n=16, seed=8)
+    dt, iters, tol = 2e-3, 300, 1e-5
+    model = K.Model(ws, "fp32", K.make_params(rho=0.1))
+    st = K.State(model)
+    tau = torch.tensor(wg.actuation(ws, 8, 0), dtype=torch.float32, device="cuda").contiguous()
+    q0 = st.body_q.clone()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        st.autotune(dt, iters, tol, tau, stream)
+    torch.cuda.synchronize()
+    assert torch.equal(st.body_q, q0)
+    mode, buckets = model.plan()
+    assert mode == K.LAUNCH_PERSISTENT
+    assert all(b["tuned_ms"] > 0 for b in buckets)
+    # eager reference on a twin state
+    st2 = K.State(model)
+    st2.step(dt, iters, tol, tau)
+    with torch.cuda.stream(stream):
+        g = st.graph(dt, iters, tol, tau, stream)
+        g.launch(stream)
+    torch.cuda.synchronize()
+    torch.testing.assert_close(st.body_u, st2.body_u, atol=1e-6, rtol=1e-5)
+    with torch.cuda.stream(stream):
+        g.launch(stream)
+        g.launch(stream)
+    torch.cuda.synchronize()
+    assert torch.isfinite(st.body_u).all()
+
+
+def test_heightfield_bipeds_fp32(K):
+    """Bipeds on the random heightfield (32 grid candidates per world, up to 276 rows, panel 8):
+    after the feet land, one FP32 step against the oracle."""
+    ws = wg.make_biped_heightfield(num_worlds=4, seed=9)
+    st = T.initial_state(ws)
+    params = T.SolverParams(rho=0.1, eps=1e-8, n_max=20000)
+    for k in range(15):
+        st, infos = T.step(ws, st, wg.actuation(ws, 9, k), 2e-3, params)
+    assert sum(len(i.contact_ids) for i in infos) > 0
+    if not _margin_clear(None, ws, st.q):
+        pytest.skip("a candidate sits on the activation threshold")
+    tau = wg.actuation(ws, 9, 15)
+    qg, ug, rep, _ = gpu_step(K, ws, st.q, st.u, tau, 2e-3, 20000, 1e-6)
+    ref, infos = oracle_step(ws, st.q, st.u, tau, 2e-3, eps=1e-10)
+    check_report(rep, infos)
+    eu, eq = errors(st.q, qg, ug, ref.q, ref.u, 2e-3)
+    assert eu <= 1e-4 and eq <= 1e-4, (eu, eq)

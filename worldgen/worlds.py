@@ -438,6 +438,14 @@ def make_biped(num_worlds=4096, seed=0, terrain=None, foot_points="corners", z_l
     return _assemble(worlds, terrain=terrain or {"kind": TERRAIN_PLANE})
 
 
+def make_biped_heightfield(num_worlds=16384, seed=0, hmax=0.05):
+    """Bipeds on a seeded 64 x 64 heightfield (heights U[0, hmax], 1/32 m cells): 4 x 4 sample
+    points under each foot (32 candidates per world, up to 276 rows), pelvis raised by hmax so the
+    feet start above the terrain."""
+    hf = make_heightfield(seed=seed, hmax=hmax)
+    return make_biped(num_worlds=num_worlds, seed=seed, terrain=hf, foot_points="grid", z_lift=hmax)
+
+
 # ----------------------------------------------------------------------------- Stewart platform
 def _stewart_world(rng):
     wd = _World(KIND_STEWART)
