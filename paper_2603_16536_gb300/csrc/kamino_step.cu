@@ -266,45 +266,90 @@ __device__ __forceinline__ void group_reduce4(T &a, T &b, T &c, T &d, T *red, in
     }
 }
 
-// y = S x for a symmetric S in packed lower column-major storage (mp x mp).  Warp w walks the
-// columns j = w, w + 8, ...; each element S(i, j), i >= j, is read once from shared memory and
-// used twice: y_i += S_ij x_j (accumulated per lane in registers) and y_j += S_ij x_i (a warp
-// reduction per column).  The per-warp partial sums meet in `partial` ([warps][mp]).
+// 16 consecutive values from a 16-byte aligned shared-memory address (vector loads).
+__device__ __forceinline__ void load16(const float *p, float (&v)[16]) {
+    const float4 *q = reinterpret_cast<const float4 *>(p);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float4 t = q[k];
+        v[4 * k] = t.x; v[4 * k + 1] = t.y; v[4 * k + 2] = t.z; v[4 * k + 3] = t.w;
+    }
+}
+__device__ __forceinline__ void load16(const double *p, double (&v)[16]) {
+    const double2 *q = reinterpret_cast<const double2 *>(p);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const double2 t = q[k];
+        v[2 * k] = t.x; v[2 * k + 1] = t.y;
+    }
+}
+
+// Sum over the 32 lanes of v[c], delivered to lane c (recursive halving: 16 + 8 + 4 + 2 + 1
+// shuffles; at each level a lane keeps the half of its values whose index has its lane bit).
+template <typename T>
+__device__ __forceinline__ T transpose_reduce32(T (&v)[32], int lane) {
+#pragma unroll
+    for (int h = 16; h >= 1; h >>= 1) {
+        const bool up = (lane & h) != 0;
+#pragma unroll
+        for (int k = 0; k < h; ++k) {
+            const T send = up ? v[k] : v[k + h];
+            const T keep = up ? v[k + h] : v[k];
+            v[k] = keep + __shfl_xor_sync(0xffffffffu, send, h);
+        }
+    }
+    return v[0];
+}
+
+// y = S x for a symmetric S in packed lower column-major storage (mp x mp).  The lower triangle is
+// cut into 32 x 32 tiles (I >= J) dealt round-robin to the warps of the group.  In a tile, lane l
+// owns row 32I + l: every element S(i, j) is read once from shared memory (consecutive lanes read
+// consecutive addresses) and used twice, for y_i += S_ij x_j in a register and for
+// y_j += S_ij x_i in a per-column register that one transpose-reduction per tile sums over the
+// lanes.  Per-warp partial rows (`partial`, [warps][mp]) are summed at the end, so the result does
+// not depend on scheduling.
 template <typename T>
 __device__ void symv_packed(const T *S, int mp, const T *x, T *y, T *partial, const Group &g) {
     const int lane = g.lane(), warp = g.warp(), nw = g.warps();
-    T part[kMaxChunks], xr[kMaxChunks];
+    T *part = partial + warp * mp;
+    for (int i = lane; i < mp; i += 32) part[i] = T(0);
+    __syncwarp();
+    const int nt = (mp + 31) >> 5;
+    const int ntiles = nt * (nt + 1) / 2;
+    for (int t = warp; t < ntiles; t += nw) {
+        int I = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+        while (I * (I + 1) / 2 > t) --I;
+        while ((I + 1) * (I + 2) / 2 <= t) ++I;
+        const int J = t - I * (I + 1) / 2;
+        const int i = 32 * I + lane;
+        const bool rowok = i < mp;
+        const T xi = rowok ? x[i] : T(0);
+        T rowacc = T(0);
+        T col[32];
+        int j = 32 * J;
+        int cs = col_start(j, mp) - j;     // S(i, j) = S[cs + i] for i >= j
 #pragma unroll
-    for (int c = 0; c < kMaxChunks; ++c) {
-        const int i = lane + 32 * c;
-        part[c] = T(0);
-        xr[c] = i < mp ? x[i] : T(0);
-    }
-    for (int j = warp; j < mp; j += nw) {
-        const T *col = S + col_start(j, mp) - j;   // col[i] = S(i, j) for i >= j
-        const T xj = x[j];
-        T dot = T(0);
-#pragma unroll
-        for (int c = 0; c < kMaxChunks; ++c) {
-            if (32 * c + 31 < j || 32 * c >= mp) continue;   // warp-uniform
-            const int i = lane + 32 * c;
-            if (i >= j && i < mp) {
-                const T s = col[i];
-                part[c] = fma(s, xj, part[c]);
-                if (i > j) dot = fma(s, xr[c], dot);
+        for (int c = 0; c < 32; ++c) {
+            T s = T(0), xj = T(0);
+            if (j < mp) {
+                xj = x[j];
+                if (rowok && i >= j) s = S[cs + i];
+                cs += mp - j - 1;
             }
+            rowacc = fma(s, xj, rowacc);
+            col[c] = i > j ? s * xi : T(0);
+            ++j;
         }
-        dot = warp_sum(dot);
-        if (lane == 0) y[j] = dot;
-    }
-#pragma unroll
-    for (int c = 0; c < kMaxChunks; ++c) {
-        const int i = lane + 32 * c;
-        if (i < mp) partial[warp * mp + i] = part[c];
+        const T csum = transpose_reduce32(col, lane);
+        if (rowok) part[i] += rowacc;
+        __syncwarp();
+        const int jc = 32 * J + lane;
+        if (jc < mp) part[jc] += csum;
+        __syncwarp();
     }
     g.sync();
     for (int i = g.tid; i < mp; i += g.size) {
-        T acc = y[i];
+        T acc = T(0);
         for (int w = 0; w < nw; ++w) acc += partial[w * mp + i];
         y[i] = acc;
     }
@@ -312,31 +357,36 @@ __device__ void symv_packed(const T *S, int mp, const T *x, T *y, T *partial, co
 }
 
 // In-place blocked sweep of a symmetric positive definite matrix in packed lower storage:
-// sweeping every pivot turns A into -A^-1.  Panels of NB columns: invert the NB x NB pivot block,
-// T = A(:,K) A_KK^-1, rank-NB update A(i,j) -= T(i,:) A(j,K)^T for i, j outside K (4x4 register
-// tiles), then A(:,K) = T and A_KK = -A_KK^-1.  `P`, `Tm`, `Dm` live in the X scratch.
+// sweeping every pivot turns A into -A^-1.  Per panel K of NB columns: PT = A(:, K)^T, the NB x NB
+// pivot block inverted by an unblocked sweep on one warp, TT = (A(:, K) A_KK^-1)^T, the rank-NB
+// update A(i, j) -= T(i, :) P(j, :)^T for i, j outside K, then A(:, K) = T and A_KK = -A_KK^-1.
+// The panels are stored transposed ([NB][mp]) so that lanes walking consecutive rows read
+// consecutive words; the update runs in strips of 32 rows x 16 columns per warp (lane = row,
+// 16 accumulators), reading the panel row of P as broadcast float4 loads.
 template <typename T, int NB>
 __device__ void sweep_inverse(T *A, int mp, T *X, const Group &g) {
-    T *P = X;                    // [mp][NB] old panel
-    T *Tm = X + mp * NB;         // [mp][NB]
-    T *Dm = X + 2 * mp * NB;     // [NB][NB]
-    const int tid = g.tid, nthr = g.size;
+    T *PT = X;                   // [NB][mp] old panel, transposed
+    T *TT = X + NB * mp;         // [NB][mp]
+    T *Dm = X + 2 * NB * mp;     // [NB][NB]
+    const int tid = g.tid, nthr = g.size, lane = g.lane(), warp = g.warp(), nw = g.warps();
+    const int nrb = (mp + 31) / 32;      // 32-row blocks
+    const int ncb = mp / 16 + (mp % 16 ? 1 : 0);
     for (int k0 = 0; k0 < mp; k0 += NB) {
-        for (int e = tid; e < mp * NB; e += nthr) {
-            const int i = e / NB, t = e - i * NB;
-            P[e] = A[sidx(i, k0 + t, mp)];
+        for (int e = tid; e < NB * mp; e += nthr) {
+            const int u = e / mp, i = e - u * mp;
+            PT[e] = A[sidx(i, k0 + u, mp)];
         }
         g.sync();
         // -- pivot block inverse by an unblocked sweep on one warp (result negated at the end)
-        if (tid < 32) {
-            for (int e = tid; e < NB * NB; e += 32) Dm[e] = P[(k0 + e / NB) * NB + (e % NB)];
+        if (warp == 0) {
+            for (int e = lane; e < NB * NB; e += 32) Dm[e] = PT[(e % NB) * mp + k0 + e / NB];
             __syncwarp();
             for (int p = 0; p < NB; ++p) {
                 const T d = T(1) / Dm[p * NB + p];
                 T nv[(NB * NB + 31) / 32];
 #pragma unroll
                 for (int q = 0; q < (NB * NB + 31) / 32; ++q) {
-                    const int e = tid + 32 * q;
+                    const int e = lane + 32 * q;
                     if (e < NB * NB) {
                         const int i = e / NB, j = e % NB;
                         const T aij = Dm[e], aip = Dm[i * NB + p], apj = Dm[p * NB + j];
@@ -349,71 +399,66 @@ __device__ void sweep_inverse(T *A, int mp, T *X, const Group &g) {
                 __syncwarp();
 #pragma unroll
                 for (int q = 0; q < (NB * NB + 31) / 32; ++q) {
-                    const int e = tid + 32 * q;
+                    const int e = lane + 32 * q;
                     if (e < NB * NB) Dm[e] = nv[q];
                 }
                 __syncwarp();
             }
-            for (int e = tid; e < NB * NB; e += 32) Dm[e] = -Dm[e];   // = A_KK^-1
+            for (int e = lane; e < NB * NB; e += 32) Dm[e] = -Dm[e];   // = A_KK^-1 (symmetric)
         }
         g.sync();
-        // -- T = A(:,K) A_KK^-1 for rows outside K
-        for (int e = tid; e < mp * NB; e += nthr) {
-            const int i = e / NB, t = e - i * NB;
-            if (i >= k0 && i < k0 + NB) continue;
+        // -- TT[t][i] = sum_u P(i, u) Dinv(u, t) for rows outside K
+        for (int e = tid; e < NB * mp; e += nthr) {
+            const int t = e / mp, i = e - t * mp;
             T acc = T(0);
+            if (i < k0 || i >= k0 + NB) {
 #pragma unroll
-            for (int u = 0; u < NB; ++u) acc = fma(P[i * NB + u], Dm[u * NB + t], acc);
-            Tm[e] = acc;
+                for (int u = 0; u < NB; ++u) acc = fma(PT[u * mp + i], Dm[u * NB + t], acc);
+            }
+            TT[e] = acc;
         }
         g.sync();
-        // -- rank-NB update of the lower triangle outside K, 4x4 tiles
-        const int nt = mp / 4;
-        const int ntiles = nt * (nt + 1) / 2;
-        const int kb0 = k0 / 4, kb1 = (k0 + NB) / 4;
-        for (int tile = tid; tile < ntiles; tile += nthr) {
-            int ti = (int)((sqrtf(8.0f * (float)tile + 1.0f) - 1.0f) * 0.5f);
-            while (ti * (ti + 1) / 2 > tile) --ti;
-            while ((ti + 1) * (ti + 2) / 2 <= tile) ++ti;
-            const int tj = tile - ti * (ti + 1) / 2;
-            if ((ti >= kb0 && ti < kb1) || (tj >= kb0 && tj < kb1)) continue;
-            T acc[4][4];
+        // -- rank-NB update of the lower triangle outside K: strips (row block R, column block C)
+        const int kc0 = k0 / 16, kc1 = (k0 + NB + 15) / 16;
+        for (int R = 0, strip = 0; R < nrb; ++R) {
+            const int cmax = min(ncb, 2 * R + 2);
+            for (int C = 0; C < cmax; ++C, ++strip) {
+                if (strip % nw != warp) continue;
+                if (NB == 16 && C >= kc0 && C < kc1) continue;    // the pivot columns
+                const int i = 32 * R + lane;
+                const bool rowin = i < mp && (i < k0 || i >= k0 + NB);
+                T acc[16];
 #pragma unroll
-            for (int a = 0; a < 4; ++a)
-#pragma unroll
-                for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
-            const T *Ti = Tm + (4 * ti) * NB;
-            const T *Pj = P + (4 * tj) * NB;
+                for (int c = 0; c < 16; ++c) acc[c] = T(0);
 #pragma unroll 4
-            for (int u = 0; u < NB; ++u) {
-                T tv[4], pv[4];
+                for (int u = 0; u < NB; ++u) {
+                    const T tv = rowin ? TT[u * mp + i] : T(0);
+                    T pr[16];
+                    load16(PT + u * mp + 16 * C, pr);   // broadcast: every lane reads the same words
 #pragma unroll
-                for (int a = 0; a < 4; ++a) { tv[a] = Ti[a * NB + u]; pv[a] = Pj[a * NB + u]; }
+                    for (int c = 0; c < 16; ++c) acc[c] = fma(tv, pr[c], acc[c]);
+                }
+                if (rowin) {
+                    int j = 16 * C;
+                    T *colp = A + col_start(j, mp) - j;
 #pragma unroll
-                for (int a = 0; a < 4; ++a)
-#pragma unroll
-                    for (int b = 0; b < 4; ++b) acc[a][b] = fma(tv[a], pv[b], acc[a][b]);
-            }
-#pragma unroll
-            for (int b = 0; b < 4; ++b) {
-                const int j = 4 * tj + b;
-                T *colj = A + col_start(j, mp) - j;
-#pragma unroll
-                for (int a = 0; a < 4; ++a) {
-                    const int i = 4 * ti + a;
-                    if (i >= j) colj[i] -= acc[a][b];
+                    for (int c = 0; c < 16; ++c) {
+                        if (j < mp && j <= i && (j < k0 || j >= k0 + NB)) colp[i] -= acc[c];
+                        colp += mp - j - 1;
+                        ++j;
+                    }
                 }
             }
         }
         g.sync();
         // -- write back the swept panel
-        for (int e = tid; e < mp * NB; e += nthr) {
-            const int i = e / NB, t = e - i * NB;
+        for (int e = tid; e < NB * mp; e += nthr) {
+            const int t = e / mp, i = e - t * mp;
             const int j = k0 + t;
             if (i >= k0 && i < k0 + NB) {
                 if (i >= j) A[pidx(i, j, mp)] = -Dm[(i - k0) * NB + t];
             } else {
-                A[sidx(i, j, mp)] = Tm[e];
+                A[sidx(i, j, mp)] = TT[e];
             }
         }
         g.sync();
@@ -439,6 +484,8 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
     T *bb = (T *)(smem + L.b), *mut = (T *)(smem + L.mut), *X = (T *)(smem + L.X), *A = (T *)(smem + L.A);
     T *red = (T *)(smem + L.red);
     int *misc = (int *)(smem + L.misc);
+    T *wv = (T *)(smem + L.wv), *fb = (T *)(smem + L.fb);
+    int *bro = (int *)(smem + L.bro), *brow = (int *)(smem + L.brow);
     const T dt = a.dt, kbias = a.beta / a.dt;
     if (tid == 0) misc[1] = 0;   // non-finite flag of this world
 
@@ -657,51 +704,113 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
     }
     g.sync();
 
-    // ---- 7. A <- -A^-1 (blocked sweep)
+    // ---- 7. A <- -A^-1 (blocked sweep); per-body row lists for the matrix-free products
     sweep_inverse<T, NB>(A, mp, X, g);
+    for (int i = tid; i < nb; i += nthr) {
+        int cnt = 0;
+        for (int r = 0; r < m; ++r) cnt += (rbody[2 * r] == i) + (rbody[2 * r + 1] == i);
+        bro[i + 1] = cnt;
+    }
+    g.sync();
+    if (tid == 0) {
+        bro[0] = 0;
+        for (int i = 0; i < nb; ++i) bro[i + 1] += bro[i];
+    }
+    g.sync();
+    for (int i = tid; i < nb; i += nthr) {
+        int e = bro[i];
+        for (int r = 0; r < m; ++r) {
+            if (rbody[2 * r] == i) brow[e++] = 2 * r;
+            if (rbody[2 * r + 1] == i) brow[e++] = 2 * r + 1;
+        }
+    }
 
-    // ---- 8. Proximal-ADMM (Alg. 1)
+    // ---- 8. Proximal-ADMM (Alg. 1).  The linear solve of every iteration is one step of
+    // iterative refinement from the previous x:  x^i = x^{i-1} - A^-1 (b + A x^{i-1}), with A x
+    // evaluated matrix-free from the rows (P J M^-1 J^T P x + (eta + rho) x) and A^-1 the swept
+    // inverse.  At a fixed point A x = -b holds to the accuracy of the matrix-free product, so the
+    // inverse's own rounding (which the nearly singular D~ would amplify) does not move the
+    // solution.
     const T eta = a.eta, rho = a.rho, irho = T(1) / a.rho;
     T acc_a = T(1), c_prev = T(INFINITY);
     T rp = T(INFINITY), rd = T(INFINITY), rc = T(INFINITY);
     int it = 0;
     bool converged = false;
-    for (it = 1; it <= a.iters; ++it) {
-        // s = Gamma(z^), b = v_f + s - eta x - rho y^ - z^
-        for (int u = tid; u < nunits; u += nthr) {
-            if (u < nbil) {
-                bb[u] = vf[u] - eta * x[u] - rho * yh[u] - zh[u];
-            } else {
-                const int r0 = nbil + 3 * (u - nbil);
-                const T s = mut[u - nbil] * sqrt(zh[r0] * zh[r0] + zh[r0 + 1] * zh[r0 + 1]);
-                for (int t = 0; t < 3; ++t)
-                    bb[r0 + t] = vf[r0 + t] + (t == 2 ? s : T(0)) - eta * x[r0 + t] - rho * yh[r0 + t] - zh[r0 + t];
+    // b = v_f + Gamma(z^) - eta x - rho y^ - z^ and w = P x for the first iteration
+    for (int u = tid; u < nunits; u += nthr) {
+        if (u < nbil) {
+            bb[u] = vf[u] - eta * x[u] - rho * yh[u] - zh[u];
+            wv[u] = p[u] * x[u];
+        } else {
+            const int r0 = nbil + 3 * (u - nbil);
+            const T s = mut[u - nbil] * sqrt(zh[r0] * zh[r0] + zh[r0 + 1] * zh[r0 + 1]);
+            for (int t = 0; t < 3; ++t) {
+                bb[r0 + t] = vf[r0 + t] + (t == 2 ? s : T(0)) - eta * x[r0 + t] - rho * yh[r0 + t] - zh[r0 + t];
+                wv[r0 + t] = p[r0 + t] * x[r0 + t];
             }
         }
+    }
+    g.sync();
+    for (it = 1; it <= a.iters; ++it) {
+        // f_b = sum over the rows of body b of J_rb^T (P x)_r
+        for (int t = tid; t < 6 * nb; t += nthr) {
+            const int i = t / 6, k = t - 6 * (t / 6);
+            T f = T(0);
+            for (int e = bro[i]; e < bro[i + 1]; ++e) {
+                const int code = brow[e];
+                f = fma(rJ[6 * code + k], wv[code >> 1], f);    // 12 r + 6 side + k
+            }
+            fb[t] = f;
+        }
         g.sync();
-        // x^i = -(D~ + (eta + rho) I)^-1 b = A b   (A holds -A_orig^-1)
+        // c = b + A x = b + P J M^-1 f + (eta + rho) x
+        for (int r = tid; r < mp; r += nthr) {
+            T cr = T(0);
+            if (r < m) {
+                const T *J = rJ + 12 * r;
+                T acc = T(0);
+                for (int sd = 0; sd < 2; ++sd) {
+                    const int body = rbody[2 * r + sd];
+                    if (body < 0) continue;
+                    const T *f = fb + 6 * body;
+                    T gang[3];
+                    symvec3(bIinv + 6 * body, f + 3, gang);
+                    const T mi = bminv[body];
+                    const T *Js = J + 6 * sd;
+                    acc += mi * (Js[0] * f[0] + Js[1] * f[1] + Js[2] * f[2]) + Js[3] * gang[0] + Js[4] * gang[1] +
+                           Js[5] * gang[2];
+                }
+                cr = bb[r] + p[r] * acc + shift * x[r];
+            }
+            bb[r] = cr;
+        }
+        g.sync();
+        // correction d = A^-1-step: xn = S c with S = -A^-1, so x^i = x^{i-1} + xn
         symv_packed(A, mp, bb, xn, X, g);
         // y^i = Pi_K(x^i - z^/rho), z^i = z^ - rho (x^i - y^i), residual terms
         T lrp = T(0), lrd = T(0), lrc = T(0), lc = T(0);
-        T ynew[kSlots][3], znew[kSlots][3];   // a thread owns units tid + s * group size, s < kSlots
+        T xnew[kSlots][3], ynew[kSlots][3], znew[kSlots][3];   // units tid + s * group size
 #pragma unroll
         for (int sl = 0; sl < kSlots; ++sl) {
             const int u = tid + sl * nthr;
             if (u >= nunits) continue;
             if (u < nbil) {
-                const T xv = xn[u];
+                const T xv = x[u] + xn[u];
                 const T yv = xv - zh[u] * irho;
                 const T zv = zh[u] - rho * (xv - yv);
                 lrp = fmax(lrp, fabs(xv - yv));
                 lrd = fmax(lrd, fabs(eta * (xv - x[u]) + rho * (yv - yh[u])));
                 lc += (zv - zh[u]) * (zv - zh[u]) * irho + rho * (yv - yh[u]) * (yv - yh[u]);
-                ynew[sl][0] = yv; znew[sl][0] = zv;
+                xnew[sl][0] = xv; ynew[sl][0] = yv; znew[sl][0] = zv;
             } else {
                 const int k = u - nbil, r0 = nbil + 3 * k;
                 const T mu = mut[k];
-                T v[3], yv[3];
+                T v[3], yv[3], xv[3];
 #pragma unroll
-                for (int t = 0; t < 3; ++t) v[t] = xn[r0 + t] - zh[r0 + t] * irho;
+                for (int t = 0; t < 3; ++t) {
+                    xv[t] = x[r0 + t] + xn[r0 + t];
+                    v[t] = xv[t] - zh[r0 + t] * irho;
+                }
                 const T tn = sqrt(v[0] * v[0] + v[1] * v[1]);
                 if (tn <= mu * v[2]) {
                     yv[0] = v[0]; yv[1] = v[1]; yv[2] = v[2];
@@ -715,20 +824,20 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
                 T ydz = T(0);
 #pragma unroll
                 for (int t = 0; t < 3; ++t) {
-                    const T xv = xn[r0 + t];
-                    const T zv = zh[r0 + t] - rho * (xv - yv[t]);
-                    lrp = fmax(lrp, fabs(xv - yv[t]));
-                    lrd = fmax(lrd, fabs(eta * (xv - x[r0 + t]) + rho * (yv[t] - yh[r0 + t])));
+                    const T zv = zh[r0 + t] - rho * (xv[t] - yv[t]);
+                    lrp = fmax(lrp, fabs(xv[t] - yv[t]));
+                    lrd = fmax(lrd, fabs(eta * (xv[t] - x[r0 + t]) + rho * (yv[t] - yh[r0 + t])));
                     lc += (zv - zh[r0 + t]) * (zv - zh[r0 + t]) * irho + rho * (yv[t] - yh[r0 + t]) * (yv[t] - yh[r0 + t]);
                     ydz += yv[t] * zv;
-                    ynew[sl][t] = yv[t]; znew[sl][t] = zv;
+                    xnew[sl][t] = xv[t]; ynew[sl][t] = yv[t]; znew[sl][t] = zv;
                 }
                 lrc = fmax(lrc, fabs(ydz));
             }
         }
         group_reduce4(lrp, lrd, lrc, lc, red, it & 1, g);
         rp = lrp; rd = lrd; rc = lrc;
-        // Nesterov with adaptive restart (uniform decision), then commit the iterates
+        // Nesterov with adaptive restart (uniform decision), then commit the iterates and form the
+        // next iteration's b and P x
         T beta_n = T(0);
         bool restart = false;
         if (a.nesterov) {
@@ -757,10 +866,19 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
                 if (!a.nesterov) { yh[r] = yv; zh[r] = zv; }
                 else if (restart) { yh[r] = y[r]; zh[r] = z[r]; }
                 else { yh[r] = yv + beta_n * (yv - y[r]); zh[r] = zv + beta_n * (zv - z[r]); }
-                y[r] = yv; z[r] = zv; x[r] = xn[r];
+                y[r] = yv; z[r] = zv; x[r] = xnew[sl][t];
+                wv[r] = p[r] * xnew[sl][t];
+            }
+            const T s = cnt == 3 ? mut[u - nbil] * sqrt(zh[r0] * zh[r0] + zh[r0 + 1] * zh[r0 + 1]) : T(0);
+#pragma unroll
+            for (int t = 0; t < 3; ++t) {
+                if (t >= cnt) break;
+                const int r = r0 + t;
+                bb[r] = vf[r] + (t == 2 ? s : T(0)) - eta * x[r] - rho * yh[r] - zh[r];
             }
         }
         if (rp < a.tol && rd < a.tol && rc < a.tol) { converged = true; break; }
+        g.sync();
     }
     if (it > a.iters) it = a.iters;
     g.sync();

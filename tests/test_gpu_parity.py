@@ -69,7 +69,10 @@ def check_report(rep, infos):
 
 
 # ----------------------------------------------------------------------------- four-bar, FP64 and FP32
-@pytest.mark.parametrize("precision,bar,tol", [("fp64", 1e-9, 1e-12), ("fp32", 1e-4, 1e-6)])
+# The PADMM stopping test bounds residuals, not the distance to the solution: slow modes of
+# D_eta_rho amplify it (the FP64 oracle stopped at 1e-6 differs from itself at 1e-12 by ~1e-3 on
+# these four-bars, at 1e-8 by ~1e-5).  Parity therefore runs the GPU to 1e-12 (FP64) / 1e-8 (FP32).
+@pytest.mark.parametrize("precision,bar,tol", [("fp64", 1e-9, 1e-12), ("fp32", 1e-4, 1e-8)])
 def test_fourbar_parity_over_steps(K, precision, bar, tol):
     """64 four-bars (1 ms): every step of a 20-step run starts the oracle from the GPU state."""
     ws = wg.make_fourbar(num_worlds=64, seed=0)
@@ -119,8 +122,8 @@ def test_biped_parity_fp32(K, steps_before):
     assert _margin_clear(None, ws, q)
     tau = wg.actuation(ws, 2, steps_before)
     dt = 2e-3
-    qg, ug, rep, _ = gpu_step(K, ws, q, u, tau, dt, 5000, 1e-6)
-    ref, infos = oracle_step(ws, q, u, tau, dt, eps=1e-10)
+    qg, ug, rep, _ = gpu_step(K, ws, q, u, tau, dt, 20000, 1e-8)
+    ref, infos = oracle_step(ws, q, u, tau, dt, eps=1e-11)
     check_report(rep, infos)
     eu, eq = errors(q, qg, ug, ref.q, ref.u, dt)
     assert eu <= 1e-4 and eq <= 1e-4, (eu, eq, rep["iterations"], rep["status"])
@@ -130,7 +133,7 @@ def test_biped_in_the_air_has_no_contacts(K):
     """Edge case: every candidate above the margin -> m = bilateral rows only."""
     ws, q, u = _biped_case(4, seed=3, z_lift=0.2)
     tau = wg.actuation(ws, 3, 0)
-    qg, ug, rep, _ = gpu_step(K, ws, q, u, tau, 2e-3, 5000, 1e-6)
+    qg, ug, rep, _ = gpu_step(K, ws, q, u, tau, 2e-3, 20000, 1e-8)
     ref, infos = oracle_step(ws, q, u, tau, 2e-3)
     check_report(rep, infos)
     assert np.all(rep["num_contacts"] == 0)
@@ -146,8 +149,8 @@ def test_heterogeneous_worlds_one_launch(K):
     q, u = ws.body_q0.copy(), ws.body_u0.copy()
     tau = wg.actuation(ws, 4, 0)
     dt = 2e-3
-    qg, ug, rep, _ = gpu_step(K, ws, q, u, tau, dt, 20000, 1e-6)
-    ref, infos = oracle_step(ws, q, u, tau, dt, eps=1e-10)
+    qg, ug, rep, _ = gpu_step(K, ws, q, u, tau, dt, 20000, 1e-8)
+    ref, infos = oracle_step(ws, q, u, tau, dt, eps=1e-11)
     check_report(rep, infos)
     for w0 in range(0, 12, 3):
         bs = slice(int(ws.world_body_offset[w0]), int(ws.world_body_offset[w0 + 3]))
@@ -172,10 +175,10 @@ def test_cached_warm_start_matches_oracle(K):
     ws, q, u = _biped_case(4, seed=5)
     dt = 2e-3
     model = K.Model(ws, "fp32", K.make_params(rho=0.1, warm_mode=K.WARM_CACHED))
-    qg1, ug1, _, cache1 = gpu_step(K, ws, q, u, wg.actuation(ws, 5, 0), dt, 5000, 1e-7, model=model)
+    qg1, ug1, _, cache1 = gpu_step(K, ws, q, u, wg.actuation(ws, 5, 0), dt, 20000, 1e-8, model=model)
     ref1, _ = oracle_step(ws, q, u, wg.actuation(ws, 5, 0), dt, warm="cached")
     # second step from the GPU state, both warm-started from their own first-step caches
-    qg2, ug2, rep2, _ = gpu_step(K, ws, qg1, ug1, wg.actuation(ws, 5, 1), dt, 5000, 1e-7, model=model,
+    qg2, ug2, rep2, _ = gpu_step(K, ws, qg1, ug1, wg.actuation(ws, 5, 1), dt, 20000, 1e-8, model=model,
                                  cache=cache1)
     ref2, infos2 = oracle_step(ws, qg1, ug1, wg.actuation(ws, 5, 1), dt, warm="cached", cache=ref1.cache)
     check_report(rep2, infos2)
@@ -233,12 +236,12 @@ def test_persistent_plan_matches_single_launch(K):
     mode, buckets = model.plan()
     assert mode == K.LAUNCH_SINGLE and len(buckets) == 4
     assert sorted(b["group_threads"] for b in buckets) == [32, 64, 64, 256]
-    q1, u1, rep1, _ = gpu_step(K, ws, ws.body_q0, ws.body_u0, tau, dt, 20000, 1e-6, model=model)
+    q1, u1, rep1, _ = gpu_step(K, ws, ws.body_q0, ws.body_u0, tau, dt, 20000, 1e-8, model=model)
     model.set_launch_mode(K.LAUNCH_PERSISTENT)
-    q2, u2, rep2, _ = gpu_step(K, ws, ws.body_q0, ws.body_u0, tau, dt, 20000, 1e-6, model=model)
+    q2, u2, rep2, _ = gpu_step(K, ws, ws.body_q0, ws.body_u0, tau, dt, 20000, 1e-8, model=model)
     np.testing.assert_array_equal(rep1["num_rows"], rep2["num_rows"])
     np.testing.assert_allclose(u2, u1, atol=1e-5 * max(1.0, np.abs(u1).max()))
-    ref, infos = oracle_step(ws, ws.body_q0, ws.body_u0, tau, dt, eps=1e-10)
+    ref, infos = oracle_step(ws, ws.body_q0, ws.body_u0, tau, dt, eps=1e-11)
     check_report(rep2, infos)
     eu, eq = errors(ws.body_q0, q2, u2, ref.q, ref.u, dt)
     assert eu <= 1e-4 and eq <= 1e-4
@@ -288,8 +291,8 @@ def test_heightfield_bipeds_fp32(K):
     if not _margin_clear(None, ws, st.q):
         pytest.skip("a candidate sits on the activation threshold")
     tau = wg.actuation(ws, 9, 15)
-    qg, ug, rep, _ = gpu_step(K, ws, st.q, st.u, tau, 2e-3, 20000, 1e-6)
-    ref, infos = oracle_step(ws, st.q, st.u, tau, 2e-3, eps=1e-10)
+    qg, ug, rep, _ = gpu_step(K, ws, st.q, st.u, tau, 2e-3, 20000, 1e-8)
+    ref, infos = oracle_step(ws, st.q, st.u, tau, 2e-3, eps=1e-11)
     check_report(rep, infos)
     eu, eq = errors(st.q, qg, ug, ref.q, ref.u, 2e-3)
     assert eu <= 1e-4 and eq <= 1e-4, (eu, eq)
