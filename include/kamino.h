@@ -237,6 +237,56 @@ kamino_status kamino_graph_create(kamino_state_t state, double dt, int32_t iters
 kamino_status kamino_graph_launch(kamino_graph_t graph, void *stream);
 kamino_status kamino_graph_destroy(kamino_graph_t graph);
 
+/* ---- Learned warm start (one MLP per world type): features of a world (per body the position
+ * relative to the first body, quaternion and twist; the first body's height; the actuation; per
+ * contact candidate the signed distance and terrain normal) -> initial impulses in the impulse-
+ * cache layout.  L = 3 hidden layers of width `hidden`, GELU, BF16 weights and activations, FP32
+ * accumulation on tensor cores (mma.sync m16n8k16), FP32 master weights and Adam.  Features and
+ * targets are normalised per column (kamino_mlp_fit_normalization).  The network only supplies
+ * the starting point of Alg. 1 (KAMINO_WARM_EXTERNAL); the solver's convergence test decides. */
+typedef struct kamino_mlp_s *kamino_mlp_t;
+typedef struct {
+    int32_t num_worlds;        /* worlds the network serves                                   */
+    int32_t d_in, d_hidden, hidden_layers, d_out;
+    int32_t max_batch;         /* largest training / prediction batch                         */
+    int64_t num_params;        /* [W0 (h x d_in), b0, W1, b1, ..., W_L (d_out x h), b_L]      */
+} kamino_mlp_info;
+
+/* `worlds` (host, `count` entries) lists worlds of one type: identical body, joint, candidate and
+ * actuator counts (KAMINO_E_TOPOLOGY otherwise).  Weights: N(0, 2 / fan_in) from `seed`, bias 0. */
+kamino_status kamino_mlp_create(kamino_model_t model, const int32_t *worlds, int32_t count, int32_t hidden,
+                                int32_t max_batch, uint64_t seed, kamino_mlp_t *out);
+kamino_status kamino_mlp_destroy(kamino_mlp_t mlp);
+kamino_status kamino_mlp_get_info(kamino_mlp_t mlp, kamino_mlp_info *out);
+/* Raw features [count][d_in] (FP32, device) of the state's worlds for actuation `tau_dev`. */
+kamino_status kamino_mlp_features(kamino_mlp_t mlp, kamino_state_t state, const void *tau_dev, float *out_dev,
+                                  void *stream);
+/* Converged impulses of the last step (the state's cache) as raw targets [count][d_out]. */
+kamino_status kamino_mlp_targets(kamino_mlp_t mlp, kamino_state_t state, float *out_dev, void *stream);
+/* Column means and standard deviations of `rows` raw feature / target rows (device). */
+kamino_status kamino_mlp_fit_normalization(kamino_mlp_t mlp, const float *x_dev, const float *y_dev, int64_t rows,
+                                           void *stream);
+/* One Adam step on the mean squared error of the normalised targets over the rows `rows_dev`
+ * ([batch] indices into x_dev / y_dev; NULL = the first `batch` rows).  `loss_dev` (nullable)
+ * receives the batch loss before the update. */
+kamino_status kamino_mlp_train_step(kamino_mlp_t mlp, const float *x_dev, const float *y_dev,
+                                    const int32_t *rows_dev, int32_t batch, float lr, float *loss_dev,
+                                    void *stream);
+/* Gradients of that loss with respect to every parameter (FP32 [num_params], device), no update. */
+kamino_status kamino_mlp_gradients(kamino_mlp_t mlp, const float *x_dev, const float *y_dev,
+                                   const int32_t *rows_dev, int32_t batch, float *grad_dev, float *loss_dev,
+                                   void *stream);
+/* Raw impulses [batch][d_out] predicted for raw features [batch][d_in]. */
+kamino_status kamino_mlp_predict(kamino_mlp_t mlp, const float *x_dev, int32_t batch, float *y_dev, void *stream);
+/* Features of the state -> prediction -> the state's KAMINO_BUF_WARM (use with warm_mode 2). */
+kamino_status kamino_mlp_warm_start(kamino_mlp_t mlp, kamino_state_t state, const void *tau_dev, void *stream);
+/* FP32 master parameters and the normalisation [x_mean(d_in), x_inv_std(d_in), y_mean(d_out),
+ * y_inv_std(d_out)] to / from host memory (synchronous). */
+kamino_status kamino_mlp_get_params(kamino_mlp_t mlp, float *host, int64_t count);
+kamino_status kamino_mlp_set_params(kamino_mlp_t mlp, const float *host, int64_t count);
+kamino_status kamino_mlp_get_normalization(kamino_mlp_t mlp, float *host);
+kamino_status kamino_mlp_set_normalization(kamino_mlp_t mlp, const float *host);
+
 /* Message of the calling thread's last failed call ("" if none). */
 const char *kamino_last_error(void);
 

@@ -14,6 +14,7 @@
 
 #include "kamino.h"
 #include "kamino_internal.h"
+#include "kamino_mlp.h"
 
 using namespace kamino;
 
@@ -843,6 +844,386 @@ kamino_status kamino_graph_destroy(kamino_graph_t g) {
     if (g->exec) cudaGraphExecDestroy(g->exec);
     if (g->graph) cudaGraphDestroy(g->graph);
     delete g;
+    return KAMINO_OK;
+}
+
+}  // extern "C"
+
+// ============================================================================ warm-start MLP
+
+namespace {
+
+constexpr int kHiddenLayers = 3;
+
+struct MlpBufs {
+    __nv_bfloat16 *Xb = nullptr, *dY = nullptr;
+    float *Y = nullptr, *dYf = nullptr, *feat = nullptr;
+    float *Z[kHiddenLayers] = {nullptr, nullptr, nullptr};
+    __nv_bfloat16 *H[kHiddenLayers] = {nullptr, nullptr, nullptr};
+    float *dZf[2] = {nullptr, nullptr};
+    __nv_bfloat16 *dZb[2] = {nullptr, nullptr};
+};
+
+uint64_t splitmix64(uint64_t &s) {
+    uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+double normal_draw(uint64_t &s) {   // Box-Muller on two uniform draws in (0, 1)
+    const double u1 = ((splitmix64(s) >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+    const double u2 = ((splitmix64(s) >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+    return std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586 * u2);
+}
+
+}  // namespace
+
+struct kamino_mlp_s {
+    kamino_model_t model = nullptr;
+    int count = 0, din = 0, dout = 0, hidden = 0, nact = 0, max_batch = 0, step = 0;
+    int dims[kHiddenLayers + 2] = {0, 0, 0, 0, 0};
+    long woff[kHiddenLayers + 1] = {0}, boff[kHiddenLayers + 1] = {0};
+    long nparams = 0;
+    int *d_worlds = nullptr;
+    float *P = nullptr, *G = nullptr, *M1 = nullptr, *M2 = nullptr, *norm = nullptr, *loss_tmp = nullptr;
+    __nv_bfloat16 *PB = nullptr;
+    unsigned char *isw = nullptr;
+    MlpBufs b;
+    std::vector<void *> allocs;
+    ~kamino_mlp_s() {
+        for (void *p : allocs) cudaFree(p);
+    }
+    float *xmean() const { return norm; }
+    float *xinv() const { return norm + din; }
+    float *ymean() const { return norm + 2 * din; }
+    float *yinv() const { return norm + 2 * din + dout; }
+};
+
+namespace {
+
+template <typename P>
+cudaError_t mlp_alloc(kamino_mlp_s *n, P **ptr, size_t count) {
+    void *d = nullptr;
+    cudaError_t e = cudaMalloc(&d, std::max<size_t>(count, 1) * sizeof(P));
+    if (e == cudaSuccess) {
+        n->allocs.push_back(d);
+        *ptr = (P *)d;
+    }
+    return e;
+}
+
+// forward pass on n->b.Xb (batch rows), leaves Z, H and Y
+cudaError_t mlp_forward(kamino_mlp_s *n, int batch, cudaStream_t s) {
+    using namespace kamino::mlp;
+    const __nv_bfloat16 *in = n->b.Xb;
+    cudaError_t e = cudaSuccess;
+    for (int l = 0; l <= kHiddenLayers && e == cudaSuccess; ++l) {
+        GemmArgs g{};
+        g.M = batch;
+        g.N = n->dims[l + 1];
+        g.K = n->dims[l];
+        g.A = in; g.sam = n->dims[l]; g.sak = 1;
+        g.B = n->PB + n->woff[l]; g.sbk = 1; g.sbn = n->dims[l];
+        g.bias = n->P + n->boff[l];
+        if (l < kHiddenLayers) {
+            g.epi = EPI_BIAS_GELU;
+            g.Cf = n->b.Z[l]; g.ldcf = n->dims[l + 1];
+            g.Cb = n->b.H[l]; g.ldcb = n->dims[l + 1];
+            in = n->b.H[l];
+        } else {
+            g.epi = EPI_BIAS_F32;
+            g.Cf = n->b.Y; g.ldcf = n->dout;
+        }
+        e = gemm(g, s);
+    }
+    return e;
+}
+
+// gradients into n->G for the batch whose forward pass and dY are in place
+cudaError_t mlp_backward(kamino_mlp_s *n, int batch, cudaStream_t s) {
+    using namespace kamino::mlp;
+    const __nv_bfloat16 *dz = n->b.dY;
+    const float *dzf = n->b.dYf;
+    cudaError_t e = cudaSuccess;
+    int cur = 0;
+    for (int l = kHiddenLayers; l >= 0 && e == cudaSuccess; --l) {
+        const int dout = n->dims[l + 1], din = n->dims[l];
+        const __nv_bfloat16 *hin = l == 0 ? n->b.Xb : n->b.H[l - 1];
+        GemmArgs gw{};   // dW_l = dZ_l^T H_{l-1}
+        gw.M = dout; gw.N = din; gw.K = batch;
+        gw.A = dz; gw.sam = 1; gw.sak = dout;
+        gw.B = hin; gw.sbk = din; gw.sbn = 1;
+        gw.epi = EPI_F32; gw.Cf = n->G + n->woff[l]; gw.ldcf = din;
+        e = gemm(gw, s);
+        if (e == cudaSuccess) e = colsum(dzf, batch, dout, dout, n->G + n->boff[l], s);
+        if (l > 0 && e == cudaSuccess) {   // dZ_{l-1} = (dZ_l W_l) * gelu'(Z_{l-1})
+            GemmArgs gh{};
+            gh.M = batch; gh.N = din; gh.K = dout;
+            gh.A = dz; gh.sam = dout; gh.sak = 1;
+            gh.B = n->PB + n->woff[l]; gh.sbk = din; gh.sbn = 1;
+            gh.epi = EPI_GELU_BWD;
+            gh.Zin = n->b.Z[l - 1]; gh.ldz = din;
+            gh.Cf = n->b.dZf[cur]; gh.ldcf = din;
+            gh.Cb = n->b.dZb[cur]; gh.ldcb = din;
+            e = gemm(gh, s);
+            dz = n->b.dZb[cur];
+            dzf = n->b.dZf[cur];
+            cur ^= 1;
+        }
+    }
+    return e;
+}
+
+kamino_status mlp_loss_and_grads(kamino_mlp_s *n, const float *x, const float *y, const int *rows, int batch,
+                                 float *loss, cudaStream_t s) {
+    using namespace kamino::mlp;
+    if (batch < 1 || batch > n->max_batch) return fail(KAMINO_E_INVALID_ARG, "batch %d outside [1, %d]", batch, n->max_batch);
+    if (!x || !y) return fail(KAMINO_E_INVALID_ARG, "x and y must not be NULL");
+    cudaError_t e = normalize_rows(x, n->din, rows, batch, n->xmean(), n->xinv(), n->b.Xb, s);
+    if (e == cudaSuccess) e = mlp_forward(n, batch, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(n->loss_tmp, 0, sizeof(float), s);
+    if (e == cudaSuccess)
+        e = loss_grad(n->b.Y, y, n->dout, rows, batch, n->ymean(), n->yinv(), n->b.dY, n->b.dYf, n->loss_tmp, s);
+    if (e != cudaSuccess) return cuda_fail(e, "mlp forward");
+    return KAMINO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+kamino_status kamino_mlp_create(kamino_model_t m, const int32_t *worlds, int32_t count, int32_t hidden,
+                                int32_t max_batch, uint64_t seed, kamino_mlp_t *out) {
+    if (!m || !worlds || !out) return fail(KAMINO_E_INVALID_ARG, "model, worlds and out must not be NULL");
+    *out = nullptr;
+    if (count < 1 || hidden < 8 || hidden > 4096 || max_batch < 1)
+        return fail(KAMINO_E_INVALID_ARG, "count >= 1, hidden in [8, 4096] and max_batch >= 1 required");
+    // sizes of the first world define the type; all listed worlds must match
+    std::vector<int4> wa(m->W), wb(m->W);
+    cudaError_t e = cudaMemcpy(wa.data(), m->world_a, m->W * sizeof(int4), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(wb.data(), m->world_b, m->W * sizeof(int4), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "mlp create (read model)");
+    for (int i = 0; i < count; ++i)
+        if (worlds[i] < 0 || worlds[i] >= m->W) return fail(KAMINO_E_INVALID_ARG, "world %d out of range", worlds[i]);
+    const int4 ref = wb[worlds[0]];
+    for (int i = 1; i < count; ++i) {
+        const int4 c = wb[worlds[i]];
+        if (c.x != ref.x || c.y != ref.y || c.z != ref.z || c.w != ref.w)
+            return fail(KAMINO_E_TOPOLOGY, "world %d does not match the sizes of world %d", worlds[i], worlds[0]);
+    }
+    auto *n = new kamino_mlp_s();
+    n->model = m;
+    n->count = count;
+    n->hidden = hidden;
+    n->nact = m->n_act_max;
+    n->din = 13 * ref.x + 1 + n->nact + 4 * ref.z;
+    n->dout = ref.w + 3 * ref.z;
+    n->max_batch = std::max(max_batch, count);
+    n->dims[0] = n->din;
+    for (int l = 1; l <= kHiddenLayers; ++l) n->dims[l] = hidden;
+    n->dims[kHiddenLayers + 1] = n->dout;
+    long off = 0;
+    for (int l = 0; l <= kHiddenLayers; ++l) {
+        n->woff[l] = off;
+        off += (long)n->dims[l + 1] * n->dims[l];
+        n->boff[l] = off;
+        off += n->dims[l + 1];
+    }
+    n->nparams = off;
+    const int B = n->max_batch;
+    e = mlp_alloc(n, &n->d_worlds, count);
+    if (e == cudaSuccess) e = cudaMemcpy(n->d_worlds, worlds, count * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = mlp_alloc(n, &n->P, off);
+    if (e == cudaSuccess) e = mlp_alloc(n, &n->G, off);
+    if (e == cudaSuccess) e = mlp_alloc(n, &n->M1, off);
+    if (e == cudaSuccess) e = mlp_alloc(n, &n->M2, off);
+    if (e == cudaSuccess) e = mlp_alloc(n, &n->PB, off);
+    if (e == cudaSuccess) e = mlp_alloc(n, &n->isw, off);
+    if (e == cudaSuccess) e = mlp_alloc(n, &n->norm, 2 * (size_t)(n->din + n->dout));
+    if (e == cudaSuccess) e = mlp_alloc(n, &n->loss_tmp, 1);
+    if (e == cudaSuccess) e = mlp_alloc(n, &n->b.Xb, (size_t)B * n->din);
+    if (e == cudaSuccess) e = mlp_alloc(n, &n->b.feat, (size_t)count * n->din);
+    if (e == cudaSuccess) e = mlp_alloc(n, &n->b.Y, (size_t)B * n->dout);
+    if (e == cudaSuccess) e = mlp_alloc(n, &n->b.dY, (size_t)B * n->dout);
+    if (e == cudaSuccess) e = mlp_alloc(n, &n->b.dYf, (size_t)B * n->dout);
+    for (int l = 0; l < kHiddenLayers && e == cudaSuccess; ++l) {
+        e = mlp_alloc(n, &n->b.Z[l], (size_t)B * hidden);
+        if (e == cudaSuccess) e = mlp_alloc(n, &n->b.H[l], (size_t)B * hidden);
+    }
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+        e = mlp_alloc(n, &n->b.dZf[k], (size_t)B * hidden);
+        if (e == cudaSuccess) e = mlp_alloc(n, &n->b.dZb[k], (size_t)B * hidden);
+    }
+    if (e != cudaSuccess) { delete n; return cuda_fail(e, "mlp allocation"); }
+    // initial parameters and identity normalisation
+    std::vector<float> p(off, 0.0f);
+    std::vector<unsigned char> isw(off, 0);
+    uint64_t st = seed;
+    for (int l = 0; l <= kHiddenLayers; ++l) {
+        const double sd = std::sqrt(2.0 / n->dims[l]) * (l == kHiddenLayers ? 0.5 : 1.0);
+        for (long i = 0; i < (long)n->dims[l + 1] * n->dims[l]; ++i) {
+            p[n->woff[l] + i] = (float)(sd * normal_draw(st));
+            isw[n->woff[l] + i] = 1;
+        }
+    }
+    std::vector<float> nm(2 * (size_t)(n->din + n->dout), 0.0f);
+    for (int i = 0; i < n->din; ++i) nm[n->din + i] = 1.0f;
+    for (int i = 0; i < n->dout; ++i) nm[2 * n->din + n->dout + i] = 1.0f;
+    e = cudaMemcpy(n->P, p.data(), off * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(n->isw, isw.data(), off, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(n->norm, nm.data(), nm.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(n->M1, 0, off * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemset(n->M2, 0, off * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemset(n->PB, 0, off * sizeof(__nv_bfloat16));
+    if (e == cudaSuccess) e = kamino::mlp::to_bf16(n->P, n->PB, (int)off, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) { delete n; return cuda_fail(e, "mlp initialisation"); }
+    *out = n;
+    return KAMINO_OK;
+}
+
+kamino_status kamino_mlp_destroy(kamino_mlp_t n) {
+    delete n;
+    return KAMINO_OK;
+}
+
+kamino_status kamino_mlp_get_info(kamino_mlp_t n, kamino_mlp_info *out) {
+    if (!n || !out) return fail(KAMINO_E_INVALID_ARG, "mlp and out must not be NULL");
+    out->num_worlds = n->count;
+    out->d_in = n->din;
+    out->d_hidden = n->hidden;
+    out->hidden_layers = kHiddenLayers;
+    out->d_out = n->dout;
+    out->max_batch = n->max_batch;
+    out->num_params = n->nparams;
+    return KAMINO_OK;
+}
+
+kamino_status kamino_mlp_features(kamino_mlp_t n, kamino_state_t s, const void *tau, float *out, void *stream) {
+    if (!n || !s || !out) return fail(KAMINO_E_INVALID_ARG, "mlp, state and out must not be NULL");
+    if (s->model != n->model) return fail(KAMINO_E_INVALID_ARG, "state belongs to another model");
+    cudaError_t e;
+    if (n->model->precision == KAMINO_FP64) {
+        kamino::mlp::FeatureArgs<double> a{};
+        a.m = view<double>(n->model);
+        a.q = (const double *)s->ptr(s->off_q); a.u = (const double *)s->ptr(s->off_u); a.tau = (const double *)tau;
+        a.worlds = n->d_worlds; a.count = n->count; a.din = n->din; a.nact = n->nact; a.out = out;
+        e = kamino::mlp::features<double>(a, (cudaStream_t)stream);
+    } else {
+        kamino::mlp::FeatureArgs<float> a{};
+        a.m = view<float>(n->model);
+        a.q = (const float *)s->ptr(s->off_q); a.u = (const float *)s->ptr(s->off_u); a.tau = (const float *)tau;
+        a.worlds = n->d_worlds; a.count = n->count; a.din = n->din; a.nact = n->nact; a.out = out;
+        e = kamino::mlp::features<float>(a, (cudaStream_t)stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "mlp features");
+    return KAMINO_OK;
+}
+
+kamino_status kamino_mlp_targets(kamino_mlp_t n, kamino_state_t s, float *out, void *stream) {
+    if (!n || !s || !out) return fail(KAMINO_E_INVALID_ARG, "mlp, state and out must not be NULL");
+    if (s->model != n->model) return fail(KAMINO_E_INVALID_ARG, "state belongs to another model");
+    cudaError_t e = n->model->precision == KAMINO_FP64
+        ? kamino::mlp::targets<double>(n->model->world_a, n->d_worlds, n->count, n->dout,
+                                       (const double *)s->ptr(s->off_cache), out, (cudaStream_t)stream)
+        : kamino::mlp::targets<float>(n->model->world_a, n->d_worlds, n->count, n->dout,
+                                      (const float *)s->ptr(s->off_cache), out, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "mlp targets");
+    return KAMINO_OK;
+}
+
+kamino_status kamino_mlp_fit_normalization(kamino_mlp_t n, const float *x, const float *y, int64_t rows, void *stream) {
+    if (!n || !x || !y || rows < 1) return fail(KAMINO_E_INVALID_ARG, "mlp, x, y and rows >= 1 required");
+    cudaError_t e = kamino::mlp::colstats(x, rows, n->din, n->xmean(), n->xinv(), (cudaStream_t)stream);
+    if (e == cudaSuccess) e = kamino::mlp::colstats(y, rows, n->dout, n->ymean(), n->yinv(), (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "mlp normalisation");
+    return KAMINO_OK;
+}
+
+kamino_status kamino_mlp_gradients(kamino_mlp_t n, const float *x, const float *y, const int32_t *rows, int32_t batch,
+                                   float *grad, float *loss, void *stream) {
+    if (!n) return fail(KAMINO_E_INVALID_ARG, "mlp must not be NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    kamino_status st = mlp_loss_and_grads(n, x, y, rows, batch, loss, s);
+    if (st) return st;
+    cudaError_t e = mlp_backward(n, batch, s);
+    if (e == cudaSuccess && grad) e = cudaMemcpyAsync(grad, n->G, n->nparams * sizeof(float), cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess && loss) e = cudaMemcpyAsync(loss, n->loss_tmp, sizeof(float), cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(e, "mlp backward");
+    return KAMINO_OK;
+}
+
+kamino_status kamino_mlp_train_step(kamino_mlp_t n, const float *x, const float *y, const int32_t *rows, int32_t batch,
+                                    float lr, float *loss, void *stream) {
+    if (!n) return fail(KAMINO_E_INVALID_ARG, "mlp must not be NULL");
+    if (!(lr > 0.0f)) return fail(KAMINO_E_INVALID_ARG, "lr must be > 0");
+    kamino_status st = kamino_mlp_gradients(n, x, y, rows, batch, nullptr, loss, stream);
+    if (st) return st;
+    n->step += 1;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.0f - std::pow(b1, (float)n->step), c2 = 1.0f - std::pow(b2, (float)n->step);
+    cudaError_t e = kamino::mlp::adam(n->P, n->G, n->M1, n->M2, (int)n->nparams, lr, b1, b2, 1e-8f, c1, c2, n->PB,
+                                      n->isw, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "mlp adam");
+    return KAMINO_OK;
+}
+
+kamino_status kamino_mlp_predict(kamino_mlp_t n, const float *x, int32_t batch, float *y, void *stream) {
+    if (!n || !x || !y) return fail(KAMINO_E_INVALID_ARG, "mlp, x and y must not be NULL");
+    if (batch < 1 || batch > n->max_batch) return fail(KAMINO_E_INVALID_ARG, "batch %d outside [1, %d]", batch, n->max_batch);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = kamino::mlp::normalize_rows(x, n->din, nullptr, batch, n->xmean(), n->xinv(), n->b.Xb, s);
+    if (e == cudaSuccess) e = mlp_forward(n, batch, s);
+    if (e == cudaSuccess) e = kamino::mlp::denormalize(n->b.Y, batch, n->dout, n->ymean(), n->yinv(), y, s);
+    if (e != cudaSuccess) return cuda_fail(e, "mlp predict");
+    return KAMINO_OK;
+}
+
+kamino_status kamino_mlp_warm_start(kamino_mlp_t n, kamino_state_t s, const void *tau, void *stream) {
+    if (!n || !s) return fail(KAMINO_E_INVALID_ARG, "mlp and state must not be NULL");
+    kamino_status st = kamino_mlp_features(n, s, tau, n->b.feat, stream);
+    if (st) return st;
+    cudaStream_t cs = (cudaStream_t)stream;
+    cudaError_t e = kamino::mlp::normalize_rows(n->b.feat, n->din, nullptr, n->count, n->xmean(), n->xinv(), n->b.Xb, cs);
+    if (e == cudaSuccess) e = mlp_forward(n, n->count, cs);
+    if (e == cudaSuccess)
+        e = n->model->precision == KAMINO_FP64
+            ? kamino::mlp::warm_write<double>(n->model->world_a, n->d_worlds, n->count, n->dout, n->b.Y, n->ymean(),
+                                              n->yinv(), (double *)s->ptr(s->off_warm), cs)
+            : kamino::mlp::warm_write<float>(n->model->world_a, n->d_worlds, n->count, n->dout, n->b.Y, n->ymean(),
+                                             n->yinv(), (float *)s->ptr(s->off_warm), cs);
+    if (e != cudaSuccess) return cuda_fail(e, "mlp warm start");
+    return KAMINO_OK;
+}
+
+kamino_status kamino_mlp_get_params(kamino_mlp_t n, float *host, int64_t count) {
+    if (!n || !host || count != n->nparams) return fail(KAMINO_E_INVALID_ARG, "need num_params floats");
+    cudaError_t e = cudaMemcpy(host, n->P, count * sizeof(float), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "mlp get params");
+    return KAMINO_OK;
+}
+
+kamino_status kamino_mlp_set_params(kamino_mlp_t n, const float *host, int64_t count) {
+    if (!n || !host || count != n->nparams) return fail(KAMINO_E_INVALID_ARG, "need num_params floats");
+    cudaError_t e = cudaMemcpy(n->P, host, count * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = kamino::mlp::to_bf16(n->P, n->PB, (int)count, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "mlp set params");
+    return KAMINO_OK;
+}
+
+kamino_status kamino_mlp_get_normalization(kamino_mlp_t n, float *host) {
+    if (!n || !host) return fail(KAMINO_E_INVALID_ARG, "mlp and host must not be NULL");
+    cudaError_t e = cudaMemcpy(host, n->norm, 2 * (size_t)(n->din + n->dout) * sizeof(float), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "mlp get normalisation");
+    return KAMINO_OK;
+}
+
+kamino_status kamino_mlp_set_normalization(kamino_mlp_t n, const float *host) {
+    if (!n || !host) return fail(KAMINO_E_INVALID_ARG, "mlp and host must not be NULL");
+    cudaError_t e = cudaMemcpy(n->norm, host, 2 * (size_t)(n->din + n->dout) * sizeof(float), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "mlp set normalisation");
     return KAMINO_OK;
 }
 

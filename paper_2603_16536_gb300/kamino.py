@@ -68,6 +68,12 @@ class BucketInfo(C.Structure):
                 ("tuned_ms", C.c_float), ("reserved", C.c_float)]
 
 
+class MlpInfo(C.Structure):
+    _fields_ = [("num_worlds", C.c_int32), ("d_in", C.c_int32), ("d_hidden", C.c_int32),
+                ("hidden_layers", C.c_int32), ("d_out", C.c_int32), ("max_batch", C.c_int32),
+                ("num_params", C.c_int64)]
+
+
 RESIDUAL_DTYPE = np.dtype([("iterations", np.int32), ("status", np.int32), ("num_rows", np.int32),
                            ("num_contacts", np.int32), ("r_primal", np.float32), ("r_dual", np.float32),
                            ("r_compl", np.float32), ("reserved", np.float32)])
@@ -109,6 +115,20 @@ def load_library(path: str | None = None):
         "kamino_graph_create": ([vp, dbl, i32, dbl, vp, vp, C.POINTER(vp)], i32),
         "kamino_graph_launch": ([vp, vp], i32),
         "kamino_graph_destroy": ([vp], i32),
+        "kamino_mlp_create": ([vp, vp, i32, i32, i32, C.c_uint64, C.POINTER(vp)], i32),
+        "kamino_mlp_destroy": ([vp], i32),
+        "kamino_mlp_get_info": ([vp, C.POINTER(MlpInfo)], i32),
+        "kamino_mlp_features": ([vp, vp, vp, vp, vp], i32),
+        "kamino_mlp_targets": ([vp, vp, vp, vp], i32),
+        "kamino_mlp_fit_normalization": ([vp, vp, vp, i64, vp], i32),
+        "kamino_mlp_train_step": ([vp, vp, vp, vp, i32, C.c_float, vp, vp], i32),
+        "kamino_mlp_gradients": ([vp, vp, vp, vp, i32, vp, vp, vp], i32),
+        "kamino_mlp_predict": ([vp, vp, i32, vp, vp], i32),
+        "kamino_mlp_warm_start": ([vp, vp, vp, vp], i32),
+        "kamino_mlp_get_params": ([vp, vp, i64], i32),
+        "kamino_mlp_set_params": ([vp, vp, i64], i32),
+        "kamino_mlp_get_normalization": ([vp, vp], i32),
+        "kamino_mlp_set_normalization": ([vp, vp], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -308,4 +328,101 @@ class StepGraph:
     def __del__(self):
         if getattr(self, "handle", None) and _lib is not None:
             _lib.kamino_graph_destroy(self.handle)
+            self.handle = None
+
+
+def _dptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _sptr(stream):
+    import torch
+    return C.c_void_p((stream or torch.cuda.current_stream()).cuda_stream)
+
+
+class Mlp:
+    """Warm-start network for the worlds `worlds` of one type (kamino_mlp_create)."""
+
+    def __init__(self, model: Model, worlds, hidden: int = 256, max_batch: int = 4096, seed: int = 0):
+        self.model = model
+        w = np.ascontiguousarray(worlds, np.int32)
+        self.worlds = w
+        self.handle = C.c_void_p()
+        _check(load_library().kamino_mlp_create(model.handle, w.ctypes.data_as(C.c_void_p), len(w), int(hidden),
+                                                int(max_batch), C.c_uint64(seed), C.byref(self.handle)))
+        info = MlpInfo()
+        _check(load_library().kamino_mlp_get_info(self.handle, C.byref(info)))
+        self.info = info
+
+    def features(self, state: State, tau=None, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty((self.info.num_worlds, self.info.d_in), dtype=torch.float32, device=state._raw.device)
+        _check(load_library().kamino_mlp_features(self.handle, state.handle, _dptr(tau), _dptr(out), _sptr(stream)))
+        return out
+
+    def targets(self, state: State, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty((self.info.num_worlds, self.info.d_out), dtype=torch.float32, device=state._raw.device)
+        _check(load_library().kamino_mlp_targets(self.handle, state.handle, _dptr(out), _sptr(stream)))
+        return out
+
+    def fit_normalization(self, X, Y, stream=None):
+        _check(load_library().kamino_mlp_fit_normalization(self.handle, _dptr(X), _dptr(Y), X.shape[0], _sptr(stream)))
+
+    def train_step(self, X, Y, rows=None, lr=1e-3, loss=None, stream=None):
+        batch = self.info.num_worlds if rows is None and X is None else (rows.numel() if rows is not None else X.shape[0])
+        _check(load_library().kamino_mlp_train_step(self.handle, _dptr(X), _dptr(Y), _dptr(rows), int(batch),
+                                                    float(lr), _dptr(loss), _sptr(stream)))
+
+    def gradients(self, X, Y, rows=None, stream=None):
+        import torch
+        batch = rows.numel() if rows is not None else X.shape[0]
+        g = torch.empty(self.info.num_params, dtype=torch.float32, device=X.device)
+        loss = torch.zeros(1, dtype=torch.float32, device=X.device)
+        _check(load_library().kamino_mlp_gradients(self.handle, _dptr(X), _dptr(Y), _dptr(rows), int(batch), _dptr(g),
+                                                   _dptr(loss), _sptr(stream)))
+        return g, loss
+
+    def predict(self, X, stream=None):
+        import torch
+        y = torch.empty((X.shape[0], self.info.d_out), dtype=torch.float32, device=X.device)
+        _check(load_library().kamino_mlp_predict(self.handle, _dptr(X), X.shape[0], _dptr(y), _sptr(stream)))
+        return y
+
+    def warm_start(self, state: State, tau=None, stream=None):
+        _check(load_library().kamino_mlp_warm_start(self.handle, state.handle, _dptr(tau), _sptr(stream)))
+
+    def get_params(self) -> np.ndarray:
+        out = np.empty(self.info.num_params, np.float32)
+        _check(load_library().kamino_mlp_get_params(self.handle, out.ctypes.data_as(C.c_void_p), out.size))
+        return out
+
+    def set_params(self, p: np.ndarray):
+        p = np.ascontiguousarray(p, np.float32)
+        _check(load_library().kamino_mlp_set_params(self.handle, p.ctypes.data_as(C.c_void_p), p.size))
+
+    def get_normalization(self) -> np.ndarray:
+        out = np.empty(2 * (self.info.d_in + self.info.d_out), np.float32)
+        _check(load_library().kamino_mlp_get_normalization(self.handle, out.ctypes.data_as(C.c_void_p)))
+        return out
+
+    def set_normalization(self, v: np.ndarray):
+        v = np.ascontiguousarray(v, np.float32)
+        _check(load_library().kamino_mlp_set_normalization(self.handle, v.ctypes.data_as(C.c_void_p)))
+
+    def layer_params(self, p: np.ndarray | None = None):
+        """Split a flat parameter vector into ([W0..WL], [b0..bL]) with W_l of shape (out, in)."""
+        p = self.get_params() if p is None else p
+        dims = [self.info.d_in] + [self.info.d_hidden] * self.info.hidden_layers + [self.info.d_out]
+        Ws, bs, o = [], [], 0
+        for fin, fout in zip(dims[:-1], dims[1:]):
+            Ws.append(p[o:o + fout * fin].reshape(fout, fin)); o += fout * fin
+            bs.append(p[o:o + fout]); o += fout
+        return Ws, bs
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.kamino_mlp_destroy(self.handle)
             self.handle = None
