@@ -18,8 +18,10 @@ def quat_mul(a, b):
 
 
 def quat_to_rot(q):
-    """Rotation matrix R of a unit quaternion (x, y, z, w): v_world = R v_body."""
-    x, y, z, w = q
+    """Rotation matrix R of the rotation the quaternion (x, y, z, w) stands for: v_world = R v_body.
+    The quaternion is normalised first, so a stored state whose norm drifted by rounding maps to
+    the rotation it represents."""
+    x, y, z, w = np.asarray(q, dtype=np.float64) / np.linalg.norm(q)
     return np.array([
         [w * w + x * x - y * y - z * z, 2 * (x * y - w * z), 2 * (x * z + w * y)],
         [2 * (x * y + w * z), w * w - x * x + y * y - z * z, 2 * (y * z - w * x)],

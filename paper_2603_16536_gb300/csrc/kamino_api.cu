@@ -156,16 +156,13 @@ kamino_status build_device(kamino_model_s *m, const kamino_model_desc *d, const 
     if ((s = upload<T>(m, &m->body_inertia, inert.data(), inert.size() * sizeof(T)))) return s;
     if ((s = upload<T>(m, (void **)&m->joint_meta, jm.data(), jm.size() * sizeof(int4)))) return s;
     if ((s = upload<T>(m, (void **)&m->joint_row, jrow.data(), jrow.size() * sizeof(int)))) return s;
-    auto fr = convert<T>(frames.data(), frames.size());
-    if ((s = upload<T>(m, &m->joint_frames, fr.data(), fr.size() * sizeof(T)))) return s;
+    if ((s = upload<T>(m, &m->joint_frames, frames.data(), frames.size() * sizeof(double)))) return s;
     if (m->C > 0) {
         if ((s = upload<T>(m, (void **)&m->contact_body, d->contact_body, (size_t)m->C * sizeof(int)))) return s;
-        auto cp = convert<T>(d->contact_point, 3 * (size_t)m->C);
-        if ((s = upload<T>(m, &m->contact_point, cp.data(), cp.size() * sizeof(T)))) return s;
+        if ((s = upload<T>(m, &m->contact_point, d->contact_point, 3 * (size_t)m->C * sizeof(double)))) return s;
     }
     if (m->terrain_kind == KAMINO_TERRAIN_HEIGHTFIELD) {
-        auto hh = convert<T>(d->hf_heights, (size_t)m->hf_nx * m->hf_ny);
-        if ((s = upload<T>(m, &m->hf_heights, hh.data(), hh.size() * sizeof(T)))) return s;
+        if ((s = upload<T>(m, &m->hf_heights, d->hf_heights, (size_t)m->hf_nx * m->hf_ny * sizeof(double)))) return s;
     }
     auto qq = convert<T>(q0.data(), q0.size());
     if ((s = upload<T>(m, &m->q0, qq.data(), qq.size() * sizeof(T)))) return s;
@@ -188,16 +185,16 @@ ModelView<T> view(const kamino_model_s *m) {
     v.body_inertia = (const T *)m->body_inertia;
     v.joint_meta = m->joint_meta;
     v.joint_row = m->joint_row;
-    v.joint_frames = (const T *)m->joint_frames;
+    v.joint_frames = (const double *)m->joint_frames;
     v.contact_body = m->contact_body;
-    v.contact_point = (const T *)m->contact_point;
+    v.contact_point = (const double *)m->contact_point;
     v.terrain_kind = m->terrain_kind;
     v.hf_nx = m->hf_nx;
     v.hf_ny = m->hf_ny;
-    v.hf_x0 = (T)m->hf_x0;
-    v.hf_y0 = (T)m->hf_y0;
-    v.hf_cell = (T)m->hf_cell;
-    v.hf_heights = (const T *)m->hf_heights;
+    v.hf_x0 = m->hf_x0;
+    v.hf_y0 = m->hf_y0;
+    v.hf_cell = m->hf_cell;
+    v.hf_heights = (const double *)m->hf_heights;
     v.gx = (T)m->g[0];
     v.gy = (T)m->g[1];
     v.gz = (T)m->g[2];

@@ -79,37 +79,37 @@ __device__ __forceinline__ void onb(const T *n, T *t1, T *t2) {
     t2[0] = b; t2[1] = sign + n[1] * n[1] * a; t2[2] = -n[1];
 }
 
-// Signed distance of p to the terrain and the terrain normal there.  Plane: z = 0.  Heightfield:
-// cells split along the (i, j)-(i+1, j+1) diagonal; (x, y) clamped into the grid.
+// Signed distance of p to the terrain and the terrain normal there (FP64).  Plane: z = 0.
+// Heightfield: cells split along the (i, j)-(i+1, j+1) diagonal; (x, y) clamped into the grid.
 template <typename T>
-__device__ __forceinline__ T terrain(const ModelView<T> &m, const T *p, T *n) {
+__device__ __forceinline__ double terrain(const ModelView<T> &m, const double *p, double *n) {
     if (m.terrain_kind == KAMINO_TERRAIN_PLANE) {
-        n[0] = T(0); n[1] = T(0); n[2] = T(1);
+        n[0] = 0.0; n[1] = 0.0; n[2] = 1.0;
         return p[2];
     }
-    const T h = m.hf_cell;
-    T gx = (p[0] - m.hf_x0) / h, gy = (p[1] - m.hf_y0) / h;
-    gx = fmin(fmax(gx, T(0)), T(m.hf_nx - 1));
-    gy = fmin(fmax(gy, T(0)), T(m.hf_ny - 1));
-    int i = min((int)floor(gx), m.hf_nx - 2);
-    int j = min((int)floor(gy), m.hf_ny - 2);
-    const T fx = gx - T(i), fy = gy - T(j);
-    const T *H = m.hf_heights;
-    const T h00 = H[j * m.hf_nx + i], h11 = H[(j + 1) * m.hf_nx + i + 1];
-    T e1[3], e2[3];
+    const double h = m.hf_cell;
+    double gx = (p[0] - m.hf_x0) / h, gy = (p[1] - m.hf_y0) / h;
+    gx = fmin(fmax(gx, 0.0), (double)(m.hf_nx - 1));
+    gy = fmin(fmax(gy, 0.0), (double)(m.hf_ny - 1));
+    const int i = min((int)floor(gx), m.hf_nx - 2);
+    const int j = min((int)floor(gy), m.hf_ny - 2);
+    const double fx = gx - i, fy = gy - j;
+    const double *H = m.hf_heights;
+    const double h00 = H[j * m.hf_nx + i], h11 = H[(j + 1) * m.hf_nx + i + 1];
+    double e1[3], e2[3];
     if (fx >= fy) {   // vertices (i,j), (i+1,j), (i+1,j+1)
-        const T h10 = H[j * m.hf_nx + i + 1];
-        e1[0] = h; e1[1] = T(0); e1[2] = h10 - h00;
+        const double h10 = H[j * m.hf_nx + i + 1];
+        e1[0] = h; e1[1] = 0.0; e1[2] = h10 - h00;
         e2[0] = h; e2[1] = h; e2[2] = h11 - h00;
     } else {          // vertices (i,j), (i+1,j+1), (i,j+1)
-        const T h01 = H[(j + 1) * m.hf_nx + i];
+        const double h01 = H[(j + 1) * m.hf_nx + i];
         e1[0] = h; e1[1] = h; e1[2] = h11 - h00;
-        e2[0] = T(0); e2[1] = h; e2[2] = h01 - h00;
+        e2[0] = 0.0; e2[1] = h; e2[2] = h01 - h00;
     }
     cross3(e1, e2, n);
-    const T inv = rsq(dot3(n, n));
+    const double inv = 1.0 / sqrt(dot3(n, n));
     n[0] *= inv; n[1] *= inv; n[2] *= inv;
-    const T q[3] = {gx * h - T(i) * h, gy * h - T(j) * h, p[2] - h00};
+    const double q[3] = {(gx - i) * h, (gy - j) * h, p[2] - h00};
     return dot3(q, n);
 }
 

@@ -29,12 +29,14 @@ struct ModelView {
     const T *body_inertia;     // [B*3]
     const int4 *joint_meta;    // (type, parent, child, actuator)
     const int *joint_row;      // first row of the joint inside its world
-    const T *joint_frames;     // [J*14]: parent pos3 quat4, child pos3 quat4
-    const int *contact_body;   // [C]
-    const T *contact_point;    // [C*3]
+    // position-level data stays FP64 whatever T is: joint errors and contact distances are
+    // multiplied by beta / dt in the bias, which would amplify FP32 rounding of anchors by 100-200
+    const double *joint_frames;   // [J*14]: parent pos3 quat4, child pos3 quat4
+    const int *contact_body;      // [C]
+    const double *contact_point;  // [C*3]
     int terrain_kind, hf_nx, hf_ny;
-    T hf_x0, hf_y0, hf_cell;
-    const T *hf_heights;       // [ny*nx]
+    double hf_x0, hf_y0, hf_cell;
+    const double *hf_heights;     // [ny*nx]
     T gx, gy, gz;
 };
 
@@ -65,7 +67,7 @@ struct PersistentArgs {
 
 // Byte offsets of the per-world shared-memory working set.
 struct Layout {
-    size_t bq, bu, bR, bI, bIinv, bminv, bufree, jwr, cid, cslot, rbody, rJ, rvs;
+    size_t bq, bu, bR, bRd, bI, bIinv, bminv, bufree, jwr, cid, cslot, rbody, rJ, rvs;
     size_t vf, p, x, xn, y, z, yh, zh, b, mut, wv, fb, bro, brow, X, A, red, misc, total;
 };
 
@@ -80,6 +82,7 @@ __host__ __device__ inline Layout make_layout(int nb, int nj, int nc, int mp, in
     take(L.bq, nb * 7 * s);
     take(L.bu, nb * 6 * s);
     take(L.bR, nb * 9 * s);
+    take(L.bRd, nb * 9 * sizeof(double));
     take(L.bI, nb * 3 * s);
     take(L.bIinv, nb * 6 * s);
     take(L.bminv, nb * s);

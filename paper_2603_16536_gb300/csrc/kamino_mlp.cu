@@ -233,15 +233,15 @@ __global__ void features_kernel(const FeatureArgs<T> a) {
         if (a.m.terrain_kind != KAMINO_TERRAIN_NONE) {
             const int body = a.m.contact_body[c0 + c];
             const T *qb = a.q + 7 * (long)(b0 + body);
-            T R[9], p[3], n[3];
-            T qq[4] = {qb[3], qb[4], qb[5], qb[6]};
-            const T inv = dev::rsq(qq[0] * qq[0] + qq[1] * qq[1] + qq[2] * qq[2] + qq[3] * qq[3]);
+            double R[9], p[3], n[3];
+            double qq[4] = {(double)qb[3], (double)qb[4], (double)qb[5], (double)qb[6]};
+            const double inv = 1.0 / sqrt(qq[0] * qq[0] + qq[1] * qq[1] + qq[2] * qq[2] + qq[3] * qq[3]);
             for (int t = 0; t < 4; ++t) qq[t] *= inv;
             dev::quat_rot(qq, R);
-            const T *cp = a.m.contact_point + 3 * (long)(c0 + c);
+            const double *cp = a.m.contact_point + 3 * (long)(c0 + c);
             dev::matvec3(R, cp, p);
-            for (int t = 0; t < 3; ++t) p[t] += qb[t];
-            const T phi = dev::terrain(a.m, p, n);
+            for (int t = 0; t < 3; ++t) p[t] += (double)qb[t];
+            const double phi = dev::terrain(a.m, p, n);
             v = comp == 0 ? (float)phi : (float)n[comp - 1];
         }
     }

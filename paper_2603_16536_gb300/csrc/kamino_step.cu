@@ -55,28 +55,30 @@ __device__ __forceinline__ int pidx(int i, int j, int mp) {  // requires i >= j
 __device__ __forceinline__ int sidx(int i, int j, int mp) { return i >= j ? pidx(i, j, mp) : pidx(j, i, mp); }
 
 template <typename T>
-__device__ __forceinline__ void put_row(int *rbody, T *rJ, T *rvs, int row, int ba, int bb, const T *Ja, const T *Jb,
-                                        T vstar) {
+__device__ __forceinline__ void put_row(int *rbody, T *rJ, T *rvs, int row, int ba, int bb, const double *Ja,
+                                        const double *Jb, double vstar) {
     rbody[2 * row] = ba;
     rbody[2 * row + 1] = bb;
     T *J = rJ + 12 * row;
-    for (int k = 0; k < 6; ++k) { J[k] = Ja[k]; J[6 + k] = Jb[k]; }
-    rvs[row] = vstar;
+    for (int k = 0; k < 6; ++k) { J[k] = T(Ja[k]); J[6 + k] = T(Jb[k]); }
+    rvs[row] = T(vstar);
 }
 
 // Joint rows of one joint (Sec. 3): positional rows along world axes, angular rows along the
-// parent frame's axes; returns the actuation wrench (J_d^T value) for parent and child.
+// parent frame's axes; returns the actuation wrench (J_d^T value) for parent and child.  All
+// position-level quantities (anchors, frame axes, errors f) are formed in FP64 from the stored
+// pose, then J and the bias are rounded to T.
 template <typename T>
-__device__ void joint_rows(int type, int par, int ch, const T *fr, const T *bq, const T *bR, int row0, T kbias,
-                           int *rbody, T *rJ, T *rvs, bool actuated, T value, T *wr) {
-    T rA[3] = {T(0), T(0), T(0)}, RA[9] = {T(1), T(0), T(0), T(0), T(1), T(0), T(0), T(0), T(1)};
+__device__ void joint_rows(int type, int par, int ch, const double *fr, const T *bq, const double *bRd, int row0,
+                           double kbias, int *rbody, T *rJ, T *rvs, bool actuated, T value, T *wr) {
+    double rA[3] = {0.0, 0.0, 0.0}, RA[9] = {1.0, 0.0, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0, 1.0};
     if (par >= 0) {
-        for (int k = 0; k < 3; ++k) rA[k] = bq[7 * par + k];
-        for (int k = 0; k < 9; ++k) RA[k] = bR[9 * par + k];
+        for (int k = 0; k < 3; ++k) rA[k] = (double)bq[7 * par + k];
+        for (int k = 0; k < 9; ++k) RA[k] = bRd[9 * par + k];
     }
-    const T *rB = bq + 7 * ch;
-    const T *RB = bR + 9 * ch;
-    T cA[3], cB[3], pA[3], pB[3], QA[9], QB[9], FA[9], FB[9];
+    const double rB[3] = {(double)bq[7 * ch], (double)bq[7 * ch + 1], (double)bq[7 * ch + 2]};
+    const double *RB = bRd + 9 * ch;
+    double cA[3], cB[3], pA[3], pB[3], QA[9], QB[9], FA[9], FB[9];
     matvec3(RA, fr, cA);
     matvec3(RB, fr + 7, cB);
     for (int k = 0; k < 3; ++k) { pA[k] = rA[k] + cA[k]; pB[k] = rB[k] + cB[k]; }
@@ -84,17 +86,17 @@ __device__ void joint_rows(int type, int par, int ch, const T *fr, const T *bq, 
     quat_rot(fr + 10, QB);
     matmul3(RA, QA, FA);
     matmul3(RB, QB, FB);
-    T a[3][3], b[3][3];   // a[k] = k-th axis of the parent-side frame (column k)
+    double a[3][3], b[3][3];   // a[k] = k-th axis of the parent-side frame (column k)
     for (int k = 0; k < 3; ++k)
         for (int r = 0; r < 3; ++r) { a[k][r] = FA[3 * r + k]; b[k][r] = FB[3 * r + k]; }
-    T dp[3] = {pB[0] - pA[0], pB[1] - pA[1], pB[2] - pA[2]};
-    T Ja[6], Jb[6], t[3];
+    const double dp[3] = {pB[0] - pA[0], pB[1] - pA[1], pB[2] - pA[2]};
+    double Ja[6], Jb[6], t[3];
     int row = row0;
     const bool positional = (type == KAMINO_JOINT_REVOLUTE || type == KAMINO_JOINT_UNIVERSAL ||
                              type == KAMINO_JOINT_SPHERICAL || type == KAMINO_JOINT_FIXED);
     if (positional) {
         for (int k = 0; k < 3; ++k) {
-            T e[3] = {T(k == 0), T(k == 1), T(k == 2)};
+            const double e[3] = {double(k == 0), double(k == 1), double(k == 2)};
             cross3(cA, e, t);
             Ja[0] = -e[0]; Ja[1] = -e[1]; Ja[2] = -e[2]; Ja[3] = -t[0]; Ja[4] = -t[1]; Ja[5] = -t[2];
             cross3(cB, e, t);
@@ -103,14 +105,14 @@ __device__ void joint_rows(int type, int par, int ch, const T *fr, const T *bq, 
         }
     }
     if (type == KAMINO_JOINT_REVOLUTE) {
-        T err[3];
+        double err[3];
         cross3(a[2], b[2], err);
         for (int k = 0; k < 2; ++k) {
-            for (int r = 0; r < 3; ++r) { Ja[r] = T(0); Jb[r] = T(0); Ja[3 + r] = -a[k][r]; Jb[3 + r] = a[k][r]; }
+            for (int r = 0; r < 3; ++r) { Ja[r] = 0.0; Jb[r] = 0.0; Ja[3 + r] = -a[k][r]; Jb[3 + r] = a[k][r]; }
             put_row(rbody, rJ, rvs, row++, par, ch, Ja, Jb, kbias * dot3(a[k], err));
         }
     } else if (type == KAMINO_JOINT_PRISMATIC) {
-        T lever[3] = {pB[0] - rA[0], pB[1] - rA[1], pB[2] - rA[2]};
+        const double lever[3] = {pB[0] - rA[0], pB[1] - rA[1], pB[2] - rA[2]};
         for (int k = 0; k < 2; ++k) {
             cross3(lever, a[k], t);
             Ja[0] = -a[k][0]; Ja[1] = -a[k][1]; Ja[2] = -a[k][2]; Ja[3] = -t[0]; Ja[4] = -t[1]; Ja[5] = -t[2];
@@ -120,32 +122,33 @@ __device__ void joint_rows(int type, int par, int ch, const T *fr, const T *bq, 
         }
     }
     if (type == KAMINO_JOINT_PRISMATIC || type == KAMINO_JOINT_FIXED) {
-        T err[3] = {T(0), T(0), T(0)};
+        double err[3] = {0.0, 0.0, 0.0};
         for (int i = 0; i < 3; ++i) {
             cross3(a[i], b[i], t);
-            err[0] += T(0.5) * t[0]; err[1] += T(0.5) * t[1]; err[2] += T(0.5) * t[2];
+            err[0] += 0.5 * t[0]; err[1] += 0.5 * t[1]; err[2] += 0.5 * t[2];
         }
         for (int k = 0; k < 3; ++k) {
-            for (int r = 0; r < 3; ++r) { Ja[r] = T(0); Jb[r] = T(0); Ja[3 + r] = -a[k][r]; Jb[3 + r] = a[k][r]; }
+            for (int r = 0; r < 3; ++r) { Ja[r] = 0.0; Jb[r] = 0.0; Ja[3 + r] = -a[k][r]; Jb[3 + r] = a[k][r]; }
             put_row(rbody, rJ, rvs, row++, par, ch, Ja, Jb, kbias * dot3(a[k], err));
         }
     }
     if (type == KAMINO_JOINT_UNIVERSAL) {
-        T n[3];
+        double n[3];
         cross3(a[0], b[1], n);
-        for (int r = 0; r < 3; ++r) { Ja[r] = T(0); Jb[r] = T(0); Ja[3 + r] = n[r]; Jb[3 + r] = -n[r]; }
+        for (int r = 0; r < 3; ++r) { Ja[r] = 0.0; Jb[r] = 0.0; Ja[3 + r] = n[r]; Jb[3 + r] = -n[r]; }
         put_row(rbody, rJ, rvs, row++, par, ch, Ja, Jb, kbias * dot3(a[0], b[1]));
     }
     for (int k = 0; k < 12; ++k) wr[k] = T(0);
     if (actuated) {
+        const double v = (double)value;
         if (type == KAMINO_JOINT_REVOLUTE) {
-            for (int r = 0; r < 3; ++r) { wr[3 + r] = -value * a[2][r]; wr[9 + r] = value * a[2][r]; }
+            for (int r = 0; r < 3; ++r) { wr[3 + r] = T(-v * a[2][r]); wr[9 + r] = T(v * a[2][r]); }
         } else if (type == KAMINO_JOINT_PRISMATIC) {
-            T lever[3] = {pB[0] - rA[0], pB[1] - rA[1], pB[2] - rA[2]};
+            const double lever[3] = {pB[0] - rA[0], pB[1] - rA[1], pB[2] - rA[2]};
             cross3(lever, a[2], t);
-            for (int r = 0; r < 3; ++r) { wr[r] = -value * a[2][r]; wr[3 + r] = -value * t[r]; }
+            for (int r = 0; r < 3; ++r) { wr[r] = T(-v * a[2][r]); wr[3 + r] = T(-v * t[r]); }
             cross3(cB, a[2], t);
-            for (int r = 0; r < 3; ++r) { wr[6 + r] = value * a[2][r]; wr[9 + r] = value * t[r]; }
+            for (int r = 0; r < 3; ++r) { wr[6 + r] = T(v * a[2][r]); wr[9 + r] = T(v * t[r]); }
         }
     }
 }
@@ -374,6 +377,7 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
     const int nb = wb.x, nj = wb.y, nc = wb.z, nbil = wb.w;
     const Layout L = make_layout<T>(a.nb_max, a.nj_max, a.nc_max, a.mp_max, NB);
     T *bq = (T *)(smem + L.bq), *bu = (T *)(smem + L.bu), *bR = (T *)(smem + L.bR), *bI = (T *)(smem + L.bI);
+    double *bRd = (double *)(smem + L.bRd);
     T *bIinv = (T *)(smem + L.bIinv), *bminv = (T *)(smem + L.bminv), *bufree = (T *)(smem + L.bufree);
     T *jwr = (T *)(smem + L.jwr);
     int *cid = (int *)(smem + L.cid), *cslot = (int *)(smem + L.cslot), *rbody = (int *)(smem + L.rbody);
@@ -386,21 +390,23 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
     T *wv = (T *)(smem + L.wv), *fb = (T *)(smem + L.fb);
     int *bro = (int *)(smem + L.bro), *brow = (int *)(smem + L.brow);
     const T dt = a.dt, kbias = a.beta / a.dt;
+    const double dtd = (double)a.dt, kbiasd = (double)a.beta / (double)a.dt;
     if (tid == 0) misc[1] = 0;   // non-finite flag of this world
 
     // ---- 1. body kinematics
     for (int i = tid; i < nb; i += nthr) {
         const T *gq = a.body_q + 7 * (size_t)(b0 + i);
         const T *gu = a.body_u + 6 * (size_t)(b0 + i);
-        T q[7];
-        for (int k = 0; k < 7; ++k) q[k] = gq[k];
-        const T qn = rsq(q[3] * q[3] + q[4] * q[4] + q[5] * q[5] + q[6] * q[6]);
-        for (int k = 3; k < 7; ++k) q[k] *= qn;
-        for (int k = 0; k < 7; ++k) bq[7 * i + k] = q[k];
+        double qd[4] = {(double)gq[3], (double)gq[4], (double)gq[5], (double)gq[6]};
+        const double qn = 1.0 / sqrt(qd[0] * qd[0] + qd[1] * qd[1] + qd[2] * qd[2] + qd[3] * qd[3]);
+        for (int k = 0; k < 4; ++k) qd[k] *= qn;
+        for (int k = 0; k < 3; ++k) bq[7 * i + k] = gq[k];
+        for (int k = 0; k < 4; ++k) bq[7 * i + 3 + k] = T(qd[k]);
         for (int k = 0; k < 6; ++k) bu[6 * i + k] = gu[k];
+        double Rd[9];
+        quat_rot(qd, Rd);
         T R[9];
-        quat_rot(q + 3, R);
-        for (int k = 0; k < 9; ++k) bR[9 * i + k] = R[k];
+        for (int k = 0; k < 9; ++k) { bRd[9 * i + k] = Rd[k]; R[k] = T(Rd[k]); bR[9 * i + k] = R[k]; }
         const T m = M.body_mass[b0 + i];
         T inv[3];
         for (int k = 0; k < 3; ++k) {
@@ -424,7 +430,7 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
         const int4 meta = M.joint_meta[j0 + j];
         const bool act = meta.w >= 0 && a.tau != nullptr;
         const T val = act ? a.tau[(size_t)w * M.n_act_max + meta.w] : T(0);
-        joint_rows(meta.x, meta.y, meta.z, M.joint_frames + 14 * (size_t)(j0 + j), bq, bR, M.joint_row[j0 + j], kbias,
+        joint_rows(meta.x, meta.y, meta.z, M.joint_frames + 14 * (size_t)(j0 + j), bq, bRd, M.joint_row[j0 + j], kbiasd,
                    rbody, rJ, rvs, act, val, jwr + 12 * j);
     }
     if (warp == nwarps - 1) {
@@ -432,31 +438,31 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
         for (int cb = 0; cb < nc; cb += 32) {
             const int c = cb + lane;
             bool active = false;
-            T pw[3], n[3], phi = T(0), rb[3];
+            double pw[3], n[3], phi = 0.0, rb[3];
             int body = 0;
             if (c < nc && M.terrain_kind != KAMINO_TERRAIN_NONE) {
                 body = M.contact_body[c0 + c];
-                const T *cp = M.contact_point + 3 * (size_t)(c0 + c);
-                T lc[3] = {cp[0], cp[1], cp[2]}, wc[3];
-                matvec3(bR + 9 * body, lc, wc);
-                for (int k = 0; k < 3; ++k) { rb[k] = bq[7 * body + k]; pw[k] = rb[k] + wc[k]; }
+                const double *cp = M.contact_point + 3 * (size_t)(c0 + c);
+                double wc[3];
+                matvec3(bRd + 9 * body, cp, wc);
+                for (int k = 0; k < 3; ++k) { rb[k] = (double)bq[7 * body + k]; pw[k] = rb[k] + wc[k]; }
                 phi = terrain(M, pw, n);
-                active = phi < a.margin;
+                active = phi < (double)a.margin;
             }
             const unsigned mask = __ballot_sync(0xffffffffu, active);
             const int rank = count + __popc(mask & ((1u << lane) - 1u));
             if (c < nc) cslot[c] = active ? rank : -1;
             if (active) {
                 cid[rank] = c;
-                T t1[3], t2[3], lev[3], Ja[6] = {T(0), T(0), T(0), T(0), T(0), T(0)}, Jb[6], cr[3];
+                double t1[3], t2[3], lev[3], Ja[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0}, Jb[6], cr[3];
                 onb(n, t1, t2);
                 for (int k = 0; k < 3; ++k) lev[k] = pw[k] - rb[k];
-                const T *dirs[3] = {t1, t2, n};
+                const double *dirs[3] = {t1, t2, n};
                 const int row0 = nbil + 3 * rank;
                 for (int d = 0; d < 3; ++d) {
                     cross3(lev, dirs[d], cr);
                     for (int k = 0; k < 3; ++k) { Jb[k] = dirs[d][k]; Jb[3 + k] = cr[k]; }
-                    const T vs = d < 2 ? T(0) : (phi > T(0) ? phi / dt : kbias * phi);
+                    const double vs = d < 2 ? 0.0 : (phi > 0.0 ? phi / dtd : kbiasd * phi);
                     put_row(rbody, rJ, rvs, row0 + d, -1, body, Ja, Jb, vs);
                 }
             }
@@ -651,7 +657,7 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
     }
     g.sync();
     for (it = 1; it <= a.iters; ++it) {
-        // f_b = sum over the rows of body b of J_rb^T (P x)_r
+        // [8a] f_b = sum over the rows of body b of J_rb^T (P x)_r
         for (int t = tid; t < 6 * nb; t += nthr) {
             const int i = t / 6, k = t - 6 * (t / 6);
             T f = T(0);
@@ -662,7 +668,7 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
             fb[t] = f;
         }
         g.sync();
-        // c = b + A x = b + P J M^-1 f + (eta + rho) x
+        // [8b] c = b + A x = b + P J M^-1 f + (eta + rho) x
         for (int r = tid; r < mp; r += nthr) {
             T cr = T(0);
             if (r < m) {
@@ -684,9 +690,9 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
             bb[r] = cr;
         }
         g.sync();
-        // correction d = A^-1-step: xn = S c with S = -A^-1, so x^i = x^{i-1} + xn
+        // [8c] correction: xn = S c with S = -A^-1, so x^i = x^{i-1} + xn
         symv_packed(A, mp, bb, xn, X, g);
-        // y^i = Pi_K(x^i - z^/rho), z^i = z^ - rho (x^i - y^i), residual terms
+        // [8d] y^i = Pi_K(x^i - z^/rho), z^i = z^ - rho (x^i - y^i), residual terms
         T lrp = T(0), lrd = T(0), lrc = T(0), lc = T(0);
         T xnew[kSlots][3], ynew[kSlots][3], znew[kSlots][3];   // units tid + s * group size
 #pragma unroll

@@ -50,6 +50,11 @@ def gpu_step(K, ws, q, u, tau, dt, iters, tol, precision="fp32", rho=0.1, warm=0
             st.cache.double().cpu().numpy())
 
 
+def rnd(x, precision="fp32"):
+    """The state exactly as the GPU stores it, so that both sides start from identical inputs."""
+    return np.asarray(x, np.float32).astype(np.float64) if precision == "fp32" else np.asarray(x, np.float64)
+
+
 def errors(q0, q_gpu, u_gpu, q_ref, u_ref, dt):
     eu = np.abs(u_gpu - u_ref).max() / max(np.abs(u_ref).max(), G * dt)
     dq_ref = q_ref - q0
@@ -77,7 +82,7 @@ def test_fourbar_parity_over_steps(K, precision, bar, tol):
     """64 four-bars (1 ms): every step of a 20-step run starts the oracle from the GPU state."""
     ws = wg.make_fourbar(num_worlds=64, seed=0)
     dt = 1e-3
-    q, u = ws.body_q0.copy(), ws.body_u0.copy()
+    q, u = rnd(ws.body_q0, precision), rnd(ws.body_u0, precision)
     model = K.Model(ws, precision, K.make_params(rho=0.1))
     worst = (0.0, 0.0)
     for k in range(20):
@@ -98,7 +103,7 @@ def _biped_case(n, seed, steps_before=0, z_lift=0.0):
     params = T.SolverParams(rho=0.1, eps=1e-9, n_max=20000)
     for k in range(steps_before):
         st, _ = T.step(ws, st, wg.actuation(ws, seed, k), 2e-3, params)
-    return ws, st.q, st.u
+    return ws, rnd(st.q), rnd(st.u)
 
 
 def _margin_clear(infos_ws, ws, q, margin=0.005, gap=1e-5):
@@ -146,7 +151,7 @@ def test_heterogeneous_worlds_one_launch(K):
     sets = [wg.make_fourbar(3, seed=4), wg.make_stewart(3, seed=4), wg.make_excavator(3, seed=4),
             wg.make_biped(3, seed=4)]
     ws = wg.concat(sets)
-    q, u = ws.body_q0.copy(), ws.body_u0.copy()
+    q, u = rnd(ws.body_q0), rnd(ws.body_u0)
     tau = wg.actuation(ws, 4, 0)
     dt = 2e-3
     qg, ug, rep, _ = gpu_step(K, ws, q, u, tau, dt, 20000, 1e-8)
@@ -199,6 +204,8 @@ def test_full_size_bipeds_sampled_parity(K):
     """4096 bipeds, the benchmark's launch (FP32, tol 1e-5): sampled worlds against the oracle run
     to the same tolerance, plus whole-batch properties (finite, reports consistent)."""
     ws = wg.make_biped(num_worlds=4096, seed=0)
+    ws.body_q0 = rnd(ws.body_q0)
+    ws.body_u0 = rnd(ws.body_u0)
     dt = 2e-3
     tau = wg.actuation(ws, 0, 0)
     qg, ug, rep, _ = gpu_step(K, ws, ws.body_q0, ws.body_u0, tau, dt, 200, 1e-5)
@@ -208,7 +215,6 @@ def test_full_size_bipeds_sampled_parity(K):
     conv = rep["status"] == 0
     assert np.all(rep["iterations"][~conv] == 200)
     sample = [0, 1, 777, 2048, 4095]
-    sub = wg.make_biped(num_worlds=4096, seed=0)
     for w in sample:
         bs = ws.bodies(w)
         ref_st, infos = T.step(ws, T.initial_state(ws), tau, dt, T.SolverParams(rho=0.1, eps=1e-10, n_max=20000),
@@ -232,18 +238,19 @@ def test_persistent_plan_matches_single_launch(K):
     ws = _hetero()
     tau = wg.actuation(ws, 7, 0)
     dt = 2e-3
+    q0, u0 = rnd(ws.body_q0), rnd(ws.body_u0)
     model = K.Model(ws, "fp32", K.make_params(rho=0.1))
     mode, buckets = model.plan()
     assert mode == K.LAUNCH_SINGLE and len(buckets) == 4
     assert sorted(b["group_threads"] for b in buckets) == [32, 64, 64, 256]
-    q1, u1, rep1, _ = gpu_step(K, ws, ws.body_q0, ws.body_u0, tau, dt, 20000, 1e-8, model=model)
+    q1, u1, rep1, _ = gpu_step(K, ws, q0, u0, tau, dt, 20000, 1e-8, model=model)
     model.set_launch_mode(K.LAUNCH_PERSISTENT)
-    q2, u2, rep2, _ = gpu_step(K, ws, ws.body_q0, ws.body_u0, tau, dt, 20000, 1e-8, model=model)
+    q2, u2, rep2, _ = gpu_step(K, ws, q0, u0, tau, dt, 20000, 1e-8, model=model)
     np.testing.assert_array_equal(rep1["num_rows"], rep2["num_rows"])
     np.testing.assert_allclose(u2, u1, atol=1e-5 * max(1.0, np.abs(u1).max()))
-    ref, infos = oracle_step(ws, ws.body_q0, ws.body_u0, tau, dt, eps=1e-11)
+    ref, infos = oracle_step(ws, q0, u0, tau, dt, eps=1e-11)
     check_report(rep2, infos)
-    eu, eq = errors(ws.body_q0, q2, u2, ref.q, ref.u, dt)
+    eu, eq = errors(q0, q2, u2, ref.q, ref.u, dt)
     assert eu <= 1e-4 and eq <= 1e-4
 
 
@@ -288,11 +295,12 @@ def test_heightfield_bipeds_fp32(K):
     for k in range(15):
         st, infos = T.step(ws, st, wg.actuation(ws, 9, k), 2e-3, params)
     assert sum(len(i.contact_ids) for i in infos) > 0
-    if not _margin_clear(None, ws, st.q):
+    q, u = rnd(st.q), rnd(st.u)
+    if not _margin_clear(None, ws, q):
         pytest.skip("a candidate sits on the activation threshold")
     tau = wg.actuation(ws, 9, 15)
-    qg, ug, rep, _ = gpu_step(K, ws, st.q, st.u, tau, 2e-3, 20000, 1e-8)
-    ref, infos = oracle_step(ws, st.q, st.u, tau, 2e-3, eps=1e-11)
+    qg, ug, rep, _ = gpu_step(K, ws, q, u, tau, 2e-3, 20000, 1e-8)
+    ref, infos = oracle_step(ws, q, u, tau, 2e-3, eps=1e-11)
     check_report(rep, infos)
-    eu, eq = errors(st.q, qg, ug, ref.q, ref.u, 2e-3)
+    eu, eq = errors(q, qg, ug, ref.q, ref.u, 2e-3)
     assert eu <= 1e-4 and eq <= 1e-4, (eu, eq)
