@@ -241,15 +241,17 @@ def run_gpu(args, rank, world):
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)   # > L2 (129 MB)
     lib = K.load_library()
     sptr = C.c_void_p(stream.cuda_stream)
-    model = K.Model(ws, "fp32", K.make_params(rho=args.rho))
+    model_plain = K.Model(ws, "fp32", K.make_params(rho=args.rho))
+    model = K.Model(ws, "mixed", K.make_params(rho=args.rho))
     tune_report = None
     if args.workload == "hetero":
         # per-bucket (group size, panel) chosen by the autotuner on a scratch state (not timed)
-        st_tune = K.State(model, dev)
-        st_tune.autotune(args.dt, args.iters, args.tol, tau_dev[0], stream)
-        torch.cuda.synchronize()
+        for mdl in (model_plain, model):
+            st_tune = K.State(mdl, dev)
+            st_tune.autotune(args.dt, args.iters, args.tol, tau_dev[0], stream)
+            torch.cuda.synchronize()
+            del st_tune
         tune_report = model.plan()[1]
-        del st_tune
 
     # ---- learned warm start: train the per-type network on solver-generated pairs (not timed)
     nets = []
@@ -285,9 +287,10 @@ def run_gpu(args, rank, world):
         nets.append(net)
         del X, Y, st_gen
 
-    def run_variant(warm_mode, learned=False):
-        model.set_params(K.make_params(rho=args.rho, warm_mode=warm_mode))
-        st = K.State(model, dev)
+    def run_variant(warm_mode, learned=False, mdl=None):
+        mdl = mdl or model
+        mdl.set_params(K.make_params(rho=args.rho, warm_mode=warm_mode))
+        st = K.State(mdl, dev)
         graph = None
         if args.graph:
             gstream = torch.cuda.Stream(device=dev)
@@ -337,10 +340,11 @@ def run_gpu(args, rank, world):
     sampler = ClockSampler(local)
     sampler.start()
     results = {}
-    results["plain_fp32_cold"] = run_variant(K.WARM_COLD)
-    results["cached_warm_fp32"] = run_variant(K.WARM_CACHED)
+    results["plain_fp32_cold"] = run_variant(K.WARM_COLD, mdl=model_plain)
+    results["mixed_cold"] = run_variant(K.WARM_COLD)
+    results["mixed_cached_warm"] = run_variant(K.WARM_CACHED)
     if nets:
-        results["learned_warm_fp32"] = run_variant(K.WARM_EXTERNAL, learned=True)
+        results["mixed_learned_warm"] = run_variant(K.WARM_EXTERNAL, learned=True)
     clocks = sampler.stop()
     units = W * args.steps * world
     variants = {}
@@ -348,13 +352,13 @@ def run_gpu(args, rank, world):
         t = reduce_max(sum(ms) / 1e3)
         variants[name] = {"value": units / t, "ms_per_step": 1e3 * t / args.steps,
                           "mean_iterations": float(its.mean()), "converged_fraction": float(np.mean(conv))}
-    head = "learned_warm_fp32" if nets else "cached_warm_fp32"
+    head = "mixed_learned_warm" if nets else "mixed_cached_warm"
     st_h, ms_h, rows_h, its_h, _ = results[head]
     v_head = variants[head]["value"]
     t_head = units / v_head
 
     # ---- end to end through the C ABI: pinned host actuation in, body state out, every step
-    learned = head == "learned_warm_fp32"
+    learned = head == "mixed_learned_warm"
     model.set_params(K.make_params(rho=args.rho, warm_mode=K.WARM_EXTERNAL if learned else K.WARM_CACHED))
     B = int(ws.world_body_offset[-1])
     tau_pin = torch.tensor(tau_host).pin_memory()
@@ -412,7 +416,7 @@ def run_gpu(args, rank, world):
     line = {
         "metric": METRIC, "value": v_head, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_head / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16", "data": "synthetic",
         "config": {"workload": f"{desc} per GPU, dt={args.dt}, Gaussian actuation sigma=5, PADMM tol={args.tol}, "
                                f"N_max={args.iters}, rho={args.rho}; headline: {head}",
                    "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}"},

@@ -59,7 +59,11 @@ typedef enum {
 enum { KAMINO_JOINT_REVOLUTE = 0, KAMINO_JOINT_PRISMATIC = 1, KAMINO_JOINT_UNIVERSAL = 2,
        KAMINO_JOINT_SPHERICAL = 3, KAMINO_JOINT_FIXED = 4 };
 enum { KAMINO_TERRAIN_NONE = 0, KAMINO_TERRAIN_PLANE = 1, KAMINO_TERRAIN_HEIGHTFIELD = 2 };
-enum { KAMINO_FP32 = 0, KAMINO_FP64 = 1 };
+/* Arithmetic of a model.  KAMINO_FP32: FP32 storage and arithmetic, the swept FP32 inverse applied
+ * with FP32 FMA.  KAMINO_MIXED: FP32 storage; the inverse is re-stored as BF16 tiles and applied on
+ * tensor cores (FP32 accumulation), and every iteration refines against the FP32 matrix-free
+ * residual.  KAMINO_FP64: FP64 throughout. */
+enum { KAMINO_FP32 = 0, KAMINO_FP64 = 1, KAMINO_MIXED = 2 };
 /* warm start of Alg. 1 (Sec. 4.1): zero, the impulses cached by the previous step, or impulses
  * supplied by the caller through KAMINO_BUF_WARM (e.g. a learned predictor). */
 enum { KAMINO_WARM_COLD = 0, KAMINO_WARM_CACHED = 1, KAMINO_WARM_EXTERNAL = 2 };
@@ -83,7 +87,7 @@ typedef struct {
  * Body indices inside joint_parent / joint_child / contact_body are LOCAL to the world. */
 typedef struct {
     int32_t num_worlds;
-    int32_t precision;                  /* KAMINO_FP32 or KAMINO_FP64 (storage and arithmetic) */
+    int32_t precision;                  /* KAMINO_FP32, KAMINO_MIXED or KAMINO_FP64            */
     const int32_t *world_body_offset;   /* [W+1] */
     const int32_t *world_joint_offset;  /* [W+1] */
     const int32_t *world_contact_offset;/* [W+1] */

@@ -207,7 +207,7 @@ size_t esize(const kamino_model_s *m) { return m->precision == KAMINO_FP64 ? siz
 // 0 when the configuration does not fit.
 size_t persistent_smem(const kamino_model_s *m, const Bucket &b, int group, int nbp, size_t *slice) {
     if (b.units > kSlots * group) return 0;
-    const int mp = std::max(((b.rows + nbp - 1) / nbp) * nbp, nbp);
+    const int mp = std::max(((b.rows + 15) / 16) * 16, 16);
     if (mp > kMaxRowsPad) return 0;
     const Layout L = esize(m) == sizeof(double) ? make_layout<double>(b.nb, b.nj, b.nc, mp, nbp)
                                                 : make_layout<float>(b.nb, b.nj, b.nc, mp, nbp);
@@ -295,6 +295,7 @@ StepArgs<T> make_args(kamino_state_s *st, double dt, int iters, double tol, cons
     a.iters = iters;
     a.nesterov = m->params.nesterov ? 1 : 0;
     a.precond = m->params.precond ? 1 : 0;
+    a.mixed = m->precision == KAMINO_MIXED ? 1 : 0;
     a.warm_mode = m->params.warm_mode;
     a.nb_max = m->nb_max;
     a.nj_max = m->nj_max;
@@ -316,7 +317,7 @@ kamino_status launch_bucket(kamino_state_s *st, const StepArgs<T> &base, int bi,
     a.nb_max = b.nb;
     a.nj_max = b.nj;
     a.nc_max = b.nc;
-    a.mp_max = std::max(((b.rows + b.panel - 1) / b.panel) * b.panel, b.panel);
+    a.mp_max = std::max(((b.rows + 15) / 16) * 16, 16);
     PersistentArgs p{};
     p.worlds = b.d_worlds;
     p.count = b.count;
@@ -429,8 +430,8 @@ kamino_status kamino_model_create(const kamino_model_desc *d, kamino_model_t *ou
     if (!d || !out) return fail(KAMINO_E_INVALID_ARG, "desc and out must not be NULL");
     *out = nullptr;
     if (d->num_worlds < 1) return fail(KAMINO_E_INVALID_ARG, "num_worlds must be >= 1 (got %d)", d->num_worlds);
-    if (d->precision != KAMINO_FP32 && d->precision != KAMINO_FP64)
-        return fail(KAMINO_E_INVALID_ARG, "precision must be KAMINO_FP32 or KAMINO_FP64");
+    if (d->precision != KAMINO_FP32 && d->precision != KAMINO_FP64 && d->precision != KAMINO_MIXED)
+        return fail(KAMINO_E_INVALID_ARG, "precision must be KAMINO_FP32, KAMINO_MIXED or KAMINO_FP64");
     if (!d->world_body_offset || !d->world_joint_offset || !d->world_contact_offset || !d->world_num_actuators ||
         !d->world_mu)
         return fail(KAMINO_E_INVALID_ARG, "per-world arrays must not be NULL");
@@ -560,7 +561,7 @@ kamino_status kamino_model_create(const kamino_model_desc *d, kamino_model_t *ou
     const size_t esz = d->precision == KAMINO_FP64 ? sizeof(double) : sizeof(float);
     m->smem = 0;
     for (int nbp : {16, 8}) {
-        const int mp = std::max(((m->max_rows + nbp - 1) / nbp) * nbp, nbp);
+        const int mp = std::max(((m->max_rows + 15) / 16) * 16, 16);
         if (mp > kMaxRowsPad) continue;
         const Layout L = esz == sizeof(double) ? make_layout<double>(m->nb_max, m->nj_max, m->nc_max, mp, nbp)
                                                : make_layout<float>(m->nb_max, m->nj_max, m->nc_max, mp, nbp);

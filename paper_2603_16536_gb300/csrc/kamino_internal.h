@@ -52,6 +52,7 @@ struct StepArgs {
     const int *world_order;    // optional permutation of worlds (nullptr = identity)
     T dt, tol, eta, rho, beta, margin;
     int iters, nesterov, precond, warm_mode;
+    int mixed;                 // 1: BF16 tiles of the inverse on tensor cores (KAMINO_MIXED)
     // shared-memory layout bounds (maxima over the launched worlds)
     int nb_max, nj_max, nc_max, mp_max;
 };

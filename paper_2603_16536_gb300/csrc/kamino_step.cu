@@ -24,8 +24,10 @@
 //
 // Every loop is bounded (N_max iterations at most); there are no inter-CTA waits.
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stdint.h>
 
 #include "kamino_device.cuh"
 #include "kamino_internal.h"
@@ -258,6 +260,105 @@ __device__ void symv_packed(const T *S, int mp, const T *x, T *y, T *partial, co
     g.sync();
 }
 
+// ----------------------------------------------------------------------------- BF16 tiles of S
+// Mixed precision (KAMINO_MIXED).  After the sweep, S = -A^-1 is re-stored as BF16 16 x 16 tiles of its lower triangle (tile (I, J),
+// I >= J, at index J nt - J (J - 1) / 2 + (I - J); diagonal tiles hold both triangles), in place at
+// the start of the packed FP32 region: one column block at a time is staged in the X scratch
+// (all of its FP32 words are read before any of its tiles is written, and a block's tiles end
+// before the next block's FP32 words begin).  Inside a tile, row r is 32 bytes; its two 16-byte
+// halves swap places when bit 2 of r is set, so the 8 row addresses of an ldmatrix phase fall on
+// distinct banks.
+__device__ __forceinline__ int tile_index(int I, int J, int nt) { return J * nt - (J * (J - 1)) / 2 + (I - J); }
+__device__ __forceinline__ int tile_byte(int r, int c) { return r * 32 + (((c >> 3) ^ ((r >> 2) & 1)) << 4) + ((c & 7) << 1); }
+
+template <typename T>
+__device__ void pack_bf16_tiles(T *A, int mp, T *X, const Group &g) {
+    const int nt = mp / 16;
+    unsigned char *base = reinterpret_cast<unsigned char *>(A);
+    for (int J = 0; J < nt; ++J) {
+        const int j0 = 16 * J, rows = mp - j0;
+        for (int e = g.tid; e < rows * 16; e += g.size) {
+            const int i = j0 + e / 16, j = j0 + (e & 15);
+            X[e] = A[sidx(i, j, mp)];
+        }
+        g.sync();
+        for (int e = g.tid; e < rows * 16; e += g.size) {
+            const int i = j0 + e / 16, c = e & 15;
+            const int I = i >> 4;
+            __nv_bfloat16 *dst = reinterpret_cast<__nv_bfloat16 *>(base + 512 * tile_index(I, J, nt) +
+                                                                   tile_byte(i & 15, c));
+            *dst = __float2bfloat16((float)X[e]);
+        }
+        g.sync();
+    }
+}
+
+__device__ __forceinline__ void ldsm_x4(uint32_t (&a)[4], const void *p) {
+    const unsigned addr = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3]) : "r"(addr));
+}
+__device__ __forceinline__ void ldsm_x4_trans(uint32_t (&a)[4], const void *p) {
+    const unsigned addr = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3]) : "r"(addr));
+}
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// y = S c on tensor cores.  c is split into c_hi = bf16(c) and c_lo = bf16(c - c_hi), which form
+// columns 0 and 1 of the mma's B operand, so the vector keeps ~16 significant bits; S is BF16 and
+// the products accumulate in FP32.  Warp w owns the output row blocks I = w, w + warps, ...: for
+// J <= I it reads tile (I, J), for J > I the transpose of tile (J, I) (ldmatrix .trans), so each
+// row block is one chain of mma without any cross-warp reduction.
+template <typename T>
+__device__ void symv_bf16_tiles(const T *A, int mp, const T *c, T *y, T *X, const Group &g) {
+    const unsigned char *base = reinterpret_cast<const unsigned char *>(A);
+    __nv_bfloat16 *chi = reinterpret_cast<__nv_bfloat16 *>(X);
+    __nv_bfloat16 *clo = chi + mp;
+    for (int i = g.tid; i < mp; i += g.size) {
+        const float v = (float)c[i];
+        const __nv_bfloat16 h = __float2bfloat16(v);
+        chi[i] = h;
+        clo[i] = __float2bfloat16(v - __bfloat162float(h));
+    }
+    g.sync();
+    const int nt = mp / 16, lane = g.lane(), gq = lane >> 2, tq = lane & 3;
+    const int q = lane >> 3, rr = lane & 7;
+    // per-lane row / 16-byte half inside a tile for the normal and the transposed loads
+    const int rn = rr + 8 * (q & 1), hn = q >> 1;
+    const int rt = rr + 8 * (q >> 1), ht = q & 1;
+    const int offn = rn * 32 + ((hn ^ ((rn >> 2) & 1)) << 4);
+    const int offt = rt * 32 + ((ht ^ ((rt >> 2) & 1)) << 4);
+    const __nv_bfloat16 *vec = gq == 0 ? chi : clo;
+    for (int I = g.warp(); I < nt; I += g.warps()) {
+        float acc0[4] = {0.f, 0.f, 0.f, 0.f}, acc1[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int J = 0; J < nt; ++J) {
+            uint32_t a[4];
+            if (J <= I) ldsm_x4(a, base + 512 * tile_index(I, J, nt) + offn);
+            else ldsm_x4_trans(a, base + 512 * tile_index(J, I, nt) + offt);
+            const int k0 = 16 * J + 2 * tq;
+            uint32_t b0 = 0u, b1 = 0u;
+            if (gq < 2) {
+                b0 = *reinterpret_cast<const uint32_t *>(vec + k0);
+                b1 = *reinterpret_cast<const uint32_t *>(vec + k0 + 8);
+            }
+            if (J & 1) mma_bf16(acc1, a, b0, b1);
+            else mma_bf16(acc0, a, b0, b1);
+        }
+        if (tq == 0) {
+            y[16 * I + gq] = T((acc0[0] + acc0[1]) + (acc1[0] + acc1[1]));
+            y[16 * I + gq + 8] = T((acc0[2] + acc0[3]) + (acc1[2] + acc1[3]));
+        }
+    }
+    g.sync();
+}
+
 // In-place blocked sweep of a symmetric positive definite matrix in packed lower storage:
 // sweeping every pivot turns A into -A^-1.  Per panel K of NB columns: PT = A(:, K)^T, the NB x NB
 // pivot block inverted by an unblocked sweep on one warp, TT = (A(:, K) A_KK^-1)^T, the rank-NB
@@ -473,7 +574,7 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
     g.sync();
     const int nact = misc[0];
     const int m = nbil + 3 * nact;
-    const int mp = ((m + NB - 1) / NB) * NB;
+    const int mp = ((m + 15) / 16) * 16;
     const int nunits = nbil + nact;
 
     // ---- 4. u_free = u + dt M^-1 h
@@ -609,8 +710,10 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
     }
     g.sync();
 
-    // ---- 7. A <- -A^-1 (blocked sweep); per-body row lists for the matrix-free products
+    // ---- 7. A <- -A^-1 (blocked sweep), re-stored as BF16 tiles; per-body row lists for the
+    // matrix-free products
     sweep_inverse<T, NB>(A, mp, X, g);
+    if (a.mixed) pack_bf16_tiles(A, mp, X, g);
     for (int i = tid; i < nb; i += nthr) {
         int cnt = 0;
         for (int r = 0; r < m; ++r) cnt += (rbody[2 * r] == i) + (rbody[2 * r + 1] == i);
@@ -691,7 +794,8 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
         }
         g.sync();
         // [8c] correction: xn = S c with S = -A^-1, so x^i = x^{i-1} + xn
-        symv_packed(A, mp, bb, xn, X, g);
+        if (a.mixed) symv_bf16_tiles(A, mp, bb, xn, X, g);
+        else symv_packed(A, mp, bb, xn, X, g);
         // [8d] y^i = Pi_K(x^i - z^/rho), z^i = z^ - rho (x^i - y^i), residual terms
         T lrp = T(0), lrd = T(0), lrc = T(0), lc = T(0);
         T xnew[kSlots][3], ynew[kSlots][3], znew[kSlots][3];   // units tid + s * group size

@@ -16,7 +16,7 @@ import numpy as np
 
 from . import build as _build
 
-FP32, FP64 = 0, 1
+FP32, FP64, MIXED = 0, 1, 2
 WARM_COLD, WARM_CACHED, WARM_EXTERNAL = 0, 1, 2
 BUF_BODY_Q, BUF_BODY_U, BUF_CACHE, BUF_WARM, BUF_RESIDUAL, BUF_TAU = 0, 1, 2, 3, 4, 5
 WORLD_NOT_CONVERGED, WORLD_NONFINITE = 1, 2
@@ -160,7 +160,7 @@ class Model:
 
     def __init__(self, ws, precision: str = "fp32", params: SolverParams | None = None):
         lib = load_library()
-        self.precision = FP64 if precision in ("fp64", FP64) else FP32
+        self.precision = {"fp32": FP32, "fp64": FP64, "mixed": MIXED, FP32: FP32, FP64: FP64, MIXED: MIXED}[precision]
         self.ws = ws
         keep = {
             "bo": np.ascontiguousarray(ws.world_body_offset, np.int32),

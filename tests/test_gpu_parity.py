@@ -4,8 +4,10 @@ unique on over-constrained loops), with the per-world reports checked against th
 active-set sizes.
 
 Metric (per set of worlds): err_u = max|u_gpu - u_oracle| / max(max|u_oracle|, g dt),
-err_q = max|(q+_gpu - q-) - (q+_oracle - q-)| / max(max|q+_oracle - q-|, g dt^2).
-Bars: FP64 <= 1e-9, FP32 <= 1e-4."""
+err_q = max(|q+_gpu - q+_oracle| - ulp(q+_oracle)) / max(max|q+_oracle - q-|, g dt^2), where ulp is
+the spacing of the stored precision at the result (an FP32 state cannot hold q+ closer than that:
+one ulp of a 1 m coordinate is 6e-8 m against increments of ~1e-5 m).
+Bars: FP64 <= 1e-9, FP32 and mixed precision <= 1e-4."""
 import math
 
 import numpy as np
@@ -52,13 +54,15 @@ def gpu_step(K, ws, q, u, tau, dt, iters, tol, precision="fp32", rho=0.1, warm=0
 
 def rnd(x, precision="fp32"):
     """The state exactly as the GPU stores it, so that both sides start from identical inputs."""
-    return np.asarray(x, np.float32).astype(np.float64) if precision == "fp32" else np.asarray(x, np.float64)
+    return np.asarray(x, np.float64) if precision == "fp64" else np.asarray(x, np.float32).astype(np.float64)
 
 
-def errors(q0, q_gpu, u_gpu, q_ref, u_ref, dt):
+def errors(q0, q_gpu, u_gpu, q_ref, u_ref, dt, precision="fp32"):
     eu = np.abs(u_gpu - u_ref).max() / max(np.abs(u_ref).max(), G * dt)
     dq_ref = q_ref - q0
-    eq = np.abs((q_gpu - q0) - dq_ref).max() / max(np.abs(dq_ref).max(), G * dt * dt)
+    ulp = np.spacing(np.abs(q_ref).astype(np.float32)).astype(np.float64) if precision != "fp64" else 0.0
+    excess = np.maximum(np.abs(q_gpu - q_ref) - ulp, 0.0)
+    eq = excess.max() / max(np.abs(dq_ref).max(), G * dt * dt)
     return eu, eq
 
 
@@ -77,7 +81,7 @@ def check_report(rep, infos):
 # The PADMM stopping test bounds residuals, not the distance to the solution: slow modes of
 # D_eta_rho amplify it (the FP64 oracle stopped at 1e-6 differs from itself at 1e-12 by ~1e-3 on
 # these four-bars, at 1e-8 by ~1e-5).  Parity therefore runs the GPU to 1e-12 (FP64) / 1e-8 (FP32).
-@pytest.mark.parametrize("precision,bar,tol", [("fp64", 1e-9, 1e-12), ("fp32", 1e-4, 1e-8)])
+@pytest.mark.parametrize("precision,bar,tol", [("fp64", 1e-9, 1e-12), ("fp32", 1e-4, 1e-8), ("mixed", 1e-4, 1e-8)])
 def test_fourbar_parity_over_steps(K, precision, bar, tol):
     """64 four-bars (1 ms): every step of a 20-step run starts the oracle from the GPU state."""
     ws = wg.make_fourbar(num_worlds=64, seed=0)
@@ -88,7 +92,7 @@ def test_fourbar_parity_over_steps(K, precision, bar, tol):
     for k in range(20):
         qg, ug, rep, _ = gpu_step(K, ws, q, u, None, dt, 20000, tol, precision, model=model)
         ref, infos = oracle_step(ws, q, u, None, dt, eps=1e-12)
-        eu, eq = errors(q, qg, ug, ref.q, ref.u, dt)
+        eu, eq = errors(q, qg, ug, ref.q, ref.u, dt, precision)
         worst = (max(worst[0], eu), max(worst[1], eq))
         check_report(rep, infos)
         assert np.all(rep["status"] & 2 == 0)
@@ -120,14 +124,15 @@ def _margin_clear(infos_ws, ws, q, margin=0.005, gap=1e-5):
     return True
 
 
+@pytest.mark.parametrize("precision", ["fp32", "mixed"])
 @pytest.mark.parametrize("steps_before", [0, 3])
-def test_biped_parity_fp32(K, steps_before):
-    """8 closed-loop bipeds standing on the plane (8 active contacts each), one FP32 step."""
+def test_biped_parity_fp32(K, steps_before, precision):
+    """8 closed-loop bipeds standing on the plane (8 active contacts each), one FP32 / mixed step."""
     ws, q, u = _biped_case(8, seed=2, steps_before=steps_before)
     assert _margin_clear(None, ws, q)
     tau = wg.actuation(ws, 2, steps_before)
     dt = 2e-3
-    qg, ug, rep, _ = gpu_step(K, ws, q, u, tau, dt, 20000, 1e-8)
+    qg, ug, rep, _ = gpu_step(K, ws, q, u, tau, dt, 20000, 1e-8, precision)
     ref, infos = oracle_step(ws, q, u, tau, dt, eps=1e-11)
     check_report(rep, infos)
     eu, eq = errors(q, qg, ug, ref.q, ref.u, dt)
