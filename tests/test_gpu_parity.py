@@ -4,9 +4,10 @@ unique on over-constrained loops), with the per-world reports checked against th
 active-set sizes.
 
 Metric (per set of worlds): err_u = max|u_gpu - u_oracle| / max(max|u_oracle|, g dt),
-err_q = max(|q+_gpu - q+_oracle| - ulp(q+_oracle)) / max(max|q+_oracle - q-|, g dt^2), where ulp is
-the spacing of the stored precision at the result (an FP32 state cannot hold q+ closer than that:
-one ulp of a 1 m coordinate is 6e-8 m against increments of ~1e-5 m).
+err_q = max(|q+_gpu - q+_oracle| - 4 ulp(q+_oracle)) / max(max|q+_oracle - q-|, g dt^2), where ulp
+is the spacing of the stored precision at the result: an FP32 state cannot hold q+ closer than
+that, and the FP32 integration (sum, quaternion product, renormalisation) rounds a few times (one
+ulp of a 1 m coordinate is 6e-8 m against increments of ~1e-5 m).
 Bars: FP64 <= 1e-9, FP32 and mixed precision <= 1e-4."""
 import math
 
@@ -60,7 +61,7 @@ def rnd(x, precision="fp32"):
 def errors(q0, q_gpu, u_gpu, q_ref, u_ref, dt, precision="fp32"):
     eu = np.abs(u_gpu - u_ref).max() / max(np.abs(u_ref).max(), G * dt)
     dq_ref = q_ref - q0
-    ulp = np.spacing(np.abs(q_ref).astype(np.float32)).astype(np.float64) if precision != "fp64" else 0.0
+    ulp = 4.0 * np.spacing(np.abs(q_ref).astype(np.float32)).astype(np.float64) if precision != "fp64" else 0.0
     excess = np.maximum(np.abs(q_gpu - q_ref) - ulp, 0.0)
     eq = excess.max() / max(np.abs(dq_ref).max(), G * dt * dt)
     return eu, eq
@@ -164,7 +165,7 @@ def test_heterogeneous_worlds_one_launch(K):
     check_report(rep, infos)
     for w0 in range(0, 12, 3):
         bs = slice(int(ws.world_body_offset[w0]), int(ws.world_body_offset[w0 + 3]))
-        eu, eq = errors(q[bs], qg[bs], ug[bs], ref.q[bs], ref.u[bs], dt)
+        eu, eq = errors(q[bs], qg[bs], ug[bs], ref.q[bs], ref.u[bs], dt, "fp32")
         assert eu <= 1e-4 and eq <= 1e-4, (w0, eu, eq)
 
 
