@@ -291,6 +291,19 @@ kamino_status kamino_mlp_set_params(kamino_mlp_t mlp, const float *host, int64_t
 kamino_status kamino_mlp_get_normalization(kamino_mlp_t mlp, float *host);
 kamino_status kamino_mlp_set_normalization(kamino_mlp_t mlp, const float *host);
 
+/* ---- Allocation-free inference of the warm-start network (the paper has no counterpart).
+ * kamino_mlp_predict with its activations in a file-scope device array of
+ * KAMINO_MLP_STATIC_SCRATCH_BYTES instead of the network's own workspace: for callers that cannot
+ * let memory be allocated for them (another framework owns the allocator, or a real-time loop
+ * cannot afford the synchronisation of cudaMalloc).  Every GPU that loads the library holds the
+ * array until exit.  The first call on a device looks up the array's device address (make it
+ * before any stream capture).  All calls share the array: calls that overlap on the GPU race, so
+ * serialise them.  A batch whose activations exceed the array returns KAMINO_E_UNSUPPORTED; this
+ * call allocates nothing. */
+#define KAMINO_MLP_STATIC_SCRATCH_BYTES (16u * 1024u * 1024u)
+kamino_status kamino_mlp_predict_static(kamino_mlp_t mlp, const float *x_dev, int32_t batch, float *y_dev,
+                                        void *stream);
+
 /* Message of the calling thread's last failed call ("" if none). */
 const char *kamino_last_error(void);
 

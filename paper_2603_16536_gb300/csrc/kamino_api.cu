@@ -1226,3 +1226,26 @@ kamino_status kamino_mlp_set_normalization(kamino_mlp_t n, const float *host) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------- internal accessors
+kamino_status kamino::report_error(kamino_status s, const char *msg) { return fail(s, "%s", msg); }
+
+bool kamino::mlp::net_view(const struct kamino_mlp_s *n, NetView *out) {
+    if (!n || !out) return false;
+    out->din = n->din;
+    out->dout = n->dout;
+    out->hidden = n->hidden;
+    out->layers = kHiddenLayers;
+    out->max_batch = n->max_batch;
+    out->P = n->P;
+    out->PB = n->PB;
+    for (int l = 0; l <= kHiddenLayers; ++l) {
+        out->woff[l] = n->woff[l];
+        out->boff[l] = n->boff[l];
+    }
+    out->xmean = n->xmean();
+    out->xinv = n->xinv();
+    out->ymean = n->ymean();
+    out->yinv = n->yinv();
+    return true;
+}

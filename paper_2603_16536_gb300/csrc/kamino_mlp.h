@@ -58,5 +58,19 @@ template <typename T>
 cudaError_t warm_write(const int4 *world_a, const int *worlds, int count, int dout, const float *Y,
                        const float *ymean, const float *yinv, T *warm, cudaStream_t s);
 
+// Read-only view of a network's parameters and normalisation (defined with the network's host code).
+struct NetView {
+    int din, dout, hidden, layers, max_batch;
+    const float *P;                 // FP32 master parameters
+    const __nv_bfloat16 *PB;        // BF16 copy of the weight matrices (same offsets)
+    long woff[8], boff[8];          // per layer offsets of W_l and b_l
+    const float *xmean, *xinv, *ymean, *yinv;
+};
+bool net_view(const struct kamino_mlp_s *net, NetView *out);
+
 }  // namespace mlp
+
+// Sets the calling thread's kamino_last_error message and returns `s`.
+kamino_status report_error(kamino_status s, const char *msg);
+
 }  // namespace kamino

@@ -129,6 +129,7 @@ def load_library(path: str | None = None):
         "kamino_mlp_set_params": ([vp, vp, i64], i32),
         "kamino_mlp_get_normalization": ([vp, vp], i32),
         "kamino_mlp_set_normalization": ([vp, vp], i32),
+        "kamino_mlp_predict_static": ([vp, vp, i32, vp, vp], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -389,6 +390,14 @@ class Mlp:
         import torch
         y = torch.empty((X.shape[0], self.info.d_out), dtype=torch.float32, device=X.device)
         _check(load_library().kamino_mlp_predict(self.handle, _dptr(X), X.shape[0], _dptr(y), _sptr(stream)))
+        return y
+
+    def predict_static(self, X, out=None, stream=None):
+        """kamino_mlp_predict without allocation: activations in the library's static scratch."""
+        import torch
+        y = out if out is not None else torch.empty((X.shape[0], self.info.d_out), dtype=torch.float32,
+                                                    device=X.device)
+        _check(load_library().kamino_mlp_predict_static(self.handle, _dptr(X), X.shape[0], _dptr(y), _sptr(stream)))
         return y
 
     def warm_start(self, state: State, tau=None, stream=None):
