@@ -40,7 +40,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     p.add_argument("--worlds", type=int, default=4096)
-    p.add_argument("--iters", type=int, default=200)
+    p.add_argument("--iters", type=int, default=1000)
     p.add_argument("--tol", type=float, default=1e-5)
     p.add_argument("--dt", type=float, default=2e-3)
     p.add_argument("--rho", type=float, default=0.1)
@@ -182,6 +182,31 @@ def algorithmic_flops(rows, iters):
     return m ** 3 / 3.0 + it * (2.0 * m * m + 20.0 * m) + 2.0 * 12.0 * m * 8.0
 
 
+def kernel_source_hash():
+    """SHA-256 of the step kernel's sources: DRAM counters taken from another version are stale."""
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2603_16536_gb300", "csrc")
+    for f in ("kamino_step.cu", "kamino_device.cuh", "kamino_internal.h"):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def step_kernel_traffic(workload, worlds):
+    """dram__bytes_read.sum + dram__bytes_write.sum of one step-kernel launch, from the ncu capture
+    recorded in profiles/traffic.json, scaled from the captured world count to `worlds` (the
+    kernel's traffic is per world); None when absent or taken on other kernel sources."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        entry = json.load(open(path)).get(workload)
+    except (OSError, ValueError):
+        return None
+    if not entry or entry.get("source_sha256") != kernel_source_hash():
+        return None
+    return entry["dram_bytes"] * worlds / entry["worlds"]
+
+
 def build_workload(args, seed):
     import worldgen as wg
     if args.workload == "biped":
@@ -287,9 +312,9 @@ def run_gpu(args, rank, world):
         nets.append(net)
         del X, Y, st_gen
 
-    def run_variant(warm_mode, learned=False, mdl=None):
+    def run_variant(name, warm_mode, learned=False, mdl=None, refine64=True):
         mdl = mdl or model
-        mdl.set_params(K.make_params(rho=args.rho, warm_mode=warm_mode))
+        mdl.set_params(K.make_params(rho=args.rho, warm_mode=warm_mode, refine64=refine64))
         st = K.State(mdl, dev)
         graph = None
         if args.graph:
@@ -298,37 +323,45 @@ def run_gpu(args, rank, world):
                 graph = st.graph(args.dt, args.iters, args.tol, st.tau, gstream)
             torch.cuda.synchronize()
 
-        def one(k):
+        def one(k, ev=None):
             if learned:
                 for net in nets:
                     net.warm_start(st, tau_dev[k], stream)
+            if ev is not None:
+                ev[0].record(stream)
             if graph is not None:
                 st.tau.copy_(tau_dev[k].reshape(-1)[:st.tau.numel()])
                 graph.launch(stream)
             else:
                 st.step(args.dt, args.iters, args.tol, tau_dev[k], stream)
+            if ev is not None:
+                ev[1].record(stream)
 
         for k in range(args.warmup):
             one(k)
         torch.cuda.synchronize()
         barrier()
         torch.cuda.synchronize()
-        ms, rows, its, conv = [], [], [], []
+        ms, ms_step, rows, its, conv = [], [], [], [], []
+        torch.cuda.nvtx.range_push(f"timed_{name}")
         for k in range(args.warmup, total_steps):
             flush.zero_()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            one(k)
+            one(k, (s0, s1))
             e1.record(stream)
             e1.synchronize()
             ms.append(e0.elapsed_time(e1))
+            ms_step.append(s0.elapsed_time(s1))
             rep = st.residuals()
             rows.append(rep["num_rows"].copy())
             its.append(rep["iterations"].copy())
             conv.append(float(np.mean(rep["status"] == 0)))
+        torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
         barrier()
-        return st, ms, np.concatenate(rows), np.concatenate(its), conv
+        return st, ms, np.concatenate(rows), np.concatenate(its), conv, ms_step
 
     def reduce_max(v):
         if world == 1:
@@ -340,20 +373,20 @@ def run_gpu(args, rank, world):
     sampler = ClockSampler(local)
     sampler.start()
     results = {}
-    results["plain_fp32_cold"] = run_variant(K.WARM_COLD, mdl=model_plain)
-    results["mixed_cold"] = run_variant(K.WARM_COLD)
-    results["mixed_cached_warm"] = run_variant(K.WARM_CACHED)
+    results["plain_fp32_cold"] = run_variant("plain_fp32_cold", K.WARM_COLD, mdl=model_plain, refine64=False)
+    results["mixed_cold"] = run_variant("mixed_cold", K.WARM_COLD)
+    results["mixed_cached_warm"] = run_variant("mixed_cached_warm", K.WARM_CACHED)
     if nets:
-        results["mixed_learned_warm"] = run_variant(K.WARM_EXTERNAL, learned=True)
+        results["mixed_learned_warm"] = run_variant("mixed_learned_warm", K.WARM_EXTERNAL, learned=True)
     clocks = sampler.stop()
     units = W * args.steps * world
     variants = {}
-    for name, (_, ms, rows, its, conv) in results.items():
+    for name, (_, ms, rows, its, conv, _) in results.items():
         t = reduce_max(sum(ms) / 1e3)
         variants[name] = {"value": units / t, "ms_per_step": 1e3 * t / args.steps,
                           "mean_iterations": float(its.mean()), "converged_fraction": float(np.mean(conv))}
     head = "mixed_learned_warm" if nets else "mixed_cached_warm"
-    st_h, ms_h, rows_h, its_h, _ = results[head]
+    st_h, ms_h, rows_h, its_h, _, ms_step_h = results[head]
     v_head = variants[head]["value"]
     t_head = units / v_head
 
@@ -396,22 +429,15 @@ def run_gpu(args, rank, world):
             dist.destroy_process_group()
         return 0
 
-    # ---- roofline of the step kernel (one launch = the whole batch) for the headline variant.
-    # With the learned warm start the timed step also holds the MLP launches (< 3% of the time,
-    # measured in profiles/); the step kernel's duration is taken as the whole step time here,
-    # which understates its achieved rate slightly.
+    # ---- roofline of the step kernel (one launch = the whole batch) for the headline variant:
+    # algorithmic flops of the launch over its own duration (CUDA events around kamino_step on the
+    # launching stream, so the warm-start network's launches are not counted).
     peaks = measured_peaks()
     smax = clocks.get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
     alu_peak = SM_COUNT * FP32_LANES * 2 * smax * 1e6 / 1e12       # FP32 FMA lanes x clock, TFLOP/s
     flops = float(algorithmic_flops(rows_h, its_h).sum()) / 1e12
-    achieved = flops / (sum(ms_h) / 1e3)
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tpath):
-        try:
-            traffic = json.load(open(tpath)).get(args.workload)
-        except Exception:
-            traffic = None
+    achieved = flops / (sum(ms_step_h) / 1e3)
+    traffic = step_kernel_traffic(args.workload, W)
     launches_per_step = 1 + (7 * len(nets) if learned else 0)
     line = {
         "metric": METRIC, "value": v_head, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -428,6 +454,8 @@ def run_gpu(args, rank, world):
                 "d2h_bytes_per_step": B * 13 * 4},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                      "frac": achieved / alu_peak, "traffic": traffic,
+                     "kernel": "kamino step kernel (one launch per step)",
+                     "launch_ms": sum(ms_step_h) / len(ms_step_h),
                      "peak_note": f"derived FP32 FMA peak: {SM_COUNT} SMs x {FP32_LANES} lanes x 2 x {smax:.0f} MHz"},
         "clocks": clocks,
     }

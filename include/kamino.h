@@ -79,8 +79,14 @@ typedef struct {
     int32_t nesterov;  /* 1: Nesterov acceleration with adaptive restart (Sec. 4.1)         */
     int32_t precond;   /* 1: Jacobi preconditioning P = diag(D)^-1/2 (Sec. 4.1)              */
     int32_t warm_mode; /* KAMINO_WARM_*                                                       */
-    int32_t reserved;
+    int32_t refine64;  /* 1: once r_p and r_d fall below KAMINO_REFINE64_BELOW, the right-hand
+                        * side and the refinement residual b + A x of every PADMM solve are formed
+                        * in FP64 (FP32 and MIXED precision; FP64 worlds always are).  0: FP32.  */
 } kamino_solver_params;
+
+/* Scaled-unit residual level below which refine64 switches the refinement residual to FP64: the
+ * FP32 residual's own rounding (~1e-6 on the closed-loop bipeds) is then no longer small beside it. */
+#define KAMINO_REFINE64_BELOW 1e-5
 
 /* World description, sum-allocated over worlds: world w owns bodies
  * [world_body_offset[w], world_body_offset[w+1]) and likewise joints and contact candidates.

@@ -296,6 +296,7 @@ StepArgs<T> make_args(kamino_state_s *st, double dt, int iters, double tol, cons
     a.nesterov = m->params.nesterov ? 1 : 0;
     a.precond = m->params.precond ? 1 : 0;
     a.mixed = m->precision == KAMINO_MIXED ? 1 : 0;
+    a.refine64 = m->params.refine64 ? 1 : 0;
     a.warm_mode = m->params.warm_mode;
     a.nb_max = m->nb_max;
     a.nj_max = m->nj_max;

@@ -58,6 +58,15 @@ __device__ __forceinline__ void symvec3(const T *S, const T *v, T *o) {
     o[2] = S[4] * v[0] + S[5] * v[1] + S[2] * v[2];
 }
 
+// the same product with the vector and the result in FP64 (S in any precision)
+template <typename T>
+__device__ __forceinline__ void symvec3d(const T *S, const double *v, double *o) {
+    const double s0 = S[0], s1 = S[1], s2 = S[2], s3 = S[3], s4 = S[4], s5 = S[5];
+    o[0] = s0 * v[0] + s3 * v[1] + s4 * v[2];
+    o[1] = s3 * v[0] + s1 * v[1] + s5 * v[2];
+    o[2] = s4 * v[0] + s5 * v[1] + s2 * v[2];
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

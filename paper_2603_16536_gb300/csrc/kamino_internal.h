@@ -53,6 +53,7 @@ struct StepArgs {
     T dt, tol, eta, rho, beta, margin;
     int iters, nesterov, precond, warm_mode;
     int mixed;                 // 1: BF16 tiles of the inverse on tensor cores (KAMINO_MIXED)
+    int refine64;              // 1: FP64 right-hand side and refinement residual near convergence
     // shared-memory layout bounds (maxima over the launched worlds)
     int nb_max, nj_max, nc_max, mp_max;
 };
@@ -112,6 +113,10 @@ __host__ __device__ inline Layout make_layout(int nb, int nj, int nc, int mp, in
     size_t sweep = (size_t)2 * mp * nb_panel + (size_t)nb_panel * nb_panel;
     if (sweep > xs) xs = sweep;
     if ((size_t)kWarps * mp > xs) xs = (size_t)kWarps * mp;
+    // FP32 worlds: during PADMM the words past the mat-vec partials ([kWarps][mp]) hold the FP64
+    // vectors of the refinement residual (P x, b: mp each; per-body forces: 6 nb)
+    if (s == 4 && (size_t)kWarps * mp + 4 * (size_t)mp + 12 * (size_t)nb > xs)
+        xs = (size_t)kWarps * mp + 4 * (size_t)mp + 12 * (size_t)nb;
     take(L.X, xs * s);
     take(L.A, (size_t)mp * (mp + 1) / 2 * s);
     take(L.red, 2 * 4 * kWarps * s);

@@ -738,8 +738,16 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
     // evaluated matrix-free from the rows (P J M^-1 J^T P x + (eta + rho) x) and A^-1 the swept
     // inverse.  At a fixed point A x = -b holds to the accuracy of the matrix-free product, so the
     // inverse's own rounding (which the nearly singular D~ would amplify) does not move the
-    // solution.
+    // solution.  With refine64, once r_p and r_d fall below KAMINO_REFINE64_BELOW the right-hand
+    // side b, P x, the per-body forces and the residual b + A x are formed in FP64 (from the FP32
+    // iterates, rows and masses), so the fixed point is no longer limited by the rounding of an
+    // FP32 residual of nearly cancelling terms.
     const T eta = a.eta, rho = a.rho, irho = T(1) / a.rho;
+    double *wvd = reinterpret_cast<double *>(X + kWarps * mp);   // FP32 worlds only (make_layout)
+    double *bbd = wvd + mp;
+    double *fbd = bbd + mp;
+    const bool use64 = sizeof(T) == 4 && a.refine64;
+    bool hp = false;     // this iteration's b and P x are the FP64 ones (uniform over the group)
     T acc_a = T(1), c_prev = T(INFINITY);
     T rp = T(INFINITY), rd = T(INFINITY), rc = T(INFINITY);
     int it = 0;
@@ -761,17 +769,51 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
     g.sync();
     for (it = 1; it <= a.iters; ++it) {
         // [8a] f_b = sum over the rows of body b of J_rb^T (P x)_r
-        for (int t = tid; t < 6 * nb; t += nthr) {
-            const int i = t / 6, k = t - 6 * (t / 6);
-            T f = T(0);
-            for (int e = bro[i]; e < bro[i + 1]; ++e) {
-                const int code = brow[e];
-                f = fma(rJ[6 * code + k], wv[code >> 1], f);    // 12 r + 6 side + k
+        if (hp) {
+            for (int t = tid; t < 6 * nb; t += nthr) {
+                const int i = t / 6, k = t - 6 * (t / 6);
+                double f = 0.0;
+                for (int e = bro[i]; e < bro[i + 1]; ++e) {
+                    const int code = brow[e];
+                    f = fma((double)rJ[6 * code + k], wvd[code >> 1], f);
+                }
+                fbd[t] = f;
             }
-            fb[t] = f;
+        } else {
+            for (int t = tid; t < 6 * nb; t += nthr) {
+                const int i = t / 6, k = t - 6 * (t / 6);
+                T f = T(0);
+                for (int e = bro[i]; e < bro[i + 1]; ++e) {
+                    const int code = brow[e];
+                    f = fma(rJ[6 * code + k], wv[code >> 1], f);    // 12 r + 6 side + k
+                }
+                fb[t] = f;
+            }
         }
         g.sync();
         // [8b] c = b + A x = b + P J M^-1 f + (eta + rho) x
+        if (hp) {
+            for (int r = tid; r < mp; r += nthr) {
+                double cr = 0.0;
+                if (r < m) {
+                    const T *J = rJ + 12 * r;
+                    double acc = 0.0;
+                    for (int sd = 0; sd < 2; ++sd) {
+                        const int body = rbody[2 * r + sd];
+                        if (body < 0) continue;
+                        const double *f = fbd + 6 * body;
+                        double gang[3];
+                        symvec3d(bIinv + 6 * body, f + 3, gang);
+                        const double mi = bminv[body];
+                        const T *Js = J + 6 * sd;
+                        acc += mi * ((double)Js[0] * f[0] + (double)Js[1] * f[1] + (double)Js[2] * f[2]) +
+                               (double)Js[3] * gang[0] + (double)Js[4] * gang[1] + (double)Js[5] * gang[2];
+                    }
+                    cr = bbd[r] + (double)p[r] * acc + (double)shift * (double)x[r];
+                }
+                bb[r] = T(cr);
+            }
+        } else
         for (int r = tid; r < mp; r += nthr) {
             T cr = T(0);
             if (r < m) {
@@ -845,6 +887,7 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
         }
         group_reduce4(lrp, lrd, lrc, lc, red, it & 1, g);
         rp = lrp; rd = lrd; rc = lrc;
+        const bool hp_next = use64 && fmax(rp, rd) < T(KAMINO_REFINE64_BELOW);
         // Nesterov with adaptive restart (uniform decision), then commit the iterates and form the
         // next iteration's b and P x
         T beta_n = T(0);
@@ -878,60 +921,76 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
                 y[r] = yv; z[r] = zv; x[r] = xnew[sl][t];
                 wv[r] = p[r] * xnew[sl][t];
             }
-            const T s = cnt == 3 ? mut[u - nbil] * sqrt(zh[r0] * zh[r0] + zh[r0 + 1] * zh[r0 + 1]) : T(0);
+            if (hp_next) {
+                const double z0 = zh[r0], z1 = cnt == 3 ? (double)zh[r0 + 1] : 0.0;
+                const double s = cnt == 3 ? (double)mut[u - nbil] * sqrt(z0 * z0 + z1 * z1) : 0.0;
 #pragma unroll
-            for (int t = 0; t < 3; ++t) {
-                if (t >= cnt) break;
-                const int r = r0 + t;
-                bb[r] = vf[r] + (t == 2 ? s : T(0)) - eta * x[r] - rho * yh[r] - zh[r];
+                for (int t = 0; t < 3; ++t) {
+                    if (t >= cnt) break;
+                    const int r = r0 + t;
+                    wvd[r] = (double)p[r] * (double)x[r];
+                    bbd[r] = (double)vf[r] + (t == 2 ? s : 0.0) - (double)eta * (double)x[r] -
+                             (double)rho * (double)yh[r] - (double)zh[r];
+                }
+            } else {
+                const T s = cnt == 3 ? mut[u - nbil] * sqrt(zh[r0] * zh[r0] + zh[r0 + 1] * zh[r0 + 1]) : T(0);
+#pragma unroll
+                for (int t = 0; t < 3; ++t) {
+                    if (t >= cnt) break;
+                    const int r = r0 + t;
+                    bb[r] = vf[r] + (t == 2 ? s : T(0)) - eta * x[r] - rho * yh[r] - zh[r];
+                }
             }
         }
+        hp = hp_next;
         if (rp < a.tol && rd < a.tol && rc < a.tol) { converged = true; break; }
         g.sync();
     }
     if (it > a.iters) it = a.iters;
     g.sync();
 
-    // ---- 9. lambda = P y; u+ = u_free + M^-1 J^T lambda; integrate; cache; report
+    // ---- 9. lambda = P y; u+ = u_free + M^-1 J^T lambda; integrate; cache; report.  Formed in
+    // FP64 (once per step): u+ is a small difference of large joint impulses through light bodies,
+    // and the pose update adds a small increment to the stored pose.
     for (int r = tid; r < m; r += nthr) xn[r] = p[r] * y[r];
     g.sync();
     bool bad = false;
     for (int i = tid; i < nb; i += nthr) {
-        T f[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
-        for (int r = 0; r < m; ++r) {
-            const T l = xn[r];
-            const T *J = rJ + 12 * r;
-            if (rbody[2 * r] == i) for (int k = 0; k < 6; ++k) f[k] += J[k] * l;
-            if (rbody[2 * r + 1] == i) for (int k = 0; k < 6; ++k) f[k] += J[6 + k] * l;
+        double f[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        for (int e = bro[i]; e < bro[i + 1]; ++e) {
+            const int code = brow[e];
+            const double l = (double)p[code >> 1] * (double)y[code >> 1];
+            const T *J = rJ + 6 * code;                                 // 12 r + 6 side
+            for (int k = 0; k < 6; ++k) f[k] += (double)J[k] * l;
         }
-        T up[6], dw[3];
-        symvec3(bIinv + 6 * i, f + 3, dw);
+        double up[6], dw[3];
+        symvec3d(bIinv + 6 * i, f + 3, dw);
         for (int k = 0; k < 3; ++k) {
-            up[k] = bufree[6 * i + k] + bminv[i] * f[k];
-            up[3 + k] = bufree[6 * i + 3 + k] + dw[k];
+            up[k] = (double)bufree[6 * i + k] + (double)bminv[i] * f[k];
+            up[3 + k] = (double)bufree[6 * i + 3 + k] + dw[k];
         }
         const T *q = bq + 7 * i;
-        T th[3] = {dt * up[3], dt * up[4], dt * up[5]};
-        const T ang = sqrt(dot3(th, th));
-        T dq[4];
-        if (ang > T(0)) {
-            const T s = sin(T(0.5) * ang) / ang;
-            dq[0] = s * th[0]; dq[1] = s * th[1]; dq[2] = s * th[2]; dq[3] = cos(T(0.5) * ang);
+        const double th[3] = {dtd * up[3], dtd * up[4], dtd * up[5]};
+        const double ang = sqrt(th[0] * th[0] + th[1] * th[1] + th[2] * th[2]);
+        double dq[4];
+        if (ang > 0.0) {
+            const double s = sin(0.5 * ang) / ang;
+            dq[0] = s * th[0]; dq[1] = s * th[1]; dq[2] = s * th[2]; dq[3] = cos(0.5 * ang);
         } else {
-            dq[0] = dq[1] = dq[2] = T(0); dq[3] = T(1);
+            dq[0] = dq[1] = dq[2] = 0.0; dq[3] = 1.0;
         }
-        const T qx = q[3], qy = q[4], qz = q[5], qw = q[6];
-        T qn[4] = {dq[3] * qx + dq[0] * qw + dq[1] * qz - dq[2] * qy,
-                   dq[3] * qy - dq[0] * qz + dq[1] * qw + dq[2] * qx,
-                   dq[3] * qz + dq[0] * qy - dq[1] * qx + dq[2] * qw,
-                   dq[3] * qw - dq[0] * qx - dq[1] * qy - dq[2] * qz};
-        const T nrm = rsq(qn[0] * qn[0] + qn[1] * qn[1] + qn[2] * qn[2] + qn[3] * qn[3]);
+        const double qx = q[3], qy = q[4], qz = q[5], qw = q[6];
+        const double qn[4] = {dq[3] * qx + dq[0] * qw + dq[1] * qz - dq[2] * qy,
+                              dq[3] * qy - dq[0] * qz + dq[1] * qw + dq[2] * qx,
+                              dq[3] * qz + dq[0] * qy - dq[1] * qx + dq[2] * qw,
+                              dq[3] * qw - dq[0] * qx - dq[1] * qy - dq[2] * qz};
+        const double nrm = 1.0 / sqrt(qn[0] * qn[0] + qn[1] * qn[1] + qn[2] * qn[2] + qn[3] * qn[3]);
         T *gq = a.body_q + 7 * (size_t)(b0 + i);
         T *gu = a.body_u + 6 * (size_t)(b0 + i);
-        for (int k = 0; k < 3; ++k) gq[k] = q[k] + dt * up[k];
-        for (int k = 0; k < 4; ++k) gq[3 + k] = qn[k] * nrm;
+        for (int k = 0; k < 3; ++k) gq[k] = T((double)q[k] + dtd * up[k]);
+        for (int k = 0; k < 4; ++k) gq[3 + k] = T(qn[k] * nrm);
         for (int k = 0; k < 6; ++k) {
-            gu[k] = up[k];
+            gu[k] = T(up[k]);
             bad |= !isfinite(up[k]);
         }
     }

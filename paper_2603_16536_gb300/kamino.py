@@ -32,11 +32,12 @@ class KaminoError(RuntimeError):
 
 class SolverParams(C.Structure):
     _fields_ = [("eta", C.c_double), ("rho", C.c_double), ("beta", C.c_double), ("margin", C.c_double),
-                ("nesterov", C.c_int32), ("precond", C.c_int32), ("warm_mode", C.c_int32), ("reserved", C.c_int32)]
+                ("nesterov", C.c_int32), ("precond", C.c_int32), ("warm_mode", C.c_int32), ("refine64", C.c_int32)]
 
 
-def make_params(eta=1e-6, rho=0.1, beta=0.2, margin=0.005, nesterov=True, precond=True, warm_mode=WARM_COLD):
-    return SolverParams(eta, rho, beta, margin, int(nesterov), int(precond), int(warm_mode), 0)
+def make_params(eta=1e-6, rho=0.1, beta=0.2, margin=0.005, nesterov=True, precond=True, warm_mode=WARM_COLD,
+                refine64=True):
+    return SolverParams(eta, rho, beta, margin, int(nesterov), int(precond), int(warm_mode), int(refine64))
 
 
 _P = C.c_void_p
