@@ -75,6 +75,11 @@ struct Layout {
 
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+// Row stride of the transposed panels of the sweep: 8 words off a multiple of 32, so that rows
+// k, k+1, k+2, k+3 of a panel start on banks 0, 8, 16, 24 (conflict-free tensor-core fragment loads);
+// non-decreasing in mp, so a layout sized for the largest world fits every smaller one.
+__host__ __device__ inline int panel_ld(int mp) { return mp + (mp % 32 == 0 ? 8 : 24); }
+
 template <typename T>
 __host__ __device__ inline Layout make_layout(int nb, int nj, int nc, int mp, int nb_panel) {
     Layout L{};
@@ -110,13 +115,13 @@ __host__ __device__ inline Layout make_layout(int nb, int nj, int nc, int mp, in
     take(L.bro, (nb + 1) * sizeof(int));
     take(L.brow, 2 * mp * sizeof(int));
     size_t xs = (size_t)mp * 12;
-    size_t sweep = (size_t)2 * mp * nb_panel + (size_t)nb_panel * nb_panel;
+    size_t sweep = (size_t)2 * panel_ld(mp) * nb_panel + (size_t)nb_panel * nb_panel;
     if (sweep > xs) xs = sweep;
     if ((size_t)kWarps * mp > xs) xs = (size_t)kWarps * mp;
     // FP32 worlds: during PADMM the words past the mat-vec partials ([kWarps][mp]) hold the FP64
-    // vectors of the refinement residual (P x, b: mp each; per-body forces: 6 nb)
-    if (s == 4 && (size_t)kWarps * mp + 4 * (size_t)mp + 12 * (size_t)nb > xs)
-        xs = (size_t)kWarps * mp + 4 * (size_t)mp + 12 * (size_t)nb;
+    // vectors of the refinement residual (b: mp; per-body velocities M^-1 J^T P x: 6 nb)
+    if (s == 4 && (size_t)kWarps * mp + 2 * (size_t)mp + 12 * (size_t)nb > xs)
+        xs = (size_t)kWarps * mp + 2 * (size_t)mp + 12 * (size_t)nb;
     take(L.X, xs * s);
     take(L.A, (size_t)mp * (mp + 1) / 2 * s);
     take(L.red, 2 * 4 * kWarps * s);

@@ -311,24 +311,17 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], 
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-// y = S c on tensor cores.  c is split into c_hi = bf16(c) and c_lo = bf16(c - c_hi), which form
+// y = S c on tensor cores.  c comes split into c_hi = bf16(c) and c_lo = bf16(c - c_hi), which form
 // columns 0 and 1 of the mma's B operand, so the vector keeps ~16 significant bits; S is BF16 and
-// the products accumulate in FP32.  Warp w owns the output row blocks I = w, w + warps, ...: for
-// J <= I it reads tile (I, J), for J > I the transpose of tile (J, I) (ldmatrix .trans), so each
-// row block is one chain of mma without any cross-warp reduction.
+// the products accumulate in FP32.  Warp w owns the output row blocks I = w, w + warps, ...; it
+// runs two of them at a time (four independent accumulator chains, one B fragment per column
+// block shared by both).  For J <= I it reads tile (I, J), for J > I the transpose of tile (J, I)
+// (ldmatrix .trans), so each row block is one chain of mma without any cross-warp reduction.
 template <typename T>
-__device__ void symv_bf16_tiles(const T *A, int mp, const T *c, T *y, T *X, const Group &g) {
+__device__ void apply_bf16_tiles(const T *A, int mp, const __nv_bfloat16 *chi, const __nv_bfloat16 *clo, T *y,
+                                 const Group &g) {
     const unsigned char *base = reinterpret_cast<const unsigned char *>(A);
-    __nv_bfloat16 *chi = reinterpret_cast<__nv_bfloat16 *>(X);
-    __nv_bfloat16 *clo = chi + mp;
-    for (int i = g.tid; i < mp; i += g.size) {
-        const float v = (float)c[i];
-        const __nv_bfloat16 h = __float2bfloat16(v);
-        chi[i] = h;
-        clo[i] = __float2bfloat16(v - __bfloat162float(h));
-    }
-    g.sync();
-    const int nt = mp / 16, lane = g.lane(), gq = lane >> 2, tq = lane & 3;
+    const int nt = mp / 16, lane = g.lane(), gq = lane >> 2, tq = lane & 3, nw = g.warps();
     const int q = lane >> 3, rr = lane & 7;
     // per-lane row / 16-byte half inside a tile for the normal and the transposed loads
     const int rn = rr + 8 * (q & 1), hn = q >> 1;
@@ -336,89 +329,118 @@ __device__ void symv_bf16_tiles(const T *A, int mp, const T *c, T *y, T *X, cons
     const int offn = rn * 32 + ((hn ^ ((rn >> 2) & 1)) << 4);
     const int offt = rt * 32 + ((ht ^ ((rt >> 2) & 1)) << 4);
     const __nv_bfloat16 *vec = gq == 0 ? chi : clo;
-    for (int I = g.warp(); I < nt; I += g.warps()) {
-        float acc0[4] = {0.f, 0.f, 0.f, 0.f}, acc1[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int I0 = g.warp(); I0 < nt; I0 += 2 * nw) {
+        const int I1 = I0 + nw;
+        const bool two = I1 < nt;
+        float p0[4] = {0.f, 0.f, 0.f, 0.f}, p1[4] = {0.f, 0.f, 0.f, 0.f};
+        float q0[4] = {0.f, 0.f, 0.f, 0.f}, q1[4] = {0.f, 0.f, 0.f, 0.f};
         for (int J = 0; J < nt; ++J) {
-            uint32_t a[4];
-            if (J <= I) ldsm_x4(a, base + 512 * tile_index(I, J, nt) + offn);
-            else ldsm_x4_trans(a, base + 512 * tile_index(J, I, nt) + offt);
             const int k0 = 16 * J + 2 * tq;
             uint32_t b0 = 0u, b1 = 0u;
             if (gq < 2) {
                 b0 = *reinterpret_cast<const uint32_t *>(vec + k0);
                 b1 = *reinterpret_cast<const uint32_t *>(vec + k0 + 8);
             }
-            if (J & 1) mma_bf16(acc1, a, b0, b1);
-            else mma_bf16(acc0, a, b0, b1);
+            uint32_t t0[4];
+            if (J <= I0) ldsm_x4(t0, base + 512 * tile_index(I0, J, nt) + offn);
+            else ldsm_x4_trans(t0, base + 512 * tile_index(J, I0, nt) + offt);
+            if (two) {
+                uint32_t t1[4];
+                if (J <= I1) ldsm_x4(t1, base + 512 * tile_index(I1, J, nt) + offn);
+                else ldsm_x4_trans(t1, base + 512 * tile_index(J, I1, nt) + offt);
+                if (J & 1) mma_bf16(q1, t1, b0, b1);
+                else mma_bf16(q0, t1, b0, b1);
+            }
+            if (J & 1) mma_bf16(p1, t0, b0, b1);
+            else mma_bf16(p0, t0, b0, b1);
         }
         if (tq == 0) {
-            y[16 * I + gq] = T((acc0[0] + acc0[1]) + (acc1[0] + acc1[1]));
-            y[16 * I + gq + 8] = T((acc0[2] + acc0[3]) + (acc1[2] + acc1[3]));
+            y[16 * I0 + gq] = T((p0[0] + p0[1]) + (p1[0] + p1[1]));
+            y[16 * I0 + gq + 8] = T((p0[2] + p0[3]) + (p1[2] + p1[3]));
+            if (two) {
+                y[16 * I1 + gq] = T((q0[0] + q0[1]) + (q1[0] + q1[1]));
+                y[16 * I1 + gq + 8] = T((q0[2] + q0[3]) + (q1[2] + q1[3]));
+            }
         }
     }
     g.sync();
+}
+
+__device__ __forceinline__ uint32_t tf32_bits(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
 // In-place blocked sweep of a symmetric positive definite matrix in packed lower storage:
 // sweeping every pivot turns A into -A^-1.  Per panel K of NB columns: PT = A(:, K)^T, the NB x NB
 // pivot block inverted by an unblocked sweep on one warp, TT = (A(:, K) A_KK^-1)^T, the rank-NB
 // update A(i, j) -= T(i, :) P(j, :)^T for i, j outside K, then A(:, K) = T and A_KK = -A_KK^-1.
-// The panels are stored transposed ([NB][mp]) so that lanes walking consecutive rows read
-// consecutive words; the update runs in strips of 32 rows x 16 columns per warp (lane = row,
-// 16 accumulators), reading the panel row of P as broadcast float4 loads.
+// The panels are stored transposed ([NB][ld], ld = panel_ld(mp)) so that lanes walking
+// consecutive rows read consecutive words.  The update runs in strips of 32 rows x 16 columns per
+// warp: on FP32 lanes (lane = row, 16 accumulators, the panel row of P read as broadcast float4
+// loads), or with `tc` on tensor cores, as 8 mma.m16n8k8 TF32 products per strip with FP32
+// accumulation (the mixed-precision mode, whose inverse is stored in BF16 afterwards); ld is 8
+// words off a multiple of 32 so that the fragment loads of the four k-rows fall on distinct banks.
 template <typename T, int NB>
-__device__ void sweep_inverse(T *A, int mp, T *X, const Group &g) {
-    T *PT = X;                   // [NB][mp] old panel, transposed
-    T *TT = X + NB * mp;         // [NB][mp]
-    T *Dm = X + 2 * NB * mp;     // [NB][NB]
+__device__ void sweep_inverse(T *A, int mp, T *X, bool tc, const Group &g) {
+    const int ld = panel_ld(mp);
+    T *PT = X;                   // [NB][ld] old panel, transposed
+    T *TT = X + NB * ld;         // [NB][ld]
+    T *Dm = X + 2 * NB * ld;     // [NB][NB]
     const int tid = g.tid, nthr = g.size, lane = g.lane(), warp = g.warp(), nw = g.warps();
     const int nrb = (mp + 31) / 32;      // 32-row blocks
     const int ncb = mp / 16 + (mp % 16 ? 1 : 0);
     for (int k0 = 0; k0 < mp; k0 += NB) {
         for (int e = tid; e < NB * mp; e += nthr) {
             const int u = e / mp, i = e - u * mp;
-            PT[e] = A[sidx(i, k0 + u, mp)];
+            PT[u * ld + i] = A[sidx(i, k0 + u, mp)];
         }
         g.sync();
-        // -- pivot block inverse by an unblocked sweep on one warp (result negated at the end)
+        // -- pivot block inverse by an unblocked sweep on one warp, in registers: lane l holds row
+        // l / LR, columns (l % LR) * CPL ... + CPL - 1 of the NB x NB block; the pivot row, column and
+        // value of every step come by shuffles (result negated at the end)
         if (warp == 0) {
-            for (int e = lane; e < NB * NB; e += 32) Dm[e] = PT[(e % NB) * mp + k0 + e / NB];
-            __syncwarp();
-            for (int p = 0; p < NB; ++p) {
-                const T d = T(1) / Dm[p * NB + p];
-                T nv[(NB * NB + 31) / 32];
+            constexpr int LR = 32 / NB, CPL = NB / LR;
+            const int ri = lane / LR, h = lane % LR;
+            T v[CPL];
 #pragma unroll
-                for (int q = 0; q < (NB * NB + 31) / 32; ++q) {
-                    const int e = lane + 32 * q;
-                    if (e < NB * NB) {
-                        const int i = e / NB, j = e % NB;
-                        const T aij = Dm[e], aip = Dm[i * NB + p], apj = Dm[p * NB + j];
-                        if (i == p && j == p) nv[q] = -d;
-                        else if (i == p) nv[q] = apj * d;
-                        else if (j == p) nv[q] = aip * d;
-                        else nv[q] = aij - aip * apj * d;
-                    }
-                }
-                __syncwarp();
+            for (int c = 0; c < CPL; ++c) v[c] = PT[(h * CPL + c) * ld + k0 + ri];
 #pragma unroll
-                for (int q = 0; q < (NB * NB + 31) / 32; ++q) {
-                    const int e = lane + 32 * q;
-                    if (e < NB * NB) Dm[e] = nv[q];
+            for (int pv = 0; pv < NB; ++pv) {
+                const T d = T(1) / __shfl_sync(0xffffffffu, v[pv % CPL], pv * LR + pv / CPL);
+                const T aip = __shfl_sync(0xffffffffu, v[pv % CPL], ri * LR + pv / CPL);
+                T apj[CPL];
+#pragma unroll
+                for (int c = 0; c < CPL; ++c) apj[c] = __shfl_sync(0xffffffffu, v[c], pv * LR + h);
+#pragma unroll
+                for (int c = 0; c < CPL; ++c) {
+                    const int j = h * CPL + c;
+                    if (ri == pv) v[c] = j == pv ? -d : apj[c] * d;
+                    else if (j == pv) v[c] = aip * d;
+                    else v[c] -= aip * apj[c] * d;
                 }
-                __syncwarp();
             }
-            for (int e = lane; e < NB * NB; e += 32) Dm[e] = -Dm[e];   // = A_KK^-1 (symmetric)
+#pragma unroll
+            for (int c = 0; c < CPL; ++c) Dm[ri * NB + h * CPL + c] = -v[c];   // = A_KK^-1 (symmetric)
         }
         g.sync();
-        // -- TT[t][i] = sum_u P(i, u) Dinv(u, t) for rows outside K
+        // -- TT[t][i] = sum_u P(i, u) Dinv(u, t) for rows outside K (zero on K)
         for (int e = tid; e < NB * mp; e += nthr) {
             const int t = e / mp, i = e - t * mp;
             T acc = T(0);
             if (i < k0 || i >= k0 + NB) {
 #pragma unroll
-                for (int u = 0; u < NB; ++u) acc = fma(PT[u * mp + i], Dm[u * NB + t], acc);
+                for (int u = 0; u < NB; ++u) acc = fma(PT[u * ld + i], Dm[u * NB + t], acc);
             }
-            TT[e] = acc;
+            TT[t * ld + i] = acc;
         }
         g.sync();
         // -- rank-NB update of the lower triangle outside K: strips (row block R, column block C)
@@ -428,6 +450,54 @@ __device__ void sweep_inverse(T *A, int mp, T *X, const Group &g) {
             for (int C = 0; C < cmax; ++C, ++strip) {
                 if (strip % nw != warp) continue;
                 if (NB == 16 && C >= kc0 && C < kc1) continue;    // the pivot columns
+                if constexpr (sizeof(T) == 4) {
+                    if (tc) {
+                        const int gq = lane >> 2, tq = lane & 3;
+                        float acc[2][2][4];
+#pragma unroll
+                        for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                            for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+                                for (int e = 0; e < 4; ++e) acc[mt][nt][e] = 0.0f;
+#pragma unroll
+                        for (int ks = 0; ks < NB / 8; ++ks) {
+                            const T *t0 = TT + (8 * ks + tq) * ld, *t1 = t0 + 4 * ld;
+                            const T *p0 = PT + (8 * ks + tq) * ld, *p1 = p0 + 4 * ld;
+                            uint32_t af[2][4], bf[2][2];
+#pragma unroll
+                            for (int mt = 0; mt < 2; ++mt) {
+                                const int i0 = 32 * R + 16 * mt + gq;
+                                af[mt][0] = tf32_bits(i0 < mp ? t0[i0] : 0.0f);
+                                af[mt][1] = tf32_bits(i0 + 8 < mp ? t0[i0 + 8] : 0.0f);
+                                af[mt][2] = tf32_bits(i0 < mp ? t1[i0] : 0.0f);
+                                af[mt][3] = tf32_bits(i0 + 8 < mp ? t1[i0 + 8] : 0.0f);
+                            }
+#pragma unroll
+                            for (int nt = 0; nt < 2; ++nt) {
+                                const int j0 = 16 * C + 8 * nt + gq;
+                                bf[nt][0] = tf32_bits(j0 < mp ? p0[j0] : 0.0f);
+                                bf[nt][1] = tf32_bits(j0 < mp ? p1[j0] : 0.0f);
+                            }
+#pragma unroll
+                            for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                                for (int nt = 0; nt < 2; ++nt) mma_tf32(acc[mt][nt], af[mt], bf[nt][0], bf[nt][1]);
+                        }
+#pragma unroll
+                        for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                            for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+                                for (int e = 0; e < 4; ++e) {
+                                    const int i = 32 * R + 16 * mt + gq + (e >> 1) * 8;
+                                    const int j = 16 * C + 8 * nt + 2 * tq + (e & 1);
+                                    if (i < mp && j <= i && (i < k0 || i >= k0 + NB) && (j < k0 || j >= k0 + NB))
+                                        A[col_start(j, mp) + i - j] -= acc[mt][nt][e];
+                                }
+                        continue;
+                    }
+                }
                 const int i = 32 * R + lane;
                 const bool rowin = i < mp && (i < k0 || i >= k0 + NB);
                 T acc[16];
@@ -435,9 +505,9 @@ __device__ void sweep_inverse(T *A, int mp, T *X, const Group &g) {
                 for (int c = 0; c < 16; ++c) acc[c] = T(0);
 #pragma unroll 4
                 for (int u = 0; u < NB; ++u) {
-                    const T tv = rowin ? TT[u * mp + i] : T(0);
+                    const T tv = rowin ? TT[u * ld + i] : T(0);
                     T pr[16];
-                    load16(PT + u * mp + 16 * C, pr);   // broadcast: every lane reads the same words
+                    load16(PT + u * ld + 16 * C, pr);   // broadcast: every lane reads the same words
 #pragma unroll
                     for (int c = 0; c < 16; ++c) acc[c] = fma(tv, pr[c], acc[c]);
                 }
@@ -461,7 +531,7 @@ __device__ void sweep_inverse(T *A, int mp, T *X, const Group &g) {
             if (i >= k0 && i < k0 + NB) {
                 if (i >= j) A[pidx(i, j, mp)] = -Dm[(i - k0) * NB + t];
             } else {
-                A[sidx(i, j, mp)] = TT[e];
+                A[sidx(i, j, mp)] = TT[t * ld + i];
             }
         }
         g.sync();
@@ -712,7 +782,7 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
 
     // ---- 7. A <- -A^-1 (blocked sweep), re-stored as BF16 tiles; per-body row lists for the
     // matrix-free products
-    sweep_inverse<T, NB>(A, mp, X, g);
+    sweep_inverse<T, NB>(A, mp, X, a.mixed != 0, g);
     if (a.mixed) pack_bf16_tiles(A, mp, X, g);
     for (int i = tid; i < nb; i += nthr) {
         int cnt = 0;
@@ -739,15 +809,22 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
     // inverse.  At a fixed point A x = -b holds to the accuracy of the matrix-free product, so the
     // inverse's own rounding (which the nearly singular D~ would amplify) does not move the
     // solution.  With refine64, once r_p and r_d fall below KAMINO_REFINE64_BELOW the right-hand
-    // side b, P x, the per-body forces and the residual b + A x are formed in FP64 (from the FP32
-    // iterates, rows and masses), so the fixed point is no longer limited by the rounding of an
-    // FP32 residual of nearly cancelling terms.
+    // side b, the per-body velocities M^-1 J^T P x and the residual b + A x are formed in FP64
+    // (from the FP32 iterates, rows and masses), so the fixed point is no longer limited by the
+    // rounding of an FP32 residual of nearly cancelling terms.
+    //
+    // Unit u (a joint row, or the three rows of a contact) belongs to thread u mod group size for
+    // the whole solve: only its owner touches its b, y, z, y^, z^, so an iteration has four
+    // barriers (after the per-body gather, after the residual rows, after the mat-vec, and the
+    // residual reduction, which also publishes x and P x).
     const T eta = a.eta, rho = a.rho, irho = T(1) / a.rho;
-    double *wvd = reinterpret_cast<double *>(X + kWarps * mp);   // FP32 worlds only (make_layout)
-    double *bbd = wvd + mp;
-    double *fbd = bbd + mp;
+    double *bbd = reinterpret_cast<double *>(X + kWarps * mp);   // FP32 worlds only (make_layout)
+    double *gbd = bbd + mp;
+    __nv_bfloat16 *chi = reinterpret_cast<__nv_bfloat16 *>(X), *clo = chi + mp;   // mixed: split c
     const bool use64 = sizeof(T) == 4 && a.refine64;
-    bool hp = false;     // this iteration's b and P x are the FP64 ones (uniform over the group)
+    bool hp = false;     // b of the coming iteration is the FP64 one; set once, uniform over the group
+    int LB = 8;          // lanes per body in the gather: a power of two with LB * nb <= group size
+    while (LB > 1 && LB * nb > nthr) LB >>= 1;
     T acc_a = T(1), c_prev = T(INFINITY);
     T rp = T(INFINITY), rd = T(INFINITY), rc = T(INFINITY);
     int it = 0;
@@ -766,79 +843,115 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
             }
         }
     }
+    if (a.mixed) {
+        for (int r = m + tid; r < mp; r += nthr) {
+            chi[r] = __float2bfloat16(0.0f);
+            clo[r] = __float2bfloat16(0.0f);
+        }
+    }
     g.sync();
     for (it = 1; it <= a.iters; ++it) {
-        // [8a] f_b = sum over the rows of body b of J_rb^T (P x)_r
-        if (hp) {
-            for (int t = tid; t < 6 * nb; t += nthr) {
-                const int i = t / 6, k = t - 6 * (t / 6);
-                double f = 0.0;
-                for (int e = bro[i]; e < bro[i + 1]; ++e) {
-                    const int code = brow[e];
-                    f = fma((double)rJ[6 * code + k], wvd[code >> 1], f);
-                }
-                fbd[t] = f;
-            }
-        } else {
-            for (int t = tid; t < 6 * nb; t += nthr) {
-                const int i = t / 6, k = t - 6 * (t / 6);
-                T f = T(0);
-                for (int e = bro[i]; e < bro[i + 1]; ++e) {
-                    const int code = brow[e];
-                    f = fma(rJ[6 * code + k], wv[code >> 1], f);    // 12 r + 6 side + k
-                }
-                fb[t] = f;
-            }
-        }
-        g.sync();
-        // [8b] c = b + A x = b + P J M^-1 f + (eta + rho) x
-        if (hp) {
-            for (int r = tid; r < mp; r += nthr) {
-                double cr = 0.0;
-                if (r < m) {
-                    const T *J = rJ + 12 * r;
-                    double acc = 0.0;
-                    for (int sd = 0; sd < 2; ++sd) {
-                        const int body = rbody[2 * r + sd];
-                        if (body < 0) continue;
-                        const double *f = fbd + 6 * body;
-                        double gang[3];
-                        symvec3d(bIinv + 6 * body, f + 3, gang);
-                        const double mi = bminv[body];
-                        const T *Js = J + 6 * sd;
-                        acc += mi * ((double)Js[0] * f[0] + (double)Js[1] * f[1] + (double)Js[2] * f[2]) +
-                               (double)Js[3] * gang[0] + (double)Js[4] * gang[1] + (double)Js[5] * gang[2];
+        // [8a] per body: g_b = M_b^-1 sum over the body's rows r of J_rb^T (P x)_r; LB lanes per
+        // body take its rows round-robin, then a shuffle reduction
+        for (int base = 0; base < nb * LB; base += nthr) {
+            if (base + (tid & ~31) >= nb * LB) continue;          // the whole warp is past the bodies
+            const int t = base + tid, body = t / LB, sub = t - body * LB;
+            const bool on = t < nb * LB;
+            if (hp) {
+                double f[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+                if (on) {
+                    for (int e = bro[body] + sub; e < bro[body + 1]; e += LB) {
+                        const int code = brow[e], r = code >> 1;
+                        const double w = (double)p[r] * (double)x[r];
+                        const T *J = rJ + 6 * code;                 // 12 r + 6 side
+#pragma unroll
+                        for (int k = 0; k < 6; ++k) f[k] = fma((double)J[k], w, f[k]);
                     }
-                    cr = bbd[r] + (double)p[r] * acc + (double)shift * (double)x[r];
                 }
-                bb[r] = T(cr);
-            }
-        } else
-        for (int r = tid; r < mp; r += nthr) {
-            T cr = T(0);
-            if (r < m) {
-                const T *J = rJ + 12 * r;
-                T acc = T(0);
-                for (int sd = 0; sd < 2; ++sd) {
-                    const int body = rbody[2 * r + sd];
-                    if (body < 0) continue;
-                    const T *f = fb + 6 * body;
-                    T gang[3];
-                    symvec3(bIinv + 6 * body, f + 3, gang);
+                for (int o = LB >> 1; o > 0; o >>= 1) {
+#pragma unroll
+                    for (int k = 0; k < 6; ++k) f[k] += __shfl_xor_sync(0xffffffffu, f[k], o);
+                }
+                if (on && sub == 0) {
+                    const double mi = bminv[body];
+                    for (int k = 0; k < 3; ++k) gbd[6 * body + k] = mi * f[k];
+                    symvec3d(bIinv + 6 * body, f + 3, gbd + 6 * body + 3);
+                }
+            } else {
+                T f[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+                if (on) {
+                    for (int e = bro[body] + sub; e < bro[body + 1]; e += LB) {
+                        const int code = brow[e];
+                        const T w = wv[code >> 1];
+                        const T *J = rJ + 6 * code;
+#pragma unroll
+                        for (int k = 0; k < 6; ++k) f[k] = fma(J[k], w, f[k]);
+                    }
+                }
+                for (int o = LB >> 1; o > 0; o >>= 1) {
+#pragma unroll
+                    for (int k = 0; k < 6; ++k) f[k] += __shfl_xor_sync(0xffffffffu, f[k], o);
+                }
+                if (on && sub == 0) {
                     const T mi = bminv[body];
-                    const T *Js = J + 6 * sd;
-                    acc += mi * (Js[0] * f[0] + Js[1] * f[1] + Js[2] * f[2]) + Js[3] * gang[0] + Js[4] * gang[1] +
-                           Js[5] * gang[2];
+                    for (int k = 0; k < 3; ++k) fb[6 * body + k] = mi * f[k];
+                    symvec3(bIinv + 6 * body, f + 3, fb + 6 * body + 3);
                 }
-                cr = bb[r] + p[r] * acc + shift * x[r];
             }
-            bb[r] = cr;
         }
         g.sync();
-        // [8c] correction: xn = S c with S = -A^-1, so x^i = x^{i-1} + xn
-        if (a.mixed) symv_bf16_tiles(A, mp, bb, xn, X, g);
+        // [8b] owners: c_r = b_r + p_r J_r (g_A, g_B) + (eta + rho) x_r for the rows of their units,
+        // stored as the BF16 hi / lo split (mixed) or in bb (FP32 / FP64 mat-vec)
+#pragma unroll
+        for (int sl = 0; sl < kSlots; ++sl) {
+            const int u = tid + sl * nthr;
+            if (u >= nunits) continue;
+            const int r0 = u < nbil ? u : nbil + 3 * (u - nbil);
+            const int cnt = u < nbil ? 1 : 3;
+            for (int t = 0; t < cnt; ++t) {
+                const int r = r0 + t;
+                const int sa = rbody[2 * r], sb = rbody[2 * r + 1];
+                const T *J = rJ + 12 * r;
+                T c;
+                if (hp) {
+                    double acc = 0.0;
+                    if (sa >= 0) {
+#pragma unroll
+                        for (int k = 0; k < 6; ++k) acc = fma((double)J[k], gbd[6 * sa + k], acc);
+                    }
+                    if (sb >= 0) {
+#pragma unroll
+                        for (int k = 0; k < 6; ++k) acc = fma((double)J[6 + k], gbd[6 * sb + k], acc);
+                    }
+                    c = T(bbd[r] + (double)p[r] * acc + (double)shift * (double)x[r]);
+                } else {
+                    T acc = T(0);
+                    if (sa >= 0) {
+#pragma unroll
+                        for (int k = 0; k < 6; ++k) acc = fma(J[k], fb[6 * sa + k], acc);
+                    }
+                    if (sb >= 0) {
+#pragma unroll
+                        for (int k = 0; k < 6; ++k) acc = fma(J[6 + k], fb[6 * sb + k], acc);
+                    }
+                    c = bb[r] + p[r] * acc + shift * x[r];
+                }
+                if (a.mixed) {
+                    const float v = (float)c;
+                    const __nv_bfloat16 h = __float2bfloat16(v);
+                    chi[r] = h;
+                    clo[r] = __float2bfloat16(v - __bfloat162float(h));
+                } else {
+                    bb[r] = c;
+                }
+            }
+        }
+        g.sync();
+        // [8c] correction: xn = S c with S = -A^-1, so x^i = x^{i-1} + xn (ends with a barrier)
+        if (a.mixed) apply_bf16_tiles(A, mp, chi, clo, xn, g);
         else symv_packed(A, mp, bb, xn, X, g);
-        // [8d] y^i = Pi_K(x^i - z^/rho), z^i = z^ - rho (x^i - y^i), residual terms
+        // [8d] owners: x^i, y^i = Pi_K(x^i - z^/rho), z^i = z^ - rho (x^i - y^i), residual terms; x and
+        // P x go to shared memory at once (the reduction's barrier publishes them for [8a])
         T lrp = T(0), lrd = T(0), lrc = T(0), lc = T(0);
         T xnew[kSlots][3], ynew[kSlots][3], znew[kSlots][3];   // units tid + s * group size
 #pragma unroll
@@ -853,6 +966,8 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
                 lrd = fmax(lrd, fabs(eta * (xv - x[u]) + rho * (yv - yh[u])));
                 lc += (zv - zh[u]) * (zv - zh[u]) * irho + rho * (yv - yh[u]) * (yv - yh[u]);
                 xnew[sl][0] = xv; ynew[sl][0] = yv; znew[sl][0] = zv;
+                x[u] = xv;
+                wv[u] = p[u] * xv;
             } else {
                 const int k = u - nbil, r0 = nbil + 3 * k;
                 const T mu = mut[k];
@@ -883,13 +998,19 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
                     xnew[sl][t] = xv[t]; ynew[sl][t] = yv[t]; znew[sl][t] = zv;
                 }
                 lrc = fmax(lrc, fabs(ydz));
+#pragma unroll
+                for (int t = 0; t < 3; ++t) {
+                    x[r0 + t] = xv[t];
+                    wv[r0 + t] = p[r0 + t] * xv[t];
+                }
             }
         }
         group_reduce4(lrp, lrd, lrc, lc, red, it & 1, g);
         rp = lrp; rd = lrd; rc = lrc;
-        const bool hp_next = use64 && fmax(rp, rd) < T(KAMINO_REFINE64_BELOW);
-        // Nesterov with adaptive restart (uniform decision), then commit the iterates and form the
-        // next iteration's b and P x
+        converged = rp < a.tol && rd < a.tol && rc < a.tol;
+        hp = use64 && (hp || fmax(rp, rd) < T(KAMINO_REFINE64_BELOW));
+        // Nesterov with adaptive restart (uniform decision), then the owners commit y, z, y^, z^ and
+        // form the next iteration's b (in FP64 once hp is set)
         T beta_n = T(0);
         bool restart = false;
         if (a.nesterov) {
@@ -918,18 +1039,16 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
                 if (!a.nesterov) { yh[r] = yv; zh[r] = zv; }
                 else if (restart) { yh[r] = y[r]; zh[r] = z[r]; }
                 else { yh[r] = yv + beta_n * (yv - y[r]); zh[r] = zv + beta_n * (zv - z[r]); }
-                y[r] = yv; z[r] = zv; x[r] = xnew[sl][t];
-                wv[r] = p[r] * xnew[sl][t];
+                y[r] = yv; z[r] = zv;
             }
-            if (hp_next) {
+            if (hp) {
                 const double z0 = zh[r0], z1 = cnt == 3 ? (double)zh[r0 + 1] : 0.0;
                 const double s = cnt == 3 ? (double)mut[u - nbil] * sqrt(z0 * z0 + z1 * z1) : 0.0;
 #pragma unroll
                 for (int t = 0; t < 3; ++t) {
                     if (t >= cnt) break;
                     const int r = r0 + t;
-                    wvd[r] = (double)p[r] * (double)x[r];
-                    bbd[r] = (double)vf[r] + (t == 2 ? s : 0.0) - (double)eta * (double)x[r] -
+                    bbd[r] = (double)vf[r] + (t == 2 ? s : 0.0) - (double)eta * (double)xnew[sl][t] -
                              (double)rho * (double)yh[r] - (double)zh[r];
                 }
             } else {
@@ -938,13 +1057,11 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
                 for (int t = 0; t < 3; ++t) {
                     if (t >= cnt) break;
                     const int r = r0 + t;
-                    bb[r] = vf[r] + (t == 2 ? s : T(0)) - eta * x[r] - rho * yh[r] - zh[r];
+                    bb[r] = vf[r] + (t == 2 ? s : T(0)) - eta * xnew[sl][t] - rho * yh[r] - zh[r];
                 }
             }
         }
-        hp = hp_next;
-        if (rp < a.tol && rd < a.tol && rc < a.tol) { converged = true; break; }
-        g.sync();
+        if (converged) break;
     }
     if (it > a.iters) it = a.iters;
     g.sync();
