@@ -70,7 +70,7 @@ struct PersistentArgs {
 // Byte offsets of the per-world shared-memory working set.
 struct Layout {
     size_t bq, bu, bR, bRd, bI, bIinv, bminv, bufree, jwr, cid, cslot, rbody, rJ, rvs;
-    size_t vf, p, x, xn, y, z, yh, zh, b, mut, wv, fb, bro, brow, X, A, red, misc, total;
+    size_t vf, p, x, xn, y, z, yh, zh, b, mut, mui, wv, fb, bro, brow, X, A, red, misc, total;
 };
 
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -110,6 +110,7 @@ __host__ __device__ inline Layout make_layout(int nb, int nj, int nc, int mp, in
     take(L.zh, mp * s);
     take(L.b, mp * s);
     take(L.mut, (nc > 0 ? nc : 1) * s);
+    take(L.mui, (nc > 0 ? nc : 1) * s);
     take(L.wv, mp * s);
     take(L.fb, nb * 6 * s);
     take(L.bro, (nb + 1) * sizeof(int));

@@ -155,12 +155,22 @@ __device__ void joint_rows(int type, int par, int ch, const double *fr, const T 
     }
 }
 
-// Group-wide reductions of (max, max, max, sum); every thread gets the results.  The scratch is
+// Group-wide reductions of (max, max, max, sum) of non-negative values; every thread gets the
+// results.  The scratch is
 // double-buffered by `phase` so consecutive calls need only the one barrier inside.
 template <typename T>
 __device__ __forceinline__ void group_reduce4(T &a, T &b, T &c, T &d, T *red, int phase, const Group &g) {
     const int lane = g.lane(), warp = g.warp(), nw = g.warps();
-    a = warp_max(a); b = warp_max(b); c = warp_max(c); d = warp_sum(d);
+    if constexpr (sizeof(T) == 4) {
+        // a, b, c are maxima of absolute values: as unsigned integers their bit patterns order like
+        // the floats, so one redux.sync each
+        a = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(a)));
+        b = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(b)));
+        c = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(c)));
+    } else {
+        a = warp_max(a); b = warp_max(b); c = warp_max(c);
+    }
+    d = warp_sum(d);
     T *r = red + phase * 4 * kWarps;
     if (lane == 0) { r[warp] = a; r[kWarps + warp] = b; r[2 * kWarps + warp] = c; r[3 * kWarps + warp] = d; }
     g.sync();
@@ -399,9 +409,9 @@ __device__ void sweep_inverse(T *A, int mp, T *X, bool tc, const Group &g) {
     const int nrb = (mp + 31) / 32;      // 32-row blocks
     const int ncb = mp / 16 + (mp % 16 ? 1 : 0);
     for (int k0 = 0; k0 < mp; k0 += NB) {
-        for (int e = tid; e < NB * mp; e += nthr) {
-            const int u = e / mp, i = e - u * mp;
-            PT[u * ld + i] = A[sidx(i, k0 + u, mp)];
+        for (int i = tid; i < mp; i += nthr) {
+#pragma unroll
+            for (int u = 0; u < NB; ++u) PT[u * ld + i] = A[sidx(i, k0 + u, mp)];
         }
         g.sync();
         // -- pivot block inverse by an unblocked sweep on one warp, in registers: lane l holds row
@@ -433,14 +443,20 @@ __device__ void sweep_inverse(T *A, int mp, T *X, bool tc, const Group &g) {
         }
         g.sync();
         // -- TT[t][i] = sum_u P(i, u) Dinv(u, t) for rows outside K (zero on K)
-        for (int e = tid; e < NB * mp; e += nthr) {
-            const int t = e / mp, i = e - t * mp;
-            T acc = T(0);
+        for (int i = tid; i < mp; i += nthr) {
+            T acc[NB];
+#pragma unroll
+            for (int t = 0; t < NB; ++t) acc[t] = T(0);
             if (i < k0 || i >= k0 + NB) {
 #pragma unroll
-                for (int u = 0; u < NB; ++u) acc = fma(PT[u * ld + i], Dm[u * NB + t], acc);
+                for (int u = 0; u < NB; ++u) {
+                    const T pv = PT[u * ld + i];
+#pragma unroll
+                    for (int t = 0; t < NB; ++t) acc[t] = fma(pv, Dm[u * NB + t], acc[t]);
+                }
             }
-            TT[t * ld + i] = acc;
+#pragma unroll
+            for (int t = 0; t < NB; ++t) TT[t * ld + i] = acc[t];
         }
         g.sync();
         // -- rank-NB update of the lower triangle outside K: strips (row block R, column block C)
@@ -484,17 +500,39 @@ __device__ void sweep_inverse(T *A, int mp, T *X, bool tc, const Group &g) {
 #pragma unroll
                                 for (int nt = 0; nt < 2; ++nt) mma_tf32(acc[mt][nt], af[mt], bf[nt][0], bf[nt][1]);
                         }
-#pragma unroll
-                        for (int mt = 0; mt < 2; ++mt)
+                        const int r0 = 32 * R, c0 = 16 * C;
+                        const bool plain = r0 >= c0 + 15 && r0 + 31 < mp && (r0 >= k0 + NB || r0 + 31 < k0) &&
+                                           (c0 >= k0 + NB || c0 + 15 < k0);
+                        if (plain) {
+                            // every (i, j) of the strip is a lower-triangle element outside K
+                            int cs[2][2];
 #pragma unroll
                             for (int nt = 0; nt < 2; ++nt)
 #pragma unroll
-                                for (int e = 0; e < 4; ++e) {
-                                    const int i = 32 * R + 16 * mt + gq + (e >> 1) * 8;
-                                    const int j = 16 * C + 8 * nt + 2 * tq + (e & 1);
-                                    if (i < mp && j <= i && (i < k0 || i >= k0 + NB) && (j < k0 || j >= k0 + NB))
-                                        A[col_start(j, mp) + i - j] -= acc[mt][nt][e];
+                                for (int b = 0; b < 2; ++b) {
+                                    const int j = c0 + 8 * nt + 2 * tq + b;
+                                    cs[nt][b] = col_start(j, mp) - j;
                                 }
+#pragma unroll
+                            for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                                for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+                                    for (int e = 0; e < 4; ++e)
+                                        A[cs[nt][e & 1] + r0 + 16 * mt + gq + (e >> 1) * 8] -= acc[mt][nt][e];
+                        } else {
+#pragma unroll
+                            for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                                for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+                                    for (int e = 0; e < 4; ++e) {
+                                        const int i = r0 + 16 * mt + gq + (e >> 1) * 8;
+                                        const int j = c0 + 8 * nt + 2 * tq + (e & 1);
+                                        if (i < mp && j <= i && (i < k0 || i >= k0 + NB) && (j < k0 || j >= k0 + NB))
+                                            A[col_start(j, mp) + i - j] -= acc[mt][nt][e];
+                                    }
+                        }
                         continue;
                     }
                 }
@@ -525,13 +563,15 @@ __device__ void sweep_inverse(T *A, int mp, T *X, bool tc, const Group &g) {
         }
         g.sync();
         // -- write back the swept panel
-        for (int e = tid; e < NB * mp; e += nthr) {
-            const int t = e / mp, i = e - t * mp;
-            const int j = k0 + t;
-            if (i >= k0 && i < k0 + NB) {
-                if (i >= j) A[pidx(i, j, mp)] = -Dm[(i - k0) * NB + t];
-            } else {
-                A[sidx(i, j, mp)] = TT[t * ld + i];
+        for (int i = tid; i < mp; i += nthr) {
+#pragma unroll
+            for (int t = 0; t < NB; ++t) {
+                const int j = k0 + t;
+                if (i >= k0 && i < k0 + NB) {
+                    if (i >= j) A[pidx(i, j, mp)] = -Dm[(i - k0) * NB + t];
+                } else {
+                    A[sidx(i, j, mp)] = TT[t * ld + i];
+                }
             }
         }
         g.sync();
@@ -556,6 +596,7 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
     T *vf = (T *)(smem + L.vf), *p = (T *)(smem + L.p), *x = (T *)(smem + L.x), *xn = (T *)(smem + L.xn);
     T *y = (T *)(smem + L.y), *z = (T *)(smem + L.z), *yh = (T *)(smem + L.yh), *zh = (T *)(smem + L.zh);
     T *bb = (T *)(smem + L.b), *mut = (T *)(smem + L.mut), *X = (T *)(smem + L.X), *A = (T *)(smem + L.A);
+    T *mui = (T *)(smem + L.mui);
     T *red = (T *)(smem + L.red);
     int *misc = (int *)(smem + L.misc);
     T *wv = (T *)(smem + L.wv), *fb = (T *)(smem + L.fb);
@@ -716,6 +757,7 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
     for (int k = tid; k < nact; k += nthr) {
         const int rt = nbil + 3 * k;
         mut[k] = M.world_mu[w] * p[rt + 2] / p[rt];
+        mui[k] = T(1) / (T(1) + mut[k] * mut[k]);
     }
     // ---- 5c. A = P D P + (eta + rho) I in packed storage (identity on the padding rows)
     const T shift = a.eta + a.rho;
@@ -983,7 +1025,7 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
                 } else if (mu * tn <= -v[2]) {
                     yv[0] = yv[1] = yv[2] = T(0);
                 } else {
-                    const T nn = (mu * tn + v[2]) / (T(1) + mu * mu);
+                    const T nn = (mu * tn + v[2]) * mui[k];
                     const T sc = mu * nn / tn;
                     yv[0] = sc * v[0]; yv[1] = sc * v[1]; yv[2] = nn;
                 }
