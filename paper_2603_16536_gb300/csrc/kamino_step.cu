@@ -579,7 +579,8 @@ __device__ void sweep_inverse(T *A, int mp, T *X, bool tc, const Group &g) {
 }
 
 // ----------------------------------------------------------------------------- the step kernel
-template <typename T, int NB>
+// S: PADMM units per thread (units <= S * group size).
+template <typename T, int NB, int S>
 __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, const Group &g) {
     const int tid = g.tid, lane = g.lane(), warp = g.warp(), nthr = g.size, nwarps = g.warps();
     const ModelView<T> &M = a.m;
@@ -945,7 +946,7 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
         // [8b] owners: c_r = b_r + p_r J_r (g_A, g_B) + (eta + rho) x_r for the rows of their units,
         // stored as the BF16 hi / lo split (mixed) or in bb (FP32 / FP64 mat-vec)
 #pragma unroll
-        for (int sl = 0; sl < kSlots; ++sl) {
+        for (int sl = 0; sl < S; ++sl) {
             const int u = tid + sl * nthr;
             if (u >= nunits) continue;
             const int r0 = u < nbil ? u : nbil + 3 * (u - nbil);
@@ -995,9 +996,13 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
         // [8d] owners: x^i, y^i = Pi_K(x^i - z^/rho), z^i = z^ - rho (x^i - y^i), residual terms; x and
         // P x go to shared memory at once (the reduction's barrier publishes them for [8a])
         T lrp = T(0), lrd = T(0), lrc = T(0), lc = T(0);
-        T xnew[kSlots][3], ynew[kSlots][3], znew[kSlots][3];   // units tid + s * group size
+        T xnew[S][3], ynew[S][3], znew[S][3];   // units tid + s * group size
 #pragma unroll
-        for (int sl = 0; sl < kSlots; ++sl) {
+        for (int sl = 0; sl < S; ++sl)
+#pragma unroll
+            for (int t = 0; t < 3; ++t) xnew[sl][t] = ynew[sl][t] = znew[sl][t] = T(0);
+#pragma unroll
+        for (int sl = 0; sl < S; ++sl) {
             const int u = tid + sl * nthr;
             if (u >= nunits) continue;
             if (u < nbil) {
@@ -1068,38 +1073,51 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
             }
         }
 #pragma unroll
-        for (int sl = 0; sl < kSlots; ++sl) {
+        for (int sl = 0; sl < S; ++sl) {
             const int u = tid + sl * nthr;
             if (u >= nunits) continue;
             const int r0 = u < nbil ? u : nbil + 3 * (u - nbil);
             const int cnt = u < nbil ? 1 : 3;
+            // all loads first and every new value kept in registers: the vectors share one
+            // shared-memory buffer, so a value stored and read back would wait for the store
+            T yo[3], zo[3], vr[3], yhv[3], zhv[3];
+#pragma unroll
+            for (int t = 0; t < 3; ++t) {
+                const bool on = t < cnt;
+                yo[t] = on ? y[r0 + t] : T(0);
+                zo[t] = on ? z[r0 + t] : T(0);
+                vr[t] = on ? vf[r0 + t] : T(0);
+            }
+            const T mu = cnt == 3 ? mut[u - nbil] : T(0);
+#pragma unroll
+            for (int t = 0; t < 3; ++t) {
+                const T yv = ynew[sl][t], zv = znew[sl][t];
+                if (!a.nesterov) { yhv[t] = yv; zhv[t] = zv; }
+                else if (restart) { yhv[t] = yo[t]; zhv[t] = zo[t]; }
+                else { yhv[t] = yv + beta_n * (yv - yo[t]); zhv[t] = zv + beta_n * (zv - zo[t]); }
+            }
 #pragma unroll
             for (int t = 0; t < 3; ++t) {
                 if (t >= cnt) break;
                 const int r = r0 + t;
-                const T yv = ynew[sl][t], zv = znew[sl][t];
-                if (!a.nesterov) { yh[r] = yv; zh[r] = zv; }
-                else if (restart) { yh[r] = y[r]; zh[r] = z[r]; }
-                else { yh[r] = yv + beta_n * (yv - y[r]); zh[r] = zv + beta_n * (zv - z[r]); }
-                y[r] = yv; z[r] = zv;
+                yh[r] = yhv[t]; zh[r] = zhv[t];
+                y[r] = ynew[sl][t]; z[r] = znew[sl][t];
             }
             if (hp) {
-                const double z0 = zh[r0], z1 = cnt == 3 ? (double)zh[r0 + 1] : 0.0;
-                const double s = cnt == 3 ? (double)mut[u - nbil] * sqrt(z0 * z0 + z1 * z1) : 0.0;
+                const double z0 = zhv[0], z1 = zhv[1];
+                const double sd = cnt == 3 ? (double)mu * sqrt(z0 * z0 + z1 * z1) : 0.0;
 #pragma unroll
                 for (int t = 0; t < 3; ++t) {
                     if (t >= cnt) break;
-                    const int r = r0 + t;
-                    bbd[r] = (double)vf[r] + (t == 2 ? s : 0.0) - (double)eta * (double)xnew[sl][t] -
-                             (double)rho * (double)yh[r] - (double)zh[r];
+                    bbd[r0 + t] = (double)vr[t] + (t == 2 ? sd : 0.0) - (double)eta * (double)xnew[sl][t] -
+                                  (double)rho * (double)yhv[t] - (double)zhv[t];
                 }
             } else {
-                const T s = cnt == 3 ? mut[u - nbil] * sqrt(zh[r0] * zh[r0] + zh[r0 + 1] * zh[r0 + 1]) : T(0);
+                const T sv = cnt == 3 ? mu * sqrt(zhv[0] * zhv[0] + zhv[1] * zhv[1]) : T(0);
 #pragma unroll
                 for (int t = 0; t < 3; ++t) {
                     if (t >= cnt) break;
-                    const int r = r0 + t;
-                    bb[r] = vf[r] + (t == 2 ? s : T(0)) - eta * xnew[sl][t] - rho * yh[r] - zh[r];
+                    bb[r0 + t] = vr[t] + (t == 2 ? sv : T(0)) - eta * xnew[sl][t] - rho * yhv[t] - zhv[t];
                 }
             }
         }
@@ -1178,13 +1196,14 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
 }
 
 
-// One world per CTA (256 threads), grid = number of worlds (or of entries in a.world_order).
-template <typename T, int NB>
+// One world per CTA (256 threads), grid = number of worlds (or of entries in a.world_order); S = 1
+// when every world has at most 256 PADMM units, else 2 (rows <= kMaxRowsPad = 288).
+template <typename T, int NB, int S>
 __global__ void __launch_bounds__(kThreads, 1) step_kernel(const StepArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int w = a.world_order ? a.world_order[blockIdx.x] : (int)blockIdx.x;
     const Group g{(int)threadIdx.x, kThreads, 0};
-    world_step<T, NB>(a, w, smem, g);
+    world_step<T, NB, S>(a, w, smem, g);
 }
 
 // Persistent launch over a list of worlds: the CTA is split into groups of `group` threads, each
@@ -1204,7 +1223,7 @@ __global__ void __launch_bounds__(kThreads, 1) step_persistent(const StepArgs<T>
         const int idx = *slot;
         g.sync();
         if (idx >= p.count) break;
-        world_step<T, NB>(a, p.worlds[idx], slice, g);
+        world_step<T, NB, kSlots>(a, p.worlds[idx], slice, g);
         g.sync();
     }
 }
@@ -1213,18 +1232,29 @@ __global__ void __launch_bounds__(kThreads, 1) step_persistent(const StepArgs<T>
 
 template <typename T>
 cudaError_t prepare_step(int nb_panel, size_t smem) {
-    if (nb_panel == 16)
-        return cudaFuncSetAttribute(step_kernel<T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    return cudaFuncSetAttribute(step_kernel<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int b = (int)smem;
+    cudaError_t e;
+    if (nb_panel == 16) {
+        e = cudaFuncSetAttribute(step_kernel<T, 16, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(step_kernel<T, 16, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+        return e;
+    }
+    e = cudaFuncSetAttribute(step_kernel<T, 8, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(step_kernel<T, 8, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    return e;
 }
 
 template <typename T>
 cudaError_t launch_step(const StepArgs<T> &args, int num_worlds, int nb_panel, size_t smem, cudaStream_t stream) {
     if (num_worlds <= 0) return cudaSuccess;
-    if (nb_panel == 16)
-        step_kernel<T, 16><<<num_worlds, kThreads, smem, stream>>>(args);
-    else
-        step_kernel<T, 8><<<num_worlds, kThreads, smem, stream>>>(args);
+    const bool one = args.mp_max <= kThreads;     // units <= rows <= mp_max
+    if (nb_panel == 16) {
+        if (one) step_kernel<T, 16, 1><<<num_worlds, kThreads, smem, stream>>>(args);
+        else step_kernel<T, 16, 2><<<num_worlds, kThreads, smem, stream>>>(args);
+    } else {
+        if (one) step_kernel<T, 8, 1><<<num_worlds, kThreads, smem, stream>>>(args);
+        else step_kernel<T, 8, 2><<<num_worlds, kThreads, smem, stream>>>(args);
+    }
     return cudaGetLastError();
 }
 
