@@ -297,6 +297,9 @@ StepArgs<T> make_args(kamino_state_s *st, double dt, int iters, double tol, cons
     a.precond = m->params.precond ? 1 : 0;
     a.mixed = m->precision == KAMINO_MIXED ? 1 : 0;
     a.refine64 = m->params.refine64 ? 1 : 0;
+    // the inverse may live in tensor memory when a world's shared memory keeps a second CTA off the SM
+    // (the 512-column allocation then never waits for another CTA)
+    a.tmem = (sizeof(T) == 4 && m->mp_max <= 256 && m->smem > kMaxSmem / 2) ? 1 : 0;
     a.warm_mode = m->params.warm_mode;
     a.nb_max = m->nb_max;
     a.nj_max = m->nj_max;
@@ -319,6 +322,7 @@ kamino_status launch_bucket(kamino_state_s *st, const StepArgs<T> &base, int bi,
     a.nj_max = b.nj;
     a.nc_max = b.nc;
     a.mp_max = std::max(((b.rows + 15) / 16) * 16, 16);
+    a.tmem = 0;                   // groups share the CTA: no tensor memory
     PersistentArgs p{};
     p.worlds = b.d_worlds;
     p.count = b.count;

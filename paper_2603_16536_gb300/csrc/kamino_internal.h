@@ -54,6 +54,7 @@ struct StepArgs {
     int iters, nesterov, precond, warm_mode;
     int mixed;                 // 1: BF16 tiles of the inverse on tensor cores (KAMINO_MIXED)
     int refine64;              // 1: FP64 right-hand side and refinement residual near convergence
+    int tmem;                  // 1: keep the swept inverse in tensor memory (FP32, whole-CTA groups, mp <= 256)
     // shared-memory layout bounds (maxima over the launched worlds)
     int nb_max, nj_max, nc_max, mp_max;
 };

@@ -389,6 +389,89 @@ __device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], 
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
+// ----------------------------------------------------------------------------- tensor memory
+// The swept inverse can live in tensor memory (TMEM, 512 columns x 128 lanes of 32 bits per SM)
+// for the whole PADMM loop: row r of S = -A^-1 sits in lane r mod 128 of chunk r / 128, chunk ch at
+// columns 256 ch ... 256 ch + mp - 1 (FP32, mp <= 256).  Warp w may only touch lanes
+// 32 (w mod 4) ... + 31, so warps 0-3 own chunk 0 and warps 4-7 chunk 1; every warp reads back
+// exactly the rows it wrote.  Used only by the one-world-per-CTA kernel when the world's shared
+// memory keeps a second CTA off the SM, so the allocation never waits for another CTA.
+constexpr int kTmemCols = 512;
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void tmem_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tmem_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tmem_st16(uint32_t t, const uint32_t (&v)[16]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};"
+                 :: "r"(t), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]),
+                    "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t t, uint32_t (&v)[16]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                   "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+                 : "r"(t) : "memory");
+}
+
+// Rows of S (packed lower FP32 in shared memory) into tensor memory; zero beyond mp.
+__device__ void tmem_store_inverse(const float *A, int mp, uint32_t tbase, const Group &g) {
+    const int warp = g.warp(), lane = g.lane();
+    const int ch = warp >> 2;
+    const int row = 128 * ch + 32 * (warp & 3) + lane;
+    if (128 * ch < mp) {
+        const uint32_t t = tbase + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(256 * ch);
+        for (int j0 = 0; j0 < mp; j0 += 16) {
+            uint32_t v[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) v[q] = __float_as_uint(row < mp ? A[sidx(row, j0 + q, mp)] : 0.0f);
+            tmem_st16(t + (uint32_t)j0, v);
+        }
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    }
+}
+
+// y = S c with S in tensor memory: lane = row, 16 columns per load (the next load in flight while
+// the current one is used), c broadcast from shared memory, four FP32 partial sums.
+__device__ __forceinline__ void fma16(const uint32_t (&v)[16], const float *c, float &a0, float &a1, float &a2,
+                                      float &a3) {
+    const float4 *cp = reinterpret_cast<const float4 *>(c);
+#pragma unroll
+    for (int q = 0; q < 16; q += 4) {
+        const float4 cc = cp[q / 4];
+        a0 = fmaf(__uint_as_float(v[q]), cc.x, a0);
+        a1 = fmaf(__uint_as_float(v[q + 1]), cc.y, a1);
+        a2 = fmaf(__uint_as_float(v[q + 2]), cc.z, a2);
+        a3 = fmaf(__uint_as_float(v[q + 3]), cc.w, a3);
+    }
+}
+
+__device__ void tmem_matvec(uint32_t tbase, int mp, const float *c, float *y, const Group &g) {
+    const int warp = g.warp(), lane = g.lane();
+    const int ch = warp >> 2;
+    const int row = 128 * ch + 32 * (warp & 3) + lane;
+    if (128 * ch < mp) {
+        const uint32_t t = tbase + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(256 * ch);
+        const int nblk = mp / 16;
+        float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
+        uint32_t v0[16], v1[16];
+        tmem_ld16(t, v0);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        for (int b = 0; b < nblk; b += 2) {
+            if (b + 1 < nblk) tmem_ld16(t + (uint32_t)(16 * (b + 1)), v1);
+            fma16(v0, c + 16 * b, a0, a1, a2, a3);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (b + 1 < nblk) {
+                if (b + 2 < nblk) tmem_ld16(t + (uint32_t)(16 * (b + 2)), v0);
+                fma16(v1, c + 16 * (b + 1), a0, a1, a2, a3);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            }
+        }
+        if (row < mp) y[row] = (a0 + a1) + (a2 + a3);
+    }
+    g.sync();
+}
+
 // In-place blocked sweep of a symmetric positive definite matrix in packed lower storage:
 // sweeping every pivot turns A into -A^-1.  Per panel K of NB columns: PT = A(:, K)^T, the NB x NB
 // pivot block inverted by an unblocked sweep on one warp, TT = (A(:, K) A_KK^-1)^T, the rank-NB
@@ -605,6 +688,22 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
     const T dt = a.dt, kbias = a.beta / a.dt;
     const double dtd = (double)a.dt, kbiasd = (double)a.beta / (double)a.dt;
     if (tid == 0) misc[1] = 0;   // non-finite flag of this world
+    // tensor memory for the inverse (whole CTA only; released at the end of the world)
+    const bool tm_cta = sizeof(T) == 4 && a.tmem && nthr == kThreads && g.bar == 0;
+    uint32_t tbase = 0;
+    if constexpr (sizeof(T) == 4) {
+        if (tm_cta) {
+            if (warp == 0) {
+                asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                             :: "r"(smem_addr(misc + 2)), "r"(kTmemCols) : "memory");
+                asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+            }
+            tmem_fence_before();
+            g.sync();
+            tmem_fence_after();
+            tbase = (uint32_t)misc[2];
+        }
+    }
 
     // ---- 1. body kinematics
     for (int i = tid; i < nb; i += nthr) {
@@ -826,7 +925,11 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
     // ---- 7. A <- -A^-1 (blocked sweep), re-stored as BF16 tiles; per-body row lists for the
     // matrix-free products
     sweep_inverse<T, NB>(A, mp, X, a.mixed != 0, g);
-    if (a.mixed) pack_bf16_tiles(A, mp, X, g);
+    const bool tm = tm_cta && mp <= 256;
+    if constexpr (sizeof(T) == 4) {
+        if (tm) tmem_store_inverse(A, mp, tbase, g);
+    }
+    if (a.mixed && !tm) pack_bf16_tiles(A, mp, X, g);
     for (int i = tid; i < nb; i += nthr) {
         int cnt = 0;
         for (int r = 0; r < m; ++r) cnt += (rbody[2 * r] == i) + (rbody[2 * r + 1] == i);
@@ -886,7 +989,7 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
             }
         }
     }
-    if (a.mixed) {
+    if (a.mixed && !tm) {
         for (int r = m + tid; r < mp; r += nthr) {
             chi[r] = __float2bfloat16(0.0f);
             clo[r] = __float2bfloat16(0.0f);
@@ -979,7 +1082,7 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
                     }
                     c = bb[r] + p[r] * acc + shift * x[r];
                 }
-                if (a.mixed) {
+                if (a.mixed && !tm) {
                     const float v = (float)c;
                     const __nv_bfloat16 h = __float2bfloat16(v);
                     chi[r] = h;
@@ -991,8 +1094,14 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
         }
         g.sync();
         // [8c] correction: xn = S c with S = -A^-1, so x^i = x^{i-1} + xn (ends with a barrier)
-        if (a.mixed) apply_bf16_tiles(A, mp, chi, clo, xn, g);
-        else symv_packed(A, mp, bb, xn, X, g);
+        bool done_c = false;
+        if constexpr (sizeof(T) == 4) {
+            if (tm) { tmem_matvec(tbase, mp, bb, xn, g); done_c = true; }
+        }
+        if (!done_c) {
+            if (a.mixed) apply_bf16_tiles(A, mp, chi, clo, xn, g);
+            else symv_packed(A, mp, bb, xn, X, g);
+        }
         // [8d] owners: x^i, y^i = Pi_K(x^i - z^/rho), z^i = z^ - rho (x^i - y^i), residual terms; x and
         // P x go to shared memory at once (the reduction's barrier publishes them for [8a])
         T lrp = T(0), lrd = T(0), lrc = T(0), lc = T(0);
@@ -1192,6 +1301,16 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
         rep.r_compl = (float)rc;
         rep.reserved = 0.0f;
         a.res[w] = rep;
+    }
+    if constexpr (sizeof(T) == 4) {
+        if (tm_cta) {
+            tmem_fence_before();
+            g.sync();
+            if (warp == 0) {
+                tmem_fence_after();
+                asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tbase), "r"(kTmemCols) : "memory");
+            }
+        }
     }
 }
 
