@@ -206,7 +206,9 @@ kamino_status kamino_step(kamino_state_t state, double dt, int32_t iters, double
 kamino_status kamino_residuals(kamino_state_t state, kamino_residual *out_dev, void *stream);
 
 /* ---- Heterogeneous worlds (Sec. 5.2: worlds with different body and constraint counts in one
- * batch).  The model groups its worlds into size buckets by padded row count.  Two launch plans:
+ * batch).  The model groups its worlds into size buckets by padded row count.  Two launch plans
+ * (both keep the swept inverse of worlds of up to 256 padded rows in tensor memory when one
+ * 256-thread CTA runs one world at a time and fills the SM's shared memory):
  *   KAMINO_LAUNCH_SINGLE      one CTA of 256 threads per world, shared memory sized for the
  *                             largest world (default; best for homogeneous batches)
  *   KAMINO_LAUNCH_PERSISTENT  one persistent launch per bucket (grid = SMs x resident CTAs); each
@@ -233,8 +235,9 @@ kamino_status kamino_plan_get(kamino_model_t model, kamino_bucket_info *out, int
 /* Select KAMINO_LAUNCH_SINGLE or KAMINO_LAUNCH_PERSISTENT for subsequent steps and graphs. */
 kamino_status kamino_plan_set_mode(kamino_model_t model, int32_t mode);
 /* Autotuner: for every bucket, time each feasible (group size, panel width) on the state's own
- * worlds (the state is snapshotted and restored around every trial, so it is left unchanged),
- * keep the fastest, and switch the model to KAMINO_LAUNCH_PERSISTENT.  Synchronous. */
+ * worlds and keep the fastest; then time one whole step with the tuned persistent plan and with
+ * KAMINO_LAUNCH_SINGLE and switch the model to the faster.  The state is snapshotted and restored
+ * around every trial, so it is left unchanged.  Synchronous. */
 kamino_status kamino_autotune(kamino_state_t state, double dt, int32_t iters, double tol,
                               const void *tau_dev, void *stream);
 

@@ -322,7 +322,9 @@ kamino_status launch_bucket(kamino_state_s *st, const StepArgs<T> &base, int bi,
     a.nj_max = b.nj;
     a.nc_max = b.nc;
     a.mp_max = std::max(((b.rows + 15) / 16) * 16, 16);
-    a.tmem = 0;                   // groups share the CTA: no tensor memory
+    // tensor memory when one 256-thread group fills the CTA and its shared memory keeps a second
+    // CTA off the SM
+    a.tmem = (sizeof(T) == 4 && b.group == kThreads && a.mp_max <= 256 && b.smem > kMaxSmem / 2) ? 1 : 0;
     PersistentArgs p{};
     p.worlds = b.d_worlds;
     p.count = b.count;
@@ -414,6 +416,22 @@ kamino_status autotune(kamino_state_s *st, double dt, int iters, double tol, con
         b.grid = 0;
         b.tuned_ms = best;
     }
+    // whole step: the tuned persistent plan against one CTA per world, keep the faster
+    float t_mode[2] = {1e30f, 1e30f};
+    const int modes[2] = {KAMINO_LAUNCH_PERSISTENT, KAMINO_LAUNCH_SINGLE};
+    for (int mi = 0; mi < 2 && !s && e == cudaSuccess; ++mi) {
+        m->launch_mode = modes[mi];
+        for (int rep = 0; rep < 3 && !s; ++rep) {
+            cudaMemcpyAsync(st->base, snap, st->bytes, cudaMemcpyDeviceToDevice, stream);
+            cudaEventRecord(e0, stream);
+            s = do_step<T>(st, dt, iters, tol, tau, stream);
+            cudaEventRecord(e1, stream);
+            if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            t_mode[mi] = std::min(t_mode[mi], ms);
+        }
+    }
     if (e == cudaSuccess) e = cudaMemcpyAsync(st->base, snap, st->bytes, cudaMemcpyDeviceToDevice, stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
     cudaEventDestroy(e0);
@@ -421,7 +439,7 @@ kamino_status autotune(kamino_state_s *st, double dt, int iters, double tol, con
     cudaFree(snap);
     if (s) return s;
     if (e != cudaSuccess) return cuda_fail(e, "autotune");
-    m->launch_mode = KAMINO_LAUNCH_PERSISTENT;
+    m->launch_mode = t_mode[1] < t_mode[0] ? KAMINO_LAUNCH_SINGLE : KAMINO_LAUNCH_PERSISTENT;
     return KAMINO_OK;
 }
 

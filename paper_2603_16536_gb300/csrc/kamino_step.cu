@@ -662,9 +662,12 @@ __device__ void sweep_inverse(T *A, int mp, T *X, bool tc, const Group &g) {
 }
 
 // ----------------------------------------------------------------------------- the step kernel
-// S: PADMM units per thread (units <= S * group size).
+// S: PADMM units per thread (units <= S * group size).  tbase: tensor-memory columns of the CTA
+// (tm_cta: allocated by the kernel, whole-CTA group) that hold the inverse of worlds of up to 256
+// padded rows.
 template <typename T, int NB, int S>
-__device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, const Group &g) {
+__device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, const Group &g, uint32_t tbase,
+                           bool tm_cta) {
     const int tid = g.tid, lane = g.lane(), warp = g.warp(), nthr = g.size, nwarps = g.warps();
     const ModelView<T> &M = a.m;
     const int4 wa = M.world_a[w], wb = M.world_b[w];
@@ -688,23 +691,6 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
     const T dt = a.dt, kbias = a.beta / a.dt;
     const double dtd = (double)a.dt, kbiasd = (double)a.beta / (double)a.dt;
     if (tid == 0) misc[1] = 0;   // non-finite flag of this world
-    // tensor memory for the inverse (whole CTA only; released at the end of the world)
-    const bool tm_cta = sizeof(T) == 4 && a.tmem && nthr == kThreads && g.bar == 0;
-    uint32_t tbase = 0;
-    if constexpr (sizeof(T) == 4) {
-        if (tm_cta) {
-            if (warp == 0) {
-                asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                             :: "r"(smem_addr(misc + 2)), "r"(kTmemCols) : "memory");
-                asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-            }
-            tmem_fence_before();
-            g.sync();
-            tmem_fence_after();
-            tbase = (uint32_t)misc[2];
-        }
-    }
-
     // ---- 1. body kinematics
     for (int i = tid; i < nb; i += nthr) {
         const T *gq = a.body_q + 7 * (size_t)(b0 + i);
@@ -1302,27 +1288,50 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
         rep.reserved = 0.0f;
         a.res[w] = rep;
     }
-    if constexpr (sizeof(T) == 4) {
-        if (tm_cta) {
-            tmem_fence_before();
-            g.sync();
-            if (warp == 0) {
-                tmem_fence_after();
-                asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tbase), "r"(kTmemCols) : "memory");
-            }
-        }
-    }
 }
 
 
 // One world per CTA (256 threads), grid = number of worlds (or of entries in a.world_order); S = 1
 // when every world has at most 256 PADMM units, else 2 (rows <= kMaxRowsPad = 288).
+// Tensor-memory columns for the CTA (a.tmem: FP32, and the host guarantees one CTA per SM, so the
+// allocation never waits); the address goes through the word misc[2] of the world layout.
+template <typename T, int NB>
+__device__ __forceinline__ uint32_t cta_tmem_alloc(const StepArgs<T> &a, unsigned char *smem) {
+    uint32_t tbase = 0;
+    if constexpr (sizeof(T) == 4) {
+        const Layout L = make_layout<T>(a.nb_max, a.nj_max, a.nc_max, a.mp_max, NB);
+        int *slot = (int *)(smem + L.misc) + 2;
+        if (threadIdx.x < 32) {
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                         :: "r"(smem_addr(slot)), "r"(kTmemCols) : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        }
+        tmem_fence_before();
+        __syncthreads();
+        tmem_fence_after();
+        tbase = (uint32_t)*slot;
+        __syncthreads();                 // every thread has read the address before a world reuses the word
+    }
+    return tbase;
+}
+__device__ __forceinline__ void cta_tmem_free(uint32_t tbase) {
+    tmem_fence_before();
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        tmem_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tbase), "r"(kTmemCols) : "memory");
+    }
+}
+
 template <typename T, int NB, int S>
 __global__ void __launch_bounds__(kThreads, 1) step_kernel(const StepArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int w = a.world_order ? a.world_order[blockIdx.x] : (int)blockIdx.x;
     const Group g{(int)threadIdx.x, kThreads, 0};
-    world_step<T, NB, S>(a, w, smem, g);
+    const bool tm = sizeof(T) == 4 && a.tmem;
+    const uint32_t tbase = tm ? cta_tmem_alloc<T, NB>(a, smem) : 0u;
+    world_step<T, NB, S>(a, w, smem, g, tbase, tm);
+    if (tm) cta_tmem_free(tbase);
 }
 
 // Persistent launch over a list of worlds: the CTA is split into groups of `group` threads, each
@@ -1336,15 +1345,19 @@ __global__ void __launch_bounds__(kThreads, 1) step_persistent(const StepArgs<T>
     const Group g{(int)threadIdx.x - gi * p.group, p.group, ngroups > 1 ? 1 + gi : 0};
     unsigned char *slice = smem + (size_t)gi * p.slice_bytes;
     int *slot = (int *)(smem + (size_t)ngroups * p.slice_bytes) + gi;
+    // tensor memory only when one group fills the CTA (a.tmem is set by the host for such buckets)
+    const bool tm = sizeof(T) == 4 && a.tmem && ngroups == 1;
+    const uint32_t tbase = tm ? cta_tmem_alloc<T, NB>(a, smem) : 0u;
     for (int round = 0; round < p.count; ++round) {   // bounded: at most one world per round
         if (g.tid == 0) *slot = atomicAdd(p.counter, 1);
         g.sync();
         const int idx = *slot;
         g.sync();
         if (idx >= p.count) break;
-        world_step<T, NB, kSlots>(a, p.worlds[idx], slice, g);
+        world_step<T, NB, kSlots>(a, p.worlds[idx], slice, g, tbase, tm);
         g.sync();
     }
+    if (tm) cta_tmem_free(tbase);
 }
 
 }  // namespace
