@@ -252,8 +252,8 @@ kamino_status kamino_graph_destroy(kamino_graph_t graph);
 
 /* ---- Learned warm start (one MLP per world type): features of a world (per body the position
  * relative to the first body, quaternion and twist; the first body's height; the actuation; per
- * contact candidate the signed distance and terrain normal) -> initial impulses in the impulse-
- * cache layout.  L = 3 hidden layers of width `hidden`, GELU, BF16 weights and activations, FP32
+ * contact candidate the signed distance and terrain normal; the state's impulse cache, i.e. the
+ * previous step's solution) -> initial impulses in the impulse-cache layout.  L = 3 hidden layers of width `hidden`, GELU, BF16 weights and activations, FP32
  * accumulation on tensor cores (mma.sync m16n8k16), FP32 master weights and Adam.  Features and
  * targets are normalised per column (kamino_mlp_fit_normalization).  The network only supplies
  * the starting point of Alg. 1 (KAMINO_WARM_EXTERNAL); the solver's convergence test decides. */

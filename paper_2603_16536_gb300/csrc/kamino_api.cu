@@ -1038,8 +1038,8 @@ kamino_status kamino_mlp_create(kamino_model_t m, const int32_t *worlds, int32_t
     n->count = count;
     n->hidden = hidden;
     n->nact = m->n_act_max;
-    n->din = 13 * ref.x + 1 + n->nact + 4 * ref.z;
     n->dout = ref.w + 3 * ref.z;
+    n->din = 13 * ref.x + 1 + n->nact + 4 * ref.z + n->dout;   // ... + the previous step's impulses
     n->max_batch = std::max(max_batch, count);
     n->dims[0] = n->din;
     for (int l = 1; l <= kHiddenLayers; ++l) n->dims[l] = hidden;
@@ -1129,12 +1129,14 @@ kamino_status kamino_mlp_features(kamino_mlp_t n, kamino_state_t s, const void *
         kamino::mlp::FeatureArgs<double> a{};
         a.m = view<double>(n->model);
         a.q = (const double *)s->ptr(s->off_q); a.u = (const double *)s->ptr(s->off_u); a.tau = (const double *)tau;
+        a.cache = (const double *)s->ptr(s->off_cache); a.dout = n->dout;
         a.worlds = n->d_worlds; a.count = n->count; a.din = n->din; a.nact = n->nact; a.out = out;
         e = kamino::mlp::features<double>(a, (cudaStream_t)stream);
     } else {
         kamino::mlp::FeatureArgs<float> a{};
         a.m = view<float>(n->model);
         a.q = (const float *)s->ptr(s->off_q); a.u = (const float *)s->ptr(s->off_u); a.tau = (const float *)tau;
+        a.cache = (const float *)s->ptr(s->off_cache); a.dout = n->dout;
         a.worlds = n->d_worlds; a.count = n->count; a.din = n->din; a.nact = n->nact; a.out = out;
         e = kamino::mlp::features<float>(a, (cudaStream_t)stream);
     }

@@ -244,6 +244,9 @@ __global__ void features_kernel(const FeatureArgs<T> a) {
             const double phi = dev::terrain(a.m, p, n);
             v = comp == 0 ? (float)phi : (float)n[comp - 1];
         }
+    } else {
+        const int k = f - 13 * nb - 1 - a.nact - 4 * nc;    // impulse cache, joint rows then candidates
+        if (a.cache && k < a.dout) v = (float)a.cache[wa.w + k];
     }
     a.out[e] = v;
 }

@@ -31,8 +31,9 @@ template <typename T>
 struct FeatureArgs {
     ModelView<T> m;
     const T *q, *u, *tau;
+    const T *cache;                // the state's impulse cache (the previous step's solution)
     const int *worlds;
-    int count, din, nact;
+    int count, din, nact, dout;
     float *out;                    // [count][din]
 };
 

@@ -34,7 +34,7 @@ def test_mlp_forward_and_gradients_match_fp64_reference(K):
     model = K.Model(ws, "fp32", K.make_params())
     net = K.Mlp(model, np.arange(8), hidden=64, max_batch=256, seed=3)
     din, dout = net.info.d_in, net.info.d_out
-    assert (din, dout) == (13 * 31 + 1 + 12 + 4 * 16, 180 + 3 * 16)
+    assert (din, dout) == (13 * 31 + 1 + 12 + 4 * 16 + (180 + 3 * 16), 180 + 3 * 16)   # ... + the impulse cache
     rng = np.random.default_rng(0)
     B = 96
     X = rng.standard_normal((B, din)).astype(np.float32)
