@@ -182,6 +182,28 @@ def run_reference(args, rank, world):
     return 0
 
 
+# ----------------------------------------------------------------------------- ranks (weak scaling)
+# Every rank steps its own worlds (seed + rank): no data-path collective.  The only exchange is the
+# timing: the job's time is the slowest rank's, and the job's work is the sum over the ranks.
+def rank_seed(seed, rank):
+    return seed + rank
+
+
+def job_units(worlds_per_rank, steps, world):
+    return worlds_per_rank * steps * world
+
+
+def max_over_ranks(v, world, device):
+    """The largest of the ranks' values (every rank gets it); the identity on one rank."""
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ----------------------------------------------------------------------------- GPU arm
 def algorithmic_flops(rows, iters):
     """Flops of the method per world-step: dense Cholesky m^3/3, per PADMM iteration a forward and
@@ -266,7 +288,7 @@ def run_gpu(args, rank, world):
         if world > 1:
             dist.barrier()
 
-    seed = args.seed + rank
+    seed = rank_seed(args.seed, rank)
     ws, desc = build_workload(args, seed)
     W = ws.num_worlds
     stream = torch.cuda.current_stream()
@@ -375,11 +397,7 @@ def run_gpu(args, rank, world):
         return st, ms, np.concatenate(rows), np.concatenate(its), conv, ms_step
 
     def reduce_max(v):
-        if world == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return max_over_ranks(v, world, dev)
 
     sampler = ClockSampler(local)
     sampler.start()
@@ -390,7 +408,7 @@ def run_gpu(args, rank, world):
     if nets:
         results["mixed_learned_warm"] = run_variant("mixed_learned_warm", K.WARM_EXTERNAL, learned=True)
     clocks = sampler.stop()
-    units = W * args.steps * world
+    units = job_units(W, args.steps, world)
     variants = {}
     for name, (_, ms, rows, its, conv, _) in results.items():
         t = reduce_max(sum(ms) / 1e3)
