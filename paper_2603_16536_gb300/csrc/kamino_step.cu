@@ -661,6 +661,187 @@ __device__ void sweep_inverse(T *A, int mp, T *X, bool tc, const Group &g) {
     }
 }
 
+// ----------------------------------------------------------------------------- sweep in tensor memory
+// Mixed precision, panel width 16, worlds of up to 256 padded rows run by a whole CTA: the full
+// square matrix lives in tensor memory for the whole sweep (row r in lane r mod 128 of column block
+// 256 (r / 128), as the PADMM loop reads it afterwards), so the rank-16 update of every panel is
+// four tcgen05 TF32 products accumulated straight into it (M = 128 rows, N = mp, K = 8, two K
+// steps per row chunk) and no element is read back and rewritten by the lanes.  Per panel K:
+//   P = A(:, K) (tcgen05.ld of the column block, lane = row) into shared memory, K-major;
+//   A_KK^-1 in one warp's registers; T = P A_KK^-1, stored negated (zero on the rows of K);
+//   one thread issues D += (-T) P^T and commits to an mbarrier;
+//   column block K := T (A_KK^-1 on K), row block K := T^T (the warp that owns the lanes of K).
+// Both triangles are kept, so the panels are read without index mapping.  The operands' shared-
+// memory layout is the tensor cores' K-major one: 8-row x 16-byte core matrices, word (r, k) at
+// 128 (r / 8) + 32 (k / 4) + 4 (r mod 8) + k mod 4, rows padded with zeros to 256.
+__device__ __forceinline__ int kmaj(int r, int k) { return 128 * (r >> 3) + 32 * (k >> 2) + 4 * (r & 7) + (k & 3); }
+__device__ __forceinline__ uint64_t smem_desc_kmajor(uint32_t saddr) {
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);          // start address / 16
+    d |= (uint64_t)(128u >> 4) << 16;                           // K-direction core matrices 128 B apart
+    d |= (uint64_t)(512u >> 4) << 32;                           // 8-row groups 512 B apart
+    d |= (uint64_t)1 << 46;                                     // descriptor version (tcgen05), no swizzle
+    return d;
+}
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+    for (int n = 0; n < (1 << 22); ++n) {                       // bounded (~10 ms)
+        uint32_t ok;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}" : "=r"(ok) : "r"(mbar), "r"(parity) : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+__device__ void sweep_inverse_tmem(const float *A, int mp, float *X, uint32_t tbase, int *misc, const Group &g) {
+    constexpr int NB = 16;
+    float *PT = X;                 // K-major [256 rows][16]: the panel P
+    float *TN = X + 256 * 16;      // K-major [256 rows][16]: -T
+    float *Dm = X + 2 * 256 * 16;  // [16][16]: A_KK^-1
+    const int tid = g.tid, nthr = g.size, lane = g.lane(), warp = g.warp();
+    const int ch = warp >> 2, q = warp & 3;
+    const int row = 128 * ch + 32 * q + lane;                 // the matrix row of this lane
+    const bool has_rows = 128 * ch < mp;                        // warp-uniform
+    const uint32_t trow = tbase + ((uint32_t)(32 * q) << 16) + 256u * ch;
+    const uint32_t mbar = smem_addr(misc + 4);
+    const int nch = mp > 128 ? 2 : 1;
+    // the assembled matrix (packed lower, shared memory) into tensor memory, both triangles
+    if (has_rows) {
+        for (int j0 = 0; j0 < mp; j0 += 16) {
+            uint32_t v[16];
+#pragma unroll
+            for (int c = 0; c < 16; ++c) v[c] = __float_as_uint(row < mp ? A[sidx(row, j0 + c, mp)] : 0.0f);
+            tmem_st16(trow + (uint32_t)j0, v);
+        }
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    }
+    for (int e = tid; e < 2 * 256 * 16; e += nthr) X[e] = 0.0f;   // padding rows stay zero
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(mbar), "r"(1) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tmem_fence_before();
+    g.sync();
+    tmem_fence_after();
+    // kind::tf32: D F32 (bits 4-5 = 1), A and B TF32 (bits 7-9, 10-12 = 2), both K-major, N / 8 at
+    // bits 17-22, M / 16 at bits 24-28
+    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(mp >> 3) << 17) | ((128u >> 4) << 24);
+    int panel = 0;
+    for (int k0 = 0; k0 < mp; k0 += NB, ++panel) {
+        // -- P = A(:, K): column block K of every row
+        if (has_rows) {
+            uint32_t v[16];
+            tmem_ld16(trow + (uint32_t)k0, v);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (row < mp) {
+#pragma unroll
+                for (int c = 0; c < 16; c += 4)
+                    *reinterpret_cast<float4 *>(PT + kmaj(row, c)) =
+                        make_float4(__uint_as_float(v[c]), __uint_as_float(v[c + 1]), __uint_as_float(v[c + 2]),
+                                    __uint_as_float(v[c + 3]));
+            }
+        }
+        g.sync();
+        // -- A_KK^-1 by an unblocked sweep in one warp's registers (as in sweep_inverse)
+        if (warp == 0) {
+            constexpr int LR = 32 / NB, CPL = NB / LR;
+            const int ri = lane / LR, h = lane % LR;
+            float v[CPL];
+#pragma unroll
+            for (int c = 0; c < CPL; ++c) v[c] = PT[kmaj(k0 + ri, h * CPL + c)];
+#pragma unroll
+            for (int pv = 0; pv < NB; ++pv) {
+                const float d = __frcp_rn(__shfl_sync(0xffffffffu, v[pv % CPL], pv * LR + pv / CPL));
+                const float aip = __shfl_sync(0xffffffffu, v[pv % CPL], ri * LR + pv / CPL);
+                float apj[CPL];
+#pragma unroll
+                for (int c = 0; c < CPL; ++c) apj[c] = __shfl_sync(0xffffffffu, v[c], pv * LR + h);
+#pragma unroll
+                for (int c = 0; c < CPL; ++c) {
+                    const int j = h * CPL + c;
+                    if (ri == pv) v[c] = j == pv ? -d : apj[c] * d;
+                    else if (j == pv) v[c] = aip * d;
+                    else v[c] -= aip * apj[c] * d;
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < CPL; ++c) Dm[ri * NB + h * CPL + c] = -v[c];
+        }
+        g.sync();
+        // -- -T = -P A_KK^-1 outside K (zero on K)
+        for (int i = tid; i < mp; i += nthr) {
+            float acc[NB];
+#pragma unroll
+            for (int t = 0; t < NB; ++t) acc[t] = 0.0f;
+            if (i < k0 || i >= k0 + NB) {
+#pragma unroll
+                for (int u = 0; u < NB; ++u) {
+                    const float pv = PT[kmaj(i, u)];
+#pragma unroll
+                    for (int t = 0; t < NB; ++t) acc[t] = fmaf(pv, Dm[u * NB + t], acc[t]);
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < NB; t += 4)
+                *reinterpret_cast<float4 *>(TN + kmaj(i, t)) = make_float4(-acc[t], -acc[t + 1], -acc[t + 2], -acc[t + 3]);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // P and -T visible to the tensor cores
+        tmem_fence_before();
+        g.sync();
+        // -- A += (-T) P^T on the tensor cores, accumulated in place
+        if (tid == 0) {
+            tmem_fence_after();
+            for (int c = 0; c < nch; ++c)
+                for (int ks = 0; ks < 2; ++ks) {
+                    const uint64_t da = smem_desc_kmajor(smem_addr(TN) + 8192u * c + 256u * ks);
+                    const uint64_t db = smem_desc_kmajor(smem_addr(PT) + 256u * ks);
+                    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
+                                 :: "r"(tbase + 256u * c), "l"(da), "l"(db), "r"(idesc), "r"(1u) : "memory");
+                }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         :: "r"(mbar) : "memory");
+        }
+        bool ok = mbar_wait(mbar, (uint32_t)(panel & 1));
+        if (!ok) {
+            if (tid == 0) misc[1] = 1;                          // reported as a failed world
+            ok = mbar_wait(mbar, (uint32_t)(panel & 1));        // let the products finish before going on
+        }
+        tmem_fence_after();
+        // -- column block K := T on the rows outside K, A_KK^-1 negated on K (every warp, its rows)
+        if (has_rows) {
+            uint32_t v[16];
+            const bool inK = row >= k0 && row < k0 + NB;
+#pragma unroll
+            for (int c = 0; c < 16; ++c) {
+                float x = 0.0f;
+                if (row < mp) x = inK ? -Dm[(row - k0) * NB + c] : -TN[kmaj(row, c)];
+                v[c] = __float_as_uint(x);
+            }
+            tmem_st16(trow + (uint32_t)k0, v);
+        }
+        // -- row block K := T^T outside K (the warp that owns the lanes of K; they lie in one warp)
+        if (warp == 4 * (k0 >> 7) + ((k0 & 127) >> 5)) {
+            const int r0 = k0 - (128 * ch + 32 * q);             // first lane of K in this warp
+            const bool mine = lane >= r0 && lane < r0 + NB;
+            for (int j0 = 0; j0 < mp; j0 += 16) {
+                if (j0 == k0) continue;
+                uint32_t v[16];
+                tmem_ld16(trow + (uint32_t)j0, v);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (mine) {
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) v[c] = __float_as_uint(-TN[kmaj(j0 + c, lane - r0)]);
+                }
+                tmem_st16(trow + (uint32_t)j0, v);
+            }
+        }
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        tmem_fence_before();
+        g.sync();
+        tmem_fence_after();
+    }
+}
+
 // ----------------------------------------------------------------------------- the step kernel
 // S: PADMM units per thread (units <= S * group size).  tbase: tensor-memory columns of the CTA
 // (tm_cta: allocated by the kernel, whole-CTA group) that hold the inverse of worlds of up to 256
@@ -910,10 +1091,18 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
 
     // ---- 7. A <- -A^-1 (blocked sweep), re-stored as BF16 tiles; per-body row lists for the
     // matrix-free products
-    sweep_inverse<T, NB>(A, mp, X, a.mixed != 0, g);
     const bool tm = tm_cta && mp <= 256;
+    bool in_tmem = false;                 // the inverse is already in tensor memory
+    if constexpr (sizeof(T) == 4 && NB == 16) {
+        // the two K-major panels (256 rows x 16) and the pivot block must fit the scratch X
+        if (tm && a.mixed && L.A - L.X >= (size_t)(2 * 256 * 16 + 256) * sizeof(float)) {
+            sweep_inverse_tmem(A, mp, X, tbase, misc, g);
+            in_tmem = true;
+        }
+    }
+    if (!in_tmem) sweep_inverse<T, NB>(A, mp, X, a.mixed != 0, g);
     if constexpr (sizeof(T) == 4) {
-        if (tm) tmem_store_inverse(A, mp, tbase, g);
+        if (tm && !in_tmem) tmem_store_inverse(A, mp, tbase, g);
     }
     if (a.mixed && !tm) pack_bf16_tiles(A, mp, X, g);
     for (int i = tid; i < nb; i += nthr) {
