@@ -431,8 +431,8 @@ __device__ void tmem_store_inverse(const float *A, int mp, uint32_t tbase, const
     }
 }
 
-// y = S c with S in tensor memory: lane = row, 16 columns per load (the next load in flight while
-// the current one is used), c broadcast from shared memory, four FP32 partial sums.
+// y = S c with S in tensor memory: lane = row, 32 columns per load, c broadcast from shared memory,
+// four FP32 partial sums.
 __device__ __forceinline__ void fma16(const uint32_t (&v)[16], const float *c, float &a0, float &a1, float &a2,
                                       float &a3) {
     const float4 *cp = reinterpret_cast<const float4 *>(c);
@@ -446,26 +446,38 @@ __device__ __forceinline__ void fma16(const uint32_t (&v)[16], const float *c, f
     }
 }
 
+__device__ __forceinline__ void tmem_ld32(uint32_t t, uint32_t (&v)[32]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                   "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+                   "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+                   "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                 : "r"(t) : "memory");
+}
+
 __device__ void tmem_matvec(uint32_t tbase, int mp, const float *c, float *y, const Group &g) {
     const int warp = g.warp(), lane = g.lane();
     const int ch = warp >> 2;
     const int row = 128 * ch + 32 * (warp & 3) + lane;
     if (128 * ch < mp) {
         const uint32_t t = tbase + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(256 * ch);
-        const int nblk = mp / 16;
         float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
-        uint32_t v0[16], v1[16];
-        tmem_ld16(t, v0);
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        for (int b = 0; b < nblk; b += 2) {
-            if (b + 1 < nblk) tmem_ld16(t + (uint32_t)(16 * (b + 1)), v1);
-            fma16(v0, c + 16 * b, a0, a1, a2, a3);
+        int b = 0;
+        for (; b + 32 <= mp; b += 32) {                       // 32 columns per load
+            uint32_t v[32];
+            tmem_ld32(t + (uint32_t)b, v);
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (b + 1 < nblk) {
-                if (b + 2 < nblk) tmem_ld16(t + (uint32_t)(16 * (b + 2)), v0);
-                fma16(v1, c + 16 * (b + 1), a0, a1, a2, a3);
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            }
+            const uint32_t (&v0)[16] = *reinterpret_cast<const uint32_t (*)[16]>(&v[0]);
+            const uint32_t (&v1)[16] = *reinterpret_cast<const uint32_t (*)[16]>(&v[16]);
+            fma16(v0, c + b, a0, a1, a2, a3);
+            fma16(v1, c + b + 16, a0, a1, a2, a3);
+        }
+        if (b < mp) {                                          // mp = 16 mod 32
+            uint32_t v[16];
+            tmem_ld16(t + (uint32_t)b, v);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            fma16(v, c + b, a0, a1, a2, a3);
         }
         if (row < mp) y[row] = (a0 + a1) + (a2 + a3);
     }
@@ -1135,9 +1147,10 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
     // rounding of an FP32 residual of nearly cancelling terms.
     //
     // Unit u (a joint row, or the three rows of a contact) belongs to thread u mod group size for
-    // the whole solve: only its owner touches its b, y, z, y^, z^, so an iteration has four
-    // barriers (after the per-body gather, after the residual rows, after the mat-vec, and the
-    // residual reduction, which also publishes x and P x).
+    // the whole solve: only its owner writes its x, b, y, z, y^, z^ (the residual rows read x and b
+    // row by row after a barrier), so an iteration has four barriers (after the per-body gather,
+    // after the residual rows, after the mat-vec, and the residual reduction, which also publishes
+    // x, P x and b).
     const T eta = a.eta, rho = a.rho, irho = T(1) / a.rho;
     double *bbd = reinterpret_cast<double *>(X + kWarps * mp);   // FP32 worlds only (make_layout)
     double *gbd = bbd + mp;
@@ -1221,50 +1234,43 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
             }
         }
         g.sync();
-        // [8b] owners: c_r = b_r + p_r J_r (g_A, g_B) + (eta + rho) x_r for the rows of their units,
-        // stored as the BF16 hi / lo split (mixed) or in bb (FP32 / FP64 mat-vec)
+        // [8b] thread r: c_r = b_r + p_r J_r (g_A, g_B) + (eta + rho) x_r (b_r and x_r were written by
+        // the row's owner before the last barrier), stored as the BF16 hi / lo split (mixed, inverse
+        // in shared memory) or in bb (tensor-memory, FP32 and FP64 mat-vecs)
+        for (int r = tid; r < m; r += nthr) {
+            const int sa = rbody[2 * r], sb = rbody[2 * r + 1];
+            const T *J = rJ + 12 * r;
+            T c;
+            if (hp) {
+                double acc = 0.0;
+                if (sa >= 0) {
 #pragma unroll
-        for (int sl = 0; sl < S; ++sl) {
-            const int u = tid + sl * nthr;
-            if (u >= nunits) continue;
-            const int r0 = u < nbil ? u : nbil + 3 * (u - nbil);
-            const int cnt = u < nbil ? 1 : 3;
-            for (int t = 0; t < cnt; ++t) {
-                const int r = r0 + t;
-                const int sa = rbody[2 * r], sb = rbody[2 * r + 1];
-                const T *J = rJ + 12 * r;
-                T c;
-                if (hp) {
-                    double acc = 0.0;
-                    if (sa >= 0) {
-#pragma unroll
-                        for (int k = 0; k < 6; ++k) acc = fma((double)J[k], gbd[6 * sa + k], acc);
-                    }
-                    if (sb >= 0) {
-#pragma unroll
-                        for (int k = 0; k < 6; ++k) acc = fma((double)J[6 + k], gbd[6 * sb + k], acc);
-                    }
-                    c = T(bbd[r] + (double)p[r] * acc + (double)shift * (double)x[r]);
-                } else {
-                    T acc = T(0);
-                    if (sa >= 0) {
-#pragma unroll
-                        for (int k = 0; k < 6; ++k) acc = fma(J[k], fb[6 * sa + k], acc);
-                    }
-                    if (sb >= 0) {
-#pragma unroll
-                        for (int k = 0; k < 6; ++k) acc = fma(J[6 + k], fb[6 * sb + k], acc);
-                    }
-                    c = bb[r] + p[r] * acc + shift * x[r];
+                    for (int k = 0; k < 6; ++k) acc = fma((double)J[k], gbd[6 * sa + k], acc);
                 }
-                if (a.mixed && !tm) {
-                    const float v = (float)c;
-                    const __nv_bfloat16 h = __float2bfloat16(v);
-                    chi[r] = h;
-                    clo[r] = __float2bfloat16(v - __bfloat162float(h));
-                } else {
-                    bb[r] = c;
+                if (sb >= 0) {
+#pragma unroll
+                    for (int k = 0; k < 6; ++k) acc = fma((double)J[6 + k], gbd[6 * sb + k], acc);
                 }
+                c = T(bbd[r] + (double)p[r] * acc + (double)shift * (double)x[r]);
+            } else {
+                T acc = T(0);
+                if (sa >= 0) {
+#pragma unroll
+                    for (int k = 0; k < 6; ++k) acc = fma(J[k], fb[6 * sa + k], acc);
+                }
+                if (sb >= 0) {
+#pragma unroll
+                    for (int k = 0; k < 6; ++k) acc = fma(J[6 + k], fb[6 * sb + k], acc);
+                }
+                c = bb[r] + p[r] * acc + shift * x[r];
+            }
+            if (a.mixed && !tm) {
+                const float v = (float)c;
+                const __nv_bfloat16 h = __float2bfloat16(v);
+                chi[r] = h;
+                clo[r] = __float2bfloat16(v - __bfloat162float(h));
+            } else {
+                bb[r] = c;
             }
         }
         g.sync();
