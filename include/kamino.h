@@ -79,9 +79,10 @@ typedef struct {
     int32_t nesterov;  /* 1: Nesterov acceleration with adaptive restart (Sec. 4.1)         */
     int32_t precond;   /* 1: Jacobi preconditioning P = diag(D)^-1/2 (Sec. 4.1)              */
     int32_t warm_mode; /* KAMINO_WARM_*                                                       */
-    int32_t refine64;  /* 1: once r_p and r_d fall below KAMINO_REFINE64_BELOW, the right-hand
-                        * side and the refinement residual b + A x of every PADMM solve are formed
-                        * in FP64 (FP32 and MIXED precision; FP64 worlds always are).  0: FP32.  */
+    int32_t refine64;  /* 1: when tol < KAMINO_REFINE64_BELOW, once r_p and r_d fall below that
+                        * level the right-hand side and the refinement residual b + A x of every
+                        * PADMM solve are formed in FP64 (FP32 and MIXED precision; FP64 worlds
+                        * always are).  0: FP32 throughout.                                       */
 } kamino_solver_params;
 
 /* Scaled-unit residual level below which refine64 switches the refinement residual to FP64: the

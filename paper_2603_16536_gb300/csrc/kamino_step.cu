@@ -1155,7 +1155,9 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
     double *bbd = reinterpret_cast<double *>(X + kWarps * mp);   // FP32 worlds only (make_layout)
     double *gbd = bbd + mp;
     __nv_bfloat16 *chi = reinterpret_cast<__nv_bfloat16 *>(X), *clo = chi + mp;   // mixed: split c
-    const bool use64 = sizeof(T) == 4 && a.refine64;
+    // the FP64 end game only matters below the FP32 residual floor, i.e. for tolerances under the
+    // switch level
+    const bool use64 = sizeof(T) == 4 && a.refine64 && a.tol < T(KAMINO_REFINE64_BELOW);
     bool hp = false;     // b of the coming iteration is the FP64 one; set once, uniform over the group
     int LB = 8;          // lanes per body in the gather: a power of two with LB * nb <= group size
     while (LB > 1 && LB * nb > nthr) LB >>= 1;
