@@ -20,6 +20,8 @@ What it computes, in the paper's order (Kamino, arXiv 2603.16536):
                      the cached warm start.
 * ``audit``       -- independent checks: the direct KKT solve of Eq. 2 for bilateral-only worlds
                      and the natural-map NCP residual of a returned (lambda, u+).
+* ``mlp``         -- the warm-start network (3 GELU layers) forward, loss and backward in FP64,
+                     the reference for the GPU kernels' gradients.
 
 Parity status: every function is pinned by ``tests/test_oracle_*.py`` against closed forms,
 invariants or brute force; none is "parity unpinned".
