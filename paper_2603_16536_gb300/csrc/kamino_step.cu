@@ -1422,16 +1422,23 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
     // FP64 (once per step): u+ is a small difference of large joint impulses through light bodies,
     // and the pose update adds a small increment to the stored pose.
     for (int r = tid; r < m; r += nthr) xn[r] = p[r] * y[r];
+    // J^T lambda per (body, component), one thread each, into FP64 scratch (the per-body FP64
+    // velocities of the refinement for FP32 worlds, the per-body force words for FP64 worlds)
+    double *fd = sizeof(T) == 8 ? reinterpret_cast<double *>(fb) : gbd;
+    for (int t = tid; t < 6 * nb; t += nthr) {
+        const int i = t / 6, k = t - 6 * (t / 6);
+        double f = 0.0;
+        for (int e = bro[i]; e < bro[i + 1]; ++e) {
+            const int code = brow[e];
+            f = fma((double)rJ[6 * code + k], (double)p[code >> 1] * (double)y[code >> 1], f);   // 12 r + 6 side + k
+        }
+        fd[t] = f;
+    }
     g.sync();
     bool bad = false;
     for (int i = tid; i < nb; i += nthr) {
-        double f[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-        for (int e = bro[i]; e < bro[i + 1]; ++e) {
-            const int code = brow[e];
-            const double l = (double)p[code >> 1] * (double)y[code >> 1];
-            const T *J = rJ + 6 * code;                                 // 12 r + 6 side
-            for (int k = 0; k < 6; ++k) f[k] += (double)J[k] * l;
-        }
+        double f[6];
+        for (int k = 0; k < 6; ++k) f[k] = fd[6 * i + k];
         double up[6], dw[3];
         symvec3d(bIinv + 6 * i, f + 3, dw);
         for (int k = 0; k < 3; ++k) {
