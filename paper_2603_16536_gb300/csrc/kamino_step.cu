@@ -753,8 +753,29 @@ __device__ void sweep_inverse_tmem(const float *A, int mp, float *X, uint32_t tb
             }
         }
         g.sync();
-        // -- A_KK^-1 by an unblocked sweep in one warp's registers (as in sweep_inverse)
-        if (warp == 0) {
+        // -- A_KK^-1 by an unblocked sweep in one warp's registers (as in sweep_inverse), while the
+        // warp that owns the previous pivot rows writes the rest of their row block (deferred from
+        // the previous panel: -T of that panel is still in TN, and this panel's products, which
+        // touch every column, are issued only after the next barrier)
+        const int wprev = k0 > 0 ? 4 * ((k0 - NB) >> 7) + (((k0 - NB) & 127) >> 5) : -1;
+        if (k0 > 0 && warp == wprev) {
+            const int kp = k0 - NB;                                  // the previous panel
+            const int r0 = kp - (128 * ch + 32 * q);
+            const bool mine = lane >= r0 && lane < r0 + NB;
+            for (int j0 = 0; j0 < mp; j0 += 16) {
+                if (j0 == kp || j0 == k0) continue;                 // written with that panel / before
+                uint32_t v[16];
+                tmem_ld16(trow + (uint32_t)j0, v);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (mine) {
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) v[c] = __float_as_uint(-TN[kmaj(j0 + c, lane - r0)]);
+                }
+                tmem_st16(trow + (uint32_t)j0, v);
+            }
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        }
+        if (warp == (wprev == 0 ? 1 : 0)) {
             constexpr int LR = 32 / NB, CPL = NB / LR;
             const int ri = lane / LR, h = lane % LR;
             float v[CPL];
@@ -778,7 +799,9 @@ __device__ void sweep_inverse_tmem(const float *A, int mp, float *X, uint32_t tb
 #pragma unroll
             for (int c = 0; c < CPL; ++c) Dm[ri * NB + h * CPL + c] = -v[c];
         }
+        tmem_fence_before();
         g.sync();
+        tmem_fence_after();
         // -- -T = -P A_KK^-1 outside K (zero on K)
         for (int i = tid; i < mp; i += nthr) {
             float acc[NB];
@@ -831,12 +854,15 @@ __device__ void sweep_inverse_tmem(const float *A, int mp, float *X, uint32_t tb
             }
             tmem_st16(trow + (uint32_t)k0, v);
         }
-        // -- row block K := T^T outside K (the warp that owns the lanes of K; they lie in one warp)
+        // -- row block K := T^T outside K (the warp that owns the lanes of K; they lie in one warp):
+        // now only the next panel's column block, which its panel copy reads; the rest during the
+        // next pivot inversion.  The last panel writes every column here.
         if (warp == 4 * (k0 >> 7) + ((k0 & 127) >> 5)) {
             const int r0 = k0 - (128 * ch + 32 * q);             // first lane of K in this warp
             const bool mine = lane >= r0 && lane < r0 + NB;
+            const bool last = k0 + NB >= mp;
             for (int j0 = 0; j0 < mp; j0 += 16) {
-                if (j0 == k0) continue;
+                if (j0 == k0 || (!last && j0 != k0 + NB)) continue;
                 uint32_t v[16];
                 tmem_ld16(trow + (uint32_t)j0, v);
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
