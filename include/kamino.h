@@ -191,7 +191,8 @@ kamino_status kamino_state_upload(kamino_state_t state, kamino_buffer which, con
 kamino_status kamino_state_download(kamino_state_t state, kamino_buffer which, void *host,
                                     int64_t count, void *stream);
 
-/* One time step of every world of the state (the whole hot path, one kernel launch).
+/* One time step of every world of the state (the whole hot path: one kernel launch, or one per
+ * size bucket in the persistent plan).
  *   dt      time step in seconds, > 0
  *   iters   N_max of Alg. 1, >= 1
  *   tol     epsilon of the convergence test of Alg. 1 / Sec. 4.1, >= 0 (0 = run N_max)

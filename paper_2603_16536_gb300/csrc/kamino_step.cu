@@ -1,7 +1,8 @@
 // Fused per-world constrained forward-dynamics step for sm_103a (Kamino, arXiv 2603.16536).
 //
-// One CTA (256 threads) owns one world for the whole step and keeps its working set in shared
-// memory; nothing but the state, the inputs and the impulse cache touches HBM.
+// One CTA (256 threads) owns one world for the whole step and keeps its working set on chip
+// (shared memory, and for worlds of up to 256 padded rows the matrix in tensor memory); nothing
+// but the state, the inputs and the impulse cache touches HBM.
 //
 //   1  body kinematics: R(q), world inverse inertia, M^-1 (Sec. 3, Eq. 1)
 //   2  joint rows (incl. loop closures) with Baumgarte bias; actuation as J_d^T tau (Sec. 3)
@@ -14,9 +15,10 @@
 //   7  regularised factorisation, computed once per step (Sec. 4: A is constant across the
 //      iterations).  The paper factorises with block-Cholesky and runs a backward-forward
 //      pass every iteration; here A^-1 is formed once by a blocked symmetric sweep
-//      (Gauss-Jordan on the SPD matrix, panels of NB columns, register-tiled rank-NB updates),
-//      so every iteration's solve is one fully parallel symmetric matrix-vector product instead
-//      of two length-m dependency chains.  The iterates are the same up to rounding.
+//      (Gauss-Jordan on the SPD matrix, panels of NB columns, rank-NB updates on the tensor
+//      cores in the mixed mode), so every iteration's solve is one fully parallel matrix-vector
+//      product instead of two length-m dependency chains, made exact by one refinement step
+//      against the matrix-free residual (the fixed point is that of the exact solve).
 //   8  Proximal-ADMM (Alg. 1): De Saxce correction, solve, cone projection, dual update,
 //      Nesterov with adaptive restart, infinity-norm residuals, early exit
 //   9  lambda = P y; u+ = u_free + M^-1 J^T lambda; r+ = r + dt v+, q+ = exp(dt w+) q (Sec. 3);
@@ -1127,7 +1129,9 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
     }
     g.sync();
 
-    // ---- 7. A <- -A^-1 (blocked sweep), re-stored as BF16 tiles; per-body row lists for the
+    // ---- 7. A <- -A^-1 (blocked sweep): in tensor memory (mixed mode, whole CTA, mp <= 256), else
+    // on the packed triangle in shared memory, then stored into tensor memory (FP32 mode, whole
+    // CTA) or re-stored as BF16 tiles (mixed mode otherwise); per-body row lists for the
     // matrix-free products
     const bool tm = tm_cta && mp <= 256;
     bool in_tmem = false;                 // the inverse is already in tensor memory
