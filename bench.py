@@ -314,36 +314,48 @@ def run_gpu(args, rank, world):
     # ---- learned warm start: train the per-type network on solver-generated pairs (not timed)
     nets = []
     train_report = None
-    if args.learned and args.workload in ("biped", "heightfield", "fourbar"):
+    if args.learned:
+        # one network per world type (its worlds share body, joint, candidate and actuator
+        # counts), all trained on pairs the solver generates from the same trajectory
         t0 = time.perf_counter()
         st_gen = K.State(model, dev)
-        net = K.Mlp(model, np.arange(W), hidden=256, max_batch=max(4096, W), seed=seed)
+        types = [np.nonzero(ws.world_type == t)[0] for t in np.unique(ws.world_type)]
         steps_gen = args.gen_steps
-        X = torch.empty((steps_gen * W, net.info.d_in), device=dev)
-        Y = torch.empty((steps_gen * W, net.info.d_out), device=dev)
+        bufs = []
+        for ti, worlds in enumerate(types):
+            net = K.Mlp(model, worlds, hidden=256, max_batch=max(4096, len(worlds)), seed=seed + ti)
+            X = torch.empty((steps_gen * len(worlds), net.info.d_in), device=dev)
+            Y = torch.empty((steps_gen * len(worlds), net.info.d_out), device=dev)
+            nets.append(net)
+            bufs.append((X, Y, len(worlds)))
         for k in range(steps_gen):
             tk = torch.tensor(wg.actuation(ws, seed, k), dtype=torch.float32, device=dev)
-            net.features(st_gen, tk, out=X[k * W:(k + 1) * W])
+            for net, (X, Y, n) in zip(nets, bufs):
+                net.features(st_gen, tk, out=X[k * n:(k + 1) * n])
             st_gen.step(args.dt, 4 * args.iters, args.tol / 10, tk)
-            net.targets(st_gen, out=Y[k * W:(k + 1) * W])
-        net.fit_normalization(X, Y)
+            for net, (X, Y, n) in zip(nets, bufs):
+                net.targets(st_gen, out=Y[k * n:(k + 1) * n])
         gen = torch.Generator(device=dev).manual_seed(seed)
         loss = torch.zeros(1, device=dev)
-        first = last = None
-        for it in range(args.train_steps):
-            rows = torch.randint(0, steps_gen * W, (4096,), device=dev, generator=gen, dtype=torch.int32)
-            if it == 0 or it == args.train_steps - 1:
-                loss.zero_()
-            net.train_step(X, Y, rows, lr=1e-3 if it < 0.7 * args.train_steps else 2e-4,
-                           loss=loss if it in (0, args.train_steps - 1) else None)
-            if it == 0:
-                first = loss.item()
-        last = loss.item()
+        firsts, lasts = [], []
+        for net, (X, Y, n) in zip(nets, bufs):
+            net.fit_normalization(X, Y)
+            first = None
+            for it in range(args.train_steps):
+                rows = torch.randint(0, steps_gen * n, (4096,), device=dev, generator=gen, dtype=torch.int32)
+                if it == 0 or it == args.train_steps - 1:
+                    loss.zero_()
+                net.train_step(X, Y, rows, lr=1e-3 if it < 0.7 * args.train_steps else 2e-4,
+                               loss=loss if it in (0, args.train_steps - 1) else None)
+                if it == 0:
+                    first = loss.item()
+            firsts.append(first)
+            lasts.append(loss.item())
         torch.cuda.synchronize()
-        train_report = {"pairs": steps_gen * W, "adam_steps": args.train_steps, "batch": 4096,
-                        "loss_first": first, "loss_last": last, "seconds": time.perf_counter() - t0}
-        nets.append(net)
-        del X, Y, st_gen
+        train_report = {"networks": len(nets), "pairs": steps_gen * W, "adam_steps": args.train_steps,
+                        "batch": 4096, "loss_first": firsts if len(nets) > 1 else firsts[0],
+                        "loss_last": lasts if len(nets) > 1 else lasts[0], "seconds": time.perf_counter() - t0}
+        del bufs, st_gen
 
     def run_variant(name, warm_mode, learned=False, mdl=None, refine64=True):
         mdl = mdl or model
@@ -469,7 +481,9 @@ def run_gpu(args, rank, world):
     flops = float(algorithmic_flops(rows_h, its_h).sum()) / 1e12
     achieved = flops / (sum(ms_step_h) / 1e3)
     traffic = step_kernel_traffic(args.workload, W)
-    launches_per_step = 1 + (7 * len(nets) if learned else 0)
+    plan_mode, plan_buckets = model.plan()
+    step_launches = len(plan_buckets) if plan_mode == K.LAUNCH_PERSISTENT else 1
+    launches_per_step = step_launches + (7 * len(nets) if learned else 0)
     line = {
         "metric": METRIC, "value": v_head, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_head / args.steps, "higher_is_better": True,
