@@ -105,7 +105,10 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        # the raw samples go to $KAMINO_CLOCKS_DIR (default: the system's temporary directory)
+        import tempfile
+        out_dir = os.environ.get("KAMINO_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(out_dir, f"kamino_clocks_rank{index}.csv")
 
     def start(self):
         try:
