@@ -490,7 +490,7 @@ def run_gpu(args, rank, world):
     line = {
         "metric": METRIC, "value": v_head, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_head / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+tf32+bf16", "data": "synthetic",
         "config": {"workload": f"{desc} per GPU, dt={args.dt}, Gaussian actuation sigma=5, PADMM tol={args.tol}, "
                                f"N_max={args.iters}, rho={args.rho}; headline: {head}",
                    "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}"},

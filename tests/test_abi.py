@@ -98,3 +98,15 @@ def test_valid_model_needs_a_gpu(lib):
         pytest.skip("a GPU is present")
     got, msg = _create(wg.make_fourbar(num_worlds=2))
     assert got == 4, msg
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """No CPU fallback: without the compiled library the binding raises instead of computing."""
+    from paper_2603_16536_gb300 import kamino
+    saved = kamino._lib
+    try:
+        kamino._lib = None
+        with pytest.raises(RuntimeError, match="not built"):
+            kamino.load_library(str(tmp_path / "libkamino_absent.so"))
+    finally:
+        kamino._lib = saved
