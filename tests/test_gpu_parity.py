@@ -391,9 +391,11 @@ def test_autotune_and_graph_replay(K):
     assert torch.isfinite(st.body_u).all()
 
 
-def test_heightfield_bipeds_fp32(K):
-    """Bipeds on the random heightfield (32 grid candidates per world, up to 276 rows, panel 8):
-    after the feet land, one FP32 step against the oracle."""
+@pytest.mark.parametrize("precision", ["fp32", "mixed"])
+def test_heightfield_bipeds(K, precision):
+    """Bipeds on the random heightfield (32 grid candidates per world, up to 276 rows, panel 8; the
+    inverse stays in shared memory: FP32 lanes, or TF32 mma.sync strips and BF16 tiles in the mixed
+    mode): after the feet land, one step against the oracle."""
     ws = wg.make_biped_heightfield(num_worlds=4, seed=9)
     st = T.initial_state(ws)
     params = T.SolverParams(rho=0.1, eps=1e-8, n_max=20000)
@@ -404,8 +406,8 @@ def test_heightfield_bipeds_fp32(K):
     if not _margin_clear(None, ws, q):
         pytest.skip("a candidate sits on the activation threshold")
     tau = wg.actuation(ws, 9, 15)
-    qg, ug, rep, _ = gpu_step(K, ws, q, u, tau, 2e-3, 20000, 1e-8)
+    qg, ug, rep, _ = gpu_step(K, ws, q, u, tau, 2e-3, 20000, 1e-8, precision)
     ref, infos = oracle_step(ws, q, u, tau, 2e-3, eps=1e-11)
     check_report(rep, infos)
-    eu, eq = errors(q, qg, ug, ref.q, ref.u, 2e-3)
+    eu, eq = errors(q, qg, ug, ref.q, ref.u, 2e-3, precision)
     assert eu <= 1e-4 and eq <= 1e-4, (eu, eq)
