@@ -4,8 +4,10 @@
 Workload (one "step" = one kamino_step over the whole batch, the full hot path in one launch):
 4096 synthetic bipeds (31 bodies, 36 revolute joints, 6 loops, 16 foot-corner contact candidates
 on the plane), dt = 2 ms, Gaussian actuation sigma = 5 N m from the counter-based generator,
-Proximal-ADMM to tol 1e-5 with N_max = 200, FP32.  The simulation really advances: K timed
-steps follow W warm-up steps from the standing pose.
+Proximal-ADMM to tol 1e-5 with N_max = 1000 and rho = 0.1.  Four variants are timed: plain FP32
+from a cold start, and the mixed mode (TF32 tensor-core sweep, FP32 iteration; the FP64
+refinement stays off at tol 1e-5) from a cold start, from the impulse cache and from the learned
+warm start; the headline is the last.  The simulation really advances: K timed steps follow W warm-up steps from the standing pose.
 
 Reported: ``value`` = world-steps/s with the state resident in HBM (CUDA events on the launching
 stream, L2 flushed between timed steps); ``e2e`` = the same through the C ABI with the actuation
