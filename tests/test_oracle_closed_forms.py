@@ -165,3 +165,32 @@ def test_fourbar_invariants_loop_closure_energy_rank():
     swing = max(abs(e - e0) for e in energies)
     scale = sum(ws.body_mass[i] * 9.81 * 0.1 for i in range(3))
     assert swing < 0.05 * scale
+
+
+def test_baumgarte_shrinks_joint_error_by_one_minus_beta_per_step():
+    """Sec. 3's stabilisation: the bilateral rows enforce J u+ = -(beta/dt) f(q), so a hinge whose
+    anchor gap and axis tilt are small (and which nothing else moves: no gravity, at rest) has
+    f_k = (1 - beta)^k f_0 to first order.  The error is read from the poses with scipy's
+    rotations, not from the oracle's rows."""
+    from scipy.spatial.transform import Rotation
+
+    ws = wg.make_pendulum(theta0=0.5)
+    ws.gravity = np.zeros(3)
+    st = T.initial_state(ws)
+    st.q[0, :3] += np.array([1e-6, 2e-6, -1.5e-6])
+    tilt = Rotation.from_rotvec([1e-6, 0.0, -0.7e-6])
+    st.q[0, 3:] = (tilt * Rotation.from_quat(st.q[0, 3:])).as_quat()
+    anchor = ws.joint_frame_child[0][:3]
+    axis = Rotation.from_quat(ws.joint_frame_child[0][3:]).as_matrix()[:, 2]
+
+    def joint_error(s):
+        # the hinge is at the world origin about +y: anchor gap and the axis' x and z components
+        R = Rotation.from_quat(s.q[0, 3:]).as_matrix()
+        a = R @ axis
+        return np.concatenate([s.q[0, :3] + R @ anchor, [a[0], a[2]]])
+
+    params = T.SolverParams(eps=1e-12, n_max=20000, rho=0.1)
+    e0 = joint_error(st)
+    for k in range(1, 11):
+        st, _ = T.step(ws, st, None, 1e-3, params)
+        np.testing.assert_allclose(joint_error(st), (1.0 - params.beta) ** k * e0, rtol=0, atol=2e-12)

@@ -3,7 +3,8 @@ at least one pin fail.  This shows the pins are sensitive to the plausible error
 import numpy as np
 import pytest
 
-from oracle import constraints as C, padmm as PA, rigid
+from oracle import constraints as C, padmm as PA, rigid, timestep as T
+import tests.test_oracle_closed_forms as TF
 import tests.test_oracle_constraints as TC
 import tests.test_oracle_padmm as TP
 import tests.test_oracle_rigid as TR
@@ -75,3 +76,58 @@ def test_transposed_desaxce_is_caught(monkeypatch):
 
     monkeypatch.setattr(PA, "desaxce", on_tangent)
     assert _fails(TP.test_desaxce_operator)
+
+
+def test_baumgarte_sign_flip_is_caught(monkeypatch):
+    orig = C.joint_rows
+
+    def flipped(jtype, parent, child, fp, fc, r, R):      # bias +(beta/dt) f instead of -(...)
+        return [(ba, Ja, bb, Jb, -f) for ba, Ja, bb, Jb, f in orig(jtype, parent, child, fp, fc, r, R)]
+
+    monkeypatch.setattr(C, "joint_rows", flipped)
+    assert _fails(TF.test_baumgarte_shrinks_joint_error_by_one_minus_beta_per_step)
+
+
+def test_body_frame_rotation_update_is_caught(monkeypatch):
+    def right_product(r, q, v_plus, w_plus, dt):          # world-frame omega applied on the right
+        q_new = rigid.quat_mul(q, rigid.quat_exp(dt * w_plus))
+        return r + dt * v_plus, q_new / np.linalg.norm(q_new)
+
+    monkeypatch.setattr(T, "integrate_pose", right_product)
+    assert _fails(TR.test_torque_free_symmetric_top_precession)
+
+
+def test_explicit_euler_position_update_is_caught(monkeypatch):
+    orig_step = T.step
+
+    def explicit(ws, state, tau, dt, params, worlds=None):  # r+ = r + dt u- instead of dt u+
+        new, infos = orig_step(ws, state, tau, dt, params, worlds)
+        new.q[:, :3] += dt * (state.u[:, :3] - new.u[:, :3])
+        return new, infos
+
+    monkeypatch.setattr(T, "step", explicit)
+    assert _fails(TR.test_free_body_momentum_and_ballistics)
+
+
+def test_delassus_without_inverse_mass_is_caught(monkeypatch):
+    monkeypatch.setattr(PA, "delassus", lambda J, Minv: J @ J.T)
+    assert _fails(TP.test_box_resting_on_plane_carries_its_weight)
+
+
+def test_unshared_tangential_scaling_is_caught(monkeypatch):
+    def own_scale(D, n_bilateral, n_contacts, precond=True):   # scaled cone no longer circular
+        return 1.0 / np.sqrt(np.diag(D)) if precond else np.ones(D.shape[0])
+
+    monkeypatch.setattr(PA, "jacobi_scaling", own_scale)
+    assert _fails(TP.test_sliding_box_decelerates_at_mu_g_and_stops, 1)
+
+
+def test_dropped_dual_residual_is_caught(monkeypatch):
+    orig = PA.residuals
+
+    def no_dual(*a):                                        # stops as soon as x = y
+        r_p, _, r_c = orig(*a)
+        return r_p, 0.0, r_c
+
+    monkeypatch.setattr(PA, "residuals", no_dual)
+    assert _fails(TP.test_padmm_matches_direct_kkt, TP.wg.make_fourbar, 1e-3)
