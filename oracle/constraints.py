@@ -172,3 +172,10 @@ def contact_rows(body, p, n, rb):
     t1, t2 = orthonormal_basis(n)
     c = p - rb
     return [(-1, None, body, np.concatenate([d, np.cross(c, d)]), 0.0) for d in (t1, t2, n)]
+
+
+def contact_bias(phi, beta, dt):
+    """Bias of the rows (t1, t2, n) of an active contact at signed distance ``phi`` (Sec. 3): none
+    on the friction rows; on the normal row phi/dt while the point is still apart (phi > 0, the
+    gap may close within the step but no further) and Baumgarte's beta phi/dt once it penetrates."""
+    return [0.0, 0.0, (phi if phi > 0 else beta * phi) / dt]

@@ -115,7 +115,7 @@ def build_world(ws, w, q, u, tau, dt, params):
                 contact_ids.append(k)
                 for row in C.contact_rows(b, p, nrm, r[b]):
                     rows.append(row)
-                bias.extend([0.0, 0.0, (phi if phi > 0 else params.beta * phi) / dt])
+                bias.extend(C.contact_bias(phi, params.beta, dt))
     m = len(rows)
     J = np.zeros((m, n))
     for i, (ba, Ja, bb, Jb, _) in enumerate(rows):

@@ -131,3 +131,19 @@ def test_dropped_dual_residual_is_caught(monkeypatch):
 
     monkeypatch.setattr(PA, "residuals", no_dual)
     assert _fails(TP.test_padmm_matches_direct_kkt, TP.wg.make_fourbar, 1e-3)
+
+
+def test_baumgarte_on_speculative_contacts_is_caught(monkeypatch):
+    def always_beta(phi, beta, dt):                        # beta phi/dt on gaps too
+        return [0.0, 0.0, beta * phi / dt]
+
+    monkeypatch.setattr(C, "contact_bias", always_beta)
+    assert _fails(TP.test_approaching_box_lands_on_the_surface_and_stops)
+
+
+def test_contact_bias_without_beta_is_caught(monkeypatch):
+    def full_depth(phi, beta, dt):                         # whole depth removed in one step
+        return [0.0, 0.0, phi / dt]
+
+    monkeypatch.setattr(C, "contact_bias", full_depth)
+    assert _fails(TP.test_penetrating_box_rises_at_beta_depth_over_dt)

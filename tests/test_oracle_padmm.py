@@ -234,3 +234,35 @@ def test_biped_step_satisfies_ncp_conditions():
                 assert abs(vn) < 1e-5
         r_c, r_b = A.ncp_residual(i.J, i.u_plus, i.v_star, i.lam, i.p, nb, i.mu)
         assert r_c < 1e-6 and r_b < 1e-6
+
+
+def test_penetrating_box_rises_at_beta_depth_over_dt():
+    """Without gravity, a box sunk by d is pushed out by the Baumgarte bias of its four bottom
+    corners: the first step gives it the separating velocity beta d / dt exactly, after which the
+    contacts are slack (J u >= bias holds with lambda = 0) and it keeps that velocity, so its height
+    after k steps is -d + k beta d, through the surface and beyond (restitution 0, no damping)."""
+    d, dt = 1e-3, 2e-3
+    ws = wg.make_box(mass=1.0, mu=0.5, pos=(0.0, 0.0, 0.025 - d), gravity=(0.0, 0.0, 0.0))
+    params = T.SolverParams(eps=1e-12, n_max=20000, rho=0.1)
+    st = T.initial_state(ws)
+    for k in range(1, 8):
+        st, infos = T.step(ws, st, None, dt, params)
+        assert abs(st.q[0, 2] - 0.025 - (-d + k * params.beta * d)) < 1e-12
+        np.testing.assert_allclose(st.u[0], [0, 0, params.beta * d / dt, 0, 0, 0], atol=1e-12)
+        assert len(infos[0].contact_ids) == 4
+    assert infos[0].lam.size == 12 and np.abs(infos[0].lam).max() < 1e-12
+
+
+def test_approaching_box_lands_on_the_surface_and_stops():
+    """A box falling at 2 m/s, h = 2 mm above the plane (inside the activation margin), with
+    v dt > h: the normal rows allow closing the gap in this step and no more, so the step ends
+    with the box on the surface at velocity -h/dt, and the next one brings it to rest."""
+    h, v, dt = 2e-3, -2.0, 2e-3
+    ws = wg.make_box(mass=1.0, mu=0.5, pos=(0.0, 0.0, 0.025 + h), v0=(0.0, 0.0, v), gravity=(0.0, 0.0, 0.0))
+    params = T.SolverParams(eps=1e-12, n_max=20000, rho=0.1)
+    st, _ = T.step(ws, T.initial_state(ws), None, dt, params)
+    assert abs(st.q[0, 2] - 0.025) < 1e-12
+    np.testing.assert_allclose(st.u[0], [0, 0, -h / dt, 0, 0, 0], atol=1e-12)
+    st, _ = T.step(ws, st, None, dt, params)
+    assert abs(st.q[0, 2] - 0.025) < 1e-12
+    assert np.abs(st.u[0]).max() < 1e-10
