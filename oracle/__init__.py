@@ -15,7 +15,9 @@ What it computes, in the paper's order (Kamino, arXiv 2603.16536):
                      constraint Jacobian J.
 * ``padmm``       -- Sec. 4: Delassus matrix and free velocity (Eq. 4), the Jacobi preconditioner,
                      the De Saxce operator, the friction-cone projection and Proximal-ADMM
-                     (Alg. 1) with Nesterov acceleration and adaptive restart.
+                     (Alg. 1) with Nesterov acceleration and adaptive restart; Sec. 5.1's sparse
+                     formulation: the matrix-free Delassus operator and a Conjugate Residual x-step
+                     warm-started at the previous iterate.
 * ``timestep``    -- one full time step of a set of worlds (Eq. 2 solved through Alg. 1), with
                      the cached warm start.
 * ``audit``       -- independent checks: the direct KKT solve of Eq. 2 for bilateral-only worlds

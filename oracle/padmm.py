@@ -22,6 +22,19 @@ def delassus(J, Minv):
     return J @ Minv @ J.T
 
 
+def delassus_matrix_free(J, Minv, p):
+    """Sec. 5.1's sparse formulation: the scaled Delassus operator v -> P J M^-1 J^T P v as the
+    chain of products with J^T, M^-1 and J, without forming D."""
+    def apply(v):
+        return p * (J @ (Minv @ (J.T @ (p * v))))
+    return apply
+
+
+def delassus_diagonal(J, Minv):
+    """diag(D) of Eq. 4 row by row, d_r = J_r M^-1 J_r^T, without forming D."""
+    return np.array([J[r] @ Minv @ J[r] for r in range(J.shape[0])])
+
+
 def free_velocity(J, u_free, v_star):
     """Eq. 4: v_f = J (u^- + dt M^-1 h) + v*, with u_free = u^- + dt M^-1 h."""
     return J @ u_free + v_star
@@ -29,11 +42,12 @@ def free_velocity(J, u_free, v_star):
 
 def jacobi_scaling(D, n_bilateral, n_contacts, precond=True):
     """Sec. 4.1: P = diag(D)^-1/2, once per step.  Tangential rows of a contact share
-    p_t = ((D_t1t1 + D_t2t2) / 2)^-1/2 so that the scaled friction cone stays a circular cone."""
+    p_t = ((D_t1t1 + D_t2t2) / 2)^-1/2 so that the scaled friction cone stays a circular cone.
+    ``D`` is the Delassus matrix or, for the matrix-free path, its diagonal as a vector."""
     m = D.shape[0]
     if not precond:
         return np.ones(m)
-    d = np.diag(D).copy()
+    d = (np.diag(D) if D.ndim == 2 else D).copy()
     p = 1.0 / np.sqrt(d)
     for k in range(n_contacts):
         i = n_bilateral + 3 * k
@@ -92,12 +106,19 @@ class PadmmResult:
     restarts: int
 
 
-def residuals(x, x_prev, y, y_hat_prev, z, eta, rho, n_bilateral, n_contacts):
+def residuals(x, x_prev, y, y_hat_prev, z, eta, rho, n_bilateral, n_contacts, lin_res=None):
     """Infinity-norm residuals of Sec. 4.1.  Primal: x - y.  Dual: the deviation of the x-step's
     stationarity condition once the new iterates are substituted,
-    eta (x^i - x^{i-1}) + rho (y^i - y^_{i-1}).  Complementarity: max over contacts |y_k . z_k|."""
+    eta (x^i - x^{i-1}) + rho (y^i - y^_{i-1}).  Complementarity: max over contacts |y_k . z_k|.
+
+    ``lin_res`` is the residual A x^i + b^i that an inexact x-step left (Conjugate Residual); the
+    dual residual then subtracts it, which makes it D x + v_f + Gamma - z, the stationarity of the
+    dual problem at the new iterates (the exact x-step has lin_res = 0 and the formula above)."""
     r_p = float(np.max(np.abs(x - y))) if x.size else 0.0
-    r_d = float(np.max(np.abs(eta * (x - x_prev) + rho * (y - y_hat_prev)))) if x.size else 0.0
+    dev = eta * (x - x_prev) + rho * (y - y_hat_prev)
+    if lin_res is not None:
+        dev = dev - lin_res
+    r_d = float(np.max(np.abs(dev))) if x.size else 0.0
     r_c = 0.0
     if n_contacts:
         yc = y[n_bilateral:].reshape(-1, 3)
@@ -106,8 +127,40 @@ def residuals(x, x_prev, y, y_hat_prev, z, eta, rho, n_bilateral, n_contacts):
     return r_p, r_d, r_c
 
 
+def conjugate_residual(apply_A, c, x0, iters):
+    """Conjugate Residual iterations for A x = c with A symmetric (Sec. 5.1 pairs it with the
+    matrix-free Delassus operator; the method is the textbook one, e.g. Saad, "Iterative Methods
+    for Sparse Linear Systems", Sec. 6.8).  From x0, each iteration takes the step along the search
+    direction p that minimises ||c - A x||_2, then makes the next direction A-orthogonal in the
+    A^2 inner product:
+      r0 = c - A x0, p0 = r0
+      alpha_j = (r_j, A r_j) / (A p_j, A p_j);  x_{j+1} = x_j + alpha_j p_j;  r_{j+1} = r_j - alpha_j A p_j
+      beta_j  = (r_{j+1}, A r_{j+1}) / (r_j, A r_j);  p_{j+1} = r_{j+1} + beta_j p_j,
+    with A p_{j+1} = A r_{j+1} + beta_j A p_j, so one operator application per iteration.  Runs
+    ``iters`` iterations (a fixed budget), fewer only if the residual vanishes exactly."""
+    x = np.array(x0, dtype=np.float64)
+    r = c - apply_A(x)
+    Ar = apply_A(r)
+    p, Ap = r.copy(), Ar.copy()
+    rAr = float(r @ Ar)
+    for _ in range(iters):
+        ApAp = float(Ap @ Ap)
+        if rAr == 0.0 or ApAp == 0.0:
+            break
+        alpha = rAr / ApAp
+        x = x + alpha * p
+        r = r - alpha * Ap
+        Ar = apply_A(r)
+        rAr_next = float(r @ Ar)
+        beta = rAr_next / rAr
+        rAr = rAr_next
+        p = r + beta * p
+        Ap = Ar + beta * Ap
+    return x
+
+
 def padmm(D, v_f, n_bilateral, mu, eta, rho, eps, n_max, x0=None, z0=None, nesterov=True,
-          restart_factor=0.999):
+          restart_factor=0.999, cr_iters=None):
     """Alg. 1 (one time step), on an already scaled problem (D, v_f, mu).
 
     Steps per iteration i (hats are the Nesterov-extrapolated iterates, equal to the plain ones
@@ -123,15 +176,29 @@ def padmm(D, v_f, n_bilateral, mu, eta, rho, eps, n_max, x0=None, z0=None, neste
       stop when r_p, r_d, r_c < eps.
     The factorisation of D + (eta + rho) I is computed once (Sec. 4: the left-hand side is
     constant across iterations).  Returns y^N as lambda~.
-    """
-    m = D.shape[0]
-    n_contacts = len(mu)
-    A = D + (eta + rho) * np.eye(m)
-    L = np.linalg.cholesky(A) if m else np.zeros((0, 0))
 
-    def solve(b):
-        t = _forward(L, b)
-        return _backward(L, t)
+    With ``cr_iters`` set, ``D`` is the matrix-free operator v -> D v instead (Sec. 5.1's sparse
+    formulation) and the x-step is ``cr_iters`` Conjugate Residual iterations on
+    (D + (eta + rho) I) x = -b started from the previous iterate x^{i-1}; the dual residual then
+    includes what the x-step left of that system (see ``residuals``).
+    """
+    n_contacts = len(mu)
+    if cr_iters is None:
+        m = D.shape[0]
+        A = D + (eta + rho) * np.eye(m)
+        L = np.linalg.cholesky(A) if m else np.zeros((0, 0))
+
+        def solve_x(b, x_prev):
+            t = _forward(L, b)
+            return -_backward(L, t)
+    else:
+        m = v_f.shape[0]
+
+        def apply_A(v):
+            return D(v) + (eta + rho) * v
+
+        def solve_x(b, x_prev):
+            return conjugate_residual(apply_A, -b, x_prev, cr_iters)
 
     x = np.zeros(m) if x0 is None else x0.copy()
     y = x.copy()
@@ -146,10 +213,11 @@ def padmm(D, v_f, n_bilateral, mu, eta, rho, eps, n_max, x0=None, z0=None, neste
     for it in range(1, n_max + 1):
         s = desaxce(z_hat, n_bilateral, mu)
         b = v_f + s - eta * x - rho * y_hat - z_hat
-        x_new = -solve(b)
+        x_new = solve_x(b, x)
         y_new = project_cone(x_new - z_hat / rho, n_bilateral, mu)
         z_new = z_hat - rho * (x_new - y_new)
-        r_p, r_d, r_c = residuals(x_new, x, y_new, y_hat, z_new, eta, rho, n_bilateral, n_contacts)
+        lin_res = None if cr_iters is None else apply_A(x_new) + b
+        r_p, r_d, r_c = residuals(x_new, x, y_new, y_hat, z_new, eta, rho, n_bilateral, n_contacts, lin_res)
         if nesterov:
             c = float(np.dot(z_new - z_hat, z_new - z_hat) / rho + rho * np.dot(y_new - y_hat, y_new - y_hat))
             if c < restart_factor * c_prev:

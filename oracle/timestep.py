@@ -33,6 +33,8 @@ class SolverParams:
     nesterov: bool = True
     precond: bool = True
     warm: str = "cold"          # "cold" | "cached"
+    cr_iters: int | None = None # None: dense D, factorised once (Sec. 5.1's dense formulation);
+                                # k: matrix-free D with k Conjugate Residual iterations per x-step
 
 
 @dataclass
@@ -136,8 +138,13 @@ def solve_world(ws, w, q, u, tau, dt, params, cache=None):
     m = J.shape[0]
     D = PA.delassus(J, Minv)
     v_f = PA.free_velocity(J, u_free, v_star)
-    p = PA.jacobi_scaling(D, nbil, len(cids), params.precond)
-    Ds = p[:, None] * D * p[None, :]
+    if params.cr_iters is None:
+        p = PA.jacobi_scaling(D, nbil, len(cids), params.precond)
+        Ds = p[:, None] * D * p[None, :]
+        apply_Ds = Ds.__matmul__
+    else:                       # the solve sees only the operator and diag(D), never D itself
+        p = PA.jacobi_scaling(PA.delassus_diagonal(J, Minv), nbil, len(cids), params.precond)
+        Ds = apply_Ds = PA.delassus_matrix_free(J, Minv, p)
     vs = p * v_f
     mus = mu.copy()
     for k in range(len(cids)):
@@ -152,11 +159,11 @@ def solve_world(ws, w, q, u, tau, dt, params, cache=None):
             if cid in cache[1]:
                 lam0[nbil + 3 * k:nbil + 3 * k + 3] = cache[1][cid]
         x0 = lam0 / p
-        v0 = Ds @ x0 + vs
+        v0 = apply_Ds(x0) + vs
         z0 = v0 + PA.desaxce(v0, nbil, mus)
 
     res = PA.padmm(Ds, vs, nbil, mus, params.eta, params.rho, params.eps, params.n_max, x0=x0, z0=z0,
-                   nesterov=params.nesterov)
+                   nesterov=params.nesterov, cr_iters=params.cr_iters)
     lam = p * res.y
     u_plus = u_free + Minv @ (J.T @ lam)
     new_cache = (lam[:nbil].copy(), {cid: lam[nbil + 3 * k:nbil + 3 * k + 3].copy() for k, cid in enumerate(cids)})

@@ -147,3 +147,46 @@ def test_contact_bias_without_beta_is_caught(monkeypatch):
 
     monkeypatch.setattr(C, "contact_bias", full_depth)
     assert _fails(TP.test_penetrating_box_rises_at_beta_depth_over_dt)
+
+
+def test_conjugate_gradient_steps_in_cr_are_caught(monkeypatch):
+    import tests.test_oracle_cr as TCR
+
+    def cg(apply_A, c, x0, iters):                          # (r, r) and (p, A p): CG, not CR
+        x = np.array(x0, dtype=np.float64)
+        r = c - apply_A(x)
+        p = r.copy()
+        for _ in range(iters):
+            Ap = apply_A(p)
+            rr = float(r @ r)
+            if rr == 0.0:
+                break
+            alpha = rr / float(p @ Ap)
+            x = x + alpha * p
+            r = r - alpha * Ap
+            p = r + (float(r @ r) / rr) * p
+        return x
+
+    monkeypatch.setattr(PA, "conjugate_residual", cg)
+    assert _fails(TCR.test_cr_iterate_minimises_residual_over_krylov_space, 3)
+
+
+def test_stopping_test_blind_to_the_cr_residual_is_caught(monkeypatch):
+    import tests.test_oracle_cr as TCR
+    orig = PA.residuals
+
+    def blind(*a):                                          # drops lin_res
+        return orig(*a[:9])
+
+    monkeypatch.setattr(PA, "residuals", blind)
+    assert _fails(TCR.test_cr_padmm_matches_direct_kkt, TCR.wg.make_excavator, 2e-3, 1)
+
+
+def test_one_sided_scaling_in_matrix_free_delassus_is_caught(monkeypatch):
+    import tests.test_oracle_cr as TCR
+
+    def one_sided(J, Minv, p):                              # P J M^-1 J^T v: right-hand P dropped
+        return lambda v: p * (J @ (Minv @ (J.T @ v)))
+
+    monkeypatch.setattr(PA, "delassus_matrix_free", one_sided)
+    assert _fails(TCR.test_matrix_free_delassus_is_the_scaled_delassus_matrix)
