@@ -19,7 +19,7 @@ What it computes, in the paper's order (Kamino, arXiv 2603.16536):
                      formulation: the matrix-free Delassus operator and a Conjugate Residual x-step
                      warm-started at the previous iterate.
 * ``timestep``    -- one full time step of a set of worlds (Eq. 2 solved through Alg. 1), with
-                     the cached warm start.
+                     the cached warm start; semi-implicit Euler or the Moreau-Jean midpoint scheme.
 * ``audit``       -- independent checks: the direct KKT solve of Eq. 2 for bilateral-only worlds
                      and the natural-map NCP residual of a returned (lambda, u+).
 * ``mlp``         -- the warm-start network (3 GELU layers) forward, loss and backward in FP64,

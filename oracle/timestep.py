@@ -35,6 +35,7 @@ class SolverParams:
     warm: str = "cold"          # "cold" | "cached"
     cr_iters: int | None = None # None: dense D, factorised once (Sec. 5.1's dense formulation);
                                 # k: matrix-free D with k Conjugate Residual iterations per x-step
+    integrator: str = "euler"   # "euler": semi-implicit Euler | "midpoint": Moreau-Jean (Sec. 3)
 
 
 @dataclass
@@ -175,19 +176,36 @@ def solve_world(ws, w, q, u, tau, dt, params, cache=None):
 
 def step(ws, state: WorldState, tau, dt, params: SolverParams, worlds=None):
     """Advance the given worlds (default: all) by dt.  ``tau`` is [W, n_act_max] or None.
-    Returns (new WorldState, list of WorldInfo for the stepped worlds)."""
+    Returns (new WorldState, list of WorldInfo for the stepped worlds).
+
+    Semi-implicit Euler (Sec. 3): everything is evaluated at q^-, then q+ = q^- (+) dt u+.
+    Moreau-Jean midpoint (Sec. 3, after Jean 1999): the poses first move half a step with the
+    old velocity, q_m = q^- (+) (dt/2) u^-; kinematics, M, h, the rows, the contacts and their
+    biases are evaluated at q_m, Eq. 2 gives u+ over the whole step, and q+ = q_m (+) (dt/2) u+.
+    (+) is r + dt v for positions and exp(dt w) (x) q for orientations."""
+    midpoint = params.integrator == "midpoint"
+    if not midpoint and params.integrator != "euler":
+        raise ValueError(f"unknown integrator {params.integrator!r}")
     q_new = state.q.copy()
     u_new = state.u.copy()
     cache = list(state.cache)
     infos = []
     for w in (range(ws.num_worlds) if worlds is None else worlds):
         bs = ws.bodies(w)
-        u_plus, info, cache[w] = solve_world(ws, w, state.q, state.u, None if tau is None else tau[w], dt,
+        q_eval = state.q
+        if midpoint:
+            q_eval = state.q.copy()
+            for g in range(bs.start, bs.stop):
+                r_m, q_m = integrate_pose(state.q[g, :3], state.q[g, 3:], state.u[g, :3], state.u[g, 3:], 0.5 * dt)
+                q_eval[g, :3] = r_m
+                q_eval[g, 3:] = q_m
+        u_plus, info, cache[w] = solve_world(ws, w, q_eval, state.u, None if tau is None else tau[w], dt,
                                              params, cache[w])
+        h_pose = 0.5 * dt if midpoint else dt
         for i in range(bs.stop - bs.start):
             g = bs.start + i
             u_new[g] = u_plus[i]
-            r1, q1 = integrate_pose(state.q[g, :3], state.q[g, 3:], u_plus[i, :3], u_plus[i, 3:], dt)
+            r1, q1 = integrate_pose(q_eval[g, :3], q_eval[g, 3:], u_plus[i, :3], u_plus[i, 3:], h_pose)
             q_new[g, :3] = r1
             q_new[g, 3:] = q1
         infos.append(info)
