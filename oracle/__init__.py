@@ -12,7 +12,8 @@ What it computes, in the paper's order (Kamino, arXiv 2603.16536):
                      Newton-Euler forces h, semi-implicit Euler with the SO(3) exponential map.
 * ``constraints`` -- Sec. 3: joint constraints f(q) = 0 (loop closures are ordinary joints),
                      Signorini-Coulomb contacts in (t1, t2, n) frames, Baumgarte bias v*, the dense
-                     constraint Jacobian J.
+                     constraint Jacobian J; joint coordinates with implicit PD / armature / damping
+                     rows (Eq. 2's R and v*) and unilateral joint limits.
 * ``padmm``       -- Sec. 4: Delassus matrix and free velocity (Eq. 4), the Jacobi preconditioner,
                      the De Saxce operator, the friction-cone projection and Proximal-ADMM
                      (Alg. 1) with Nesterov acceleration and adaptive restart; Sec. 5.1's sparse

@@ -28,9 +28,14 @@ def kkt_direct(J, M, u_minus_plus_dt_h, v_star, R=None):
     return sol[:n], -sol[n:]
 
 
-def ncp_residual(J, u_plus, v_star, lam, p, n_bilateral, mu):
-    """Natural-map NCP residual (scaled units) of (lambda, u+).  Returns (r_contact, r_bilateral)."""
+def ncp_residual(J, u_plus, v_star, lam, p, n_bilateral, mu, reg=None, unilateral=()):
+    """Natural-map NCP residual (scaled units) of (lambda, u+).  Returns (r_contact, r_bilateral).
+    The row velocity is v = J u+ + R lambda + v* (Eq. 2's second block row).  Contact triples and
+    unilateral rows (joint limits, lambda >= 0 ⟂ v >= 0) enter r_contact through the natural map;
+    regularised rows need v = 0 and rigid bilateral rows v = 0 on the range of J (r_bilateral)."""
     v = J @ u_plus + v_star
+    if reg is not None:
+        v = v + reg * lam
     vs = p * v
     ls = lam / p
     mus = np.array(mu, dtype=np.float64)
@@ -42,13 +47,22 @@ def ncp_residual(J, u_plus, v_star, lam, p, n_bilateral, mu):
         w = vs + PA.desaxce(vs, n_bilateral, mus)
         nat = ls - PA.project_cone(ls - w, n_bilateral, mus)
         r_c = float(np.max(np.abs(nat[n_bilateral:])))
-    r_b = 0.0
-    if n_bilateral:
-        Jb = p[:n_bilateral, None] * J[:n_bilateral]
+    uni = np.zeros(len(lam), bool)
+    uni[list(unilateral)] = True
+    if uni.any():
+        nat = ls[uni] - np.maximum(ls[uni] - vs[uni], 0.0)
+        r_c = max(r_c, float(np.max(np.abs(nat))))
+    soft = np.zeros(len(lam), bool) if reg is None else reg > 0
+    rigid = np.zeros(len(lam), bool)
+    rigid[:n_bilateral] = True
+    rigid &= ~uni & ~soft
+    r_b = float(np.max(np.abs(vs[soft]))) if soft.any() else 0.0
+    if rigid.any():
+        Jb = p[rigid, None] * J[rigid]
         U, S, _ = np.linalg.svd(Jb, full_matrices=False)
         rank = int(np.sum(S > S.max() * 1e-10)) if S.size else 0
         Q = U[:, :rank]
-        r_b = float(np.max(np.abs(Q @ (Q.T @ vs[:n_bilateral]))))
+        r_b = max(r_b, float(np.max(np.abs(Q @ (Q.T @ vs[rigid])))))
     return r_c, r_b
 
 

@@ -90,20 +90,34 @@ def joint_rows(jtype, parent, child, fp, fc, r, R):
     return [(parent, Ja, child, Jb, f) for Ja, Jb, f in rows]
 
 
-def actuation_wrench(jtype, parent, child, fp, fc, r, R, value):
-    """Generalised force of a joint actuator: J_d^T value for the joint coordinate d (rotation about
-    the hinge a3 for a revolute, slide along a3 for a prismatic).  Returns {body: wrench[6]}."""
+def joint_coordinate(jtype, parent, child, fp, fc, r, R):
+    """The joint coordinate d(q) and its row J_d (J_d u = d-dot): for a revolute the angle of the
+    child frame about the hinge a3, measured from a1 towards a2, d = atan2(a2.b1, a1.b1); for a
+    prismatic the slide d = a3.(p_B - p_A).  Drives and limits act on it (Sec. 3).
+    Returns (d, Ja, Jb)."""
     rA, pA, cA, FA, rB, pB, cB, FB = _frames(parent, child, fp, fc, r, R)
-    a3 = FA[:, 2]
-    out = {}
+    a1, a2, a3 = FA[:, 0], FA[:, 1], FA[:, 2]
     if jtype == REVOLUTE:
+        b1 = FB[:, 0]
+        d = math.atan2(float(a2 @ b1), float(a1 @ b1))
         Ja = np.concatenate([np.zeros(3), -a3])
         Jb = np.concatenate([np.zeros(3), a3])
     elif jtype == PRISMATIC:
+        d = float(a3 @ (pB - pA))
         Ja = np.concatenate([-a3, -np.cross(pB - rA, a3)])
         Jb = np.concatenate([a3, np.cross(cB, a3)])
     else:
+        raise ValueError("only revolute and prismatic joints have a joint coordinate")
+    return d, Ja, Jb
+
+
+def actuation_wrench(jtype, parent, child, fp, fc, r, R, value):
+    """Generalised force of a joint actuator: J_d^T value for the joint coordinate d (rotation about
+    the hinge a3 for a revolute, slide along a3 for a prismatic).  Returns {body: wrench[6]}."""
+    if jtype not in (REVOLUTE, PRISMATIC):
         raise ValueError("only revolute and prismatic joints carry actuators")
+    _, Ja, Jb = joint_coordinate(jtype, parent, child, fp, fc, r, R)
+    out = {}
     if parent >= 0:
         out[parent] = value * Ja
     out[child] = out.get(child, 0.0) + value * Jb
@@ -179,3 +193,24 @@ def contact_bias(phi, beta, dt):
     on the friction rows; on the normal row phi/dt while the point is still apart (phi > 0, the
     gap may close within the step but no further) and Baumgarte's beta phi/dt once it penetrates."""
     return [0.0, 0.0, (phi if phi > 0 else beta * phi) / dt]
+
+
+def drive_row(d, d_dot, target, dt, kp, kd, armature, damping):
+    """Joint-space dynamics on the joint coordinate as one regularised row (Sec. 3, Eq. 2's R and
+    v*).  The row's impulse over the step is the armature's inertial reaction plus dt times the
+    implicit PD and damping forces, all taken at the end-of-step rate d-dot+ = J_d u+ and the
+    semi-implicit end pose d + dt d-dot+:
+        lambda = I_a (d-dot- - d-dot+) + dt Kp (target - d - dt d-dot+) - dt (Kd + b) d-dot+,
+    i.e. J_d u+ + lambda / C + v* = 0 with C = I_a + dt^2 Kp + dt (Kd + b) and
+    v* = -(I_a d-dot- + dt Kp (target - d)) / C.  Returns (R, v*), or None when C = 0."""
+    C = armature + dt * dt * kp + dt * (kd + damping)
+    if C <= 0.0:
+        return None
+    return 1.0 / C, -(armature * d_dot + dt * kp * (target - d)) / C
+
+
+def unilateral_bias(g, beta, dt):
+    """Bias of a unilateral row g(q) >= 0 (a joint limit): like a contact's normal row, the gap
+    may close within the step (g/dt while g > 0) and a violation is removed at Baumgarte's rate
+    (beta g/dt once g <= 0)."""
+    return (g if g > 0 else beta * g) / dt

@@ -2,8 +2,9 @@
 
 Test infrastructure only (see ``oracle/__init__``).
 
-Conventions.  Constraint rows are the bilateral joint rows followed by one (t1, t2, n) triple
-per active contact.  ``cone_mu[k]`` is the friction coefficient of contact k.  All iterates live in
+Conventions.  Constraint rows are the joint rows (bilateral; regularised drive rows; unilateral
+joint-limit rows, listed in ``unilateral``) followed by one (t1, t2, n) triple per active contact;
+``n_bilateral`` counts every row before the contacts.  ``cone_mu[k]`` is the friction coefficient of contact k.  All iterates live in
 the Jacobi-scaled space of Sec. 4.1: x~ = P^-1 x, v~ = P v, D~ = P D P.  The two tangential
 rows of a contact share one scale so the cone stays circular with mu~ = mu p_n / p_t.
 """
@@ -17,22 +18,26 @@ from scipy.linalg import solve_triangular
 
 
 # ----------------------------------------------------------------------------- Eq. 4
-def delassus(J, Minv):
-    """Eq. 4 with R = 0: D = J M^-1 J^T."""
-    return J @ Minv @ J.T
+def delassus(J, Minv, R=None):
+    """Eq. 4: D = J M^-1 J^T + R, R the diagonal regularisation of the joint-space dynamics rows
+    (a vector, or None for none)."""
+    D = J @ Minv @ J.T
+    return D if R is None else D + np.diag(R)
 
 
-def delassus_matrix_free(J, Minv, p):
-    """Sec. 5.1's sparse formulation: the scaled Delassus operator v -> P J M^-1 J^T P v as the
-    chain of products with J^T, M^-1 and J, without forming D."""
+def delassus_matrix_free(J, Minv, p, R=None):
+    """Sec. 5.1's sparse formulation: the scaled Delassus operator v -> P (J M^-1 J^T + R) P v as
+    the chain of products with J^T, M^-1 and J, without forming D."""
     def apply(v):
-        return p * (J @ (Minv @ (J.T @ (p * v))))
+        out = p * (J @ (Minv @ (J.T @ (p * v))))
+        return out if R is None else out + p * R * p * v
     return apply
 
 
-def delassus_diagonal(J, Minv):
-    """diag(D) of Eq. 4 row by row, d_r = J_r M^-1 J_r^T, without forming D."""
-    return np.array([J[r] @ Minv @ J[r] for r in range(J.shape[0])])
+def delassus_diagonal(J, Minv, R=None):
+    """diag(D) of Eq. 4 row by row, d_r = J_r M^-1 J_r^T + R_r, without forming D."""
+    d = np.array([J[r] @ Minv @ J[r] for r in range(J.shape[0])])
+    return d if R is None else d + R
 
 
 def free_velocity(J, u_free, v_star):
@@ -67,12 +72,16 @@ def desaxce(v, n_bilateral, mu):
     return s
 
 
-def project_cone(x, n_bilateral, mu):
+def project_cone(x, n_bilateral, mu, unilateral=None):
     """Projection onto K = R^(bilateral) x prod_k K_mu_k, K_mu = {(t, n): ||t|| <= mu n}: the
     closed-form Euclidean projection onto a second-order cone, contact by contact:
     inside K -> unchanged; inside the polar cone (mu ||t|| <= -n) -> 0; otherwise onto the
-    boundary ray, n' = (mu ||t|| + n) / (1 + mu^2), t' = mu n' t / ||t||."""
+    boundary ray, n' = (mu ||t|| + n) / (1 + mu^2), t' = mu n' t / ||t||.
+    ``unilateral`` lists rows before the contacts whose set is the ray R+ (joint limits, Sec. 3):
+    they are clamped at zero."""
     y = x.copy()
+    if unilateral is not None and len(unilateral):
+        y[unilateral] = np.maximum(x[unilateral], 0.0)
     if not len(mu):
         return y
     mu = np.asarray(mu, dtype=np.float64)
@@ -106,14 +115,15 @@ class PadmmResult:
     restarts: int
 
 
-def residuals(x, x_prev, y, y_hat_prev, z, eta, rho, n_bilateral, n_contacts, lin_res=None):
+def residuals(x, x_prev, y, y_hat_prev, z, eta, rho, n_bilateral, n_contacts, lin_res=None, unilateral=None):
     """Infinity-norm residuals of Sec. 4.1.  Primal: x - y.  Dual: the deviation of the x-step's
     stationarity condition once the new iterates are substituted,
     eta (x^i - x^{i-1}) + rho (y^i - y^_{i-1}).  Complementarity: max over contacts |y_k . z_k|.
 
     ``lin_res`` is the residual A x^i + b^i that an inexact x-step left (Conjugate Residual); the
     dual residual then subtracts it, which makes it D x + v_f + Gamma - z, the stationarity of the
-    dual problem at the new iterates (the exact x-step has lin_res = 0 and the formula above)."""
+    dual problem at the new iterates (the exact x-step has lin_res = 0 and the formula above).
+    Unilateral rows (joint limits) add |y_i z_i| to the complementarity residual."""
     r_p = float(np.max(np.abs(x - y))) if x.size else 0.0
     dev = eta * (x - x_prev) + rho * (y - y_hat_prev)
     if lin_res is not None:
@@ -124,6 +134,8 @@ def residuals(x, x_prev, y, y_hat_prev, z, eta, rho, n_bilateral, n_contacts, li
         yc = y[n_bilateral:].reshape(-1, 3)
         zc = z[n_bilateral:].reshape(-1, 3)
         r_c = float(np.max(np.abs(np.sum(yc * zc, axis=1))))
+    if unilateral is not None and len(unilateral):
+        r_c = max(r_c, float(np.max(np.abs(y[unilateral] * z[unilateral]))))
     return r_p, r_d, r_c
 
 
@@ -160,7 +172,7 @@ def conjugate_residual(apply_A, c, x0, iters):
 
 
 def padmm(D, v_f, n_bilateral, mu, eta, rho, eps, n_max, x0=None, z0=None, nesterov=True,
-          restart_factor=0.999, cr_iters=None):
+          restart_factor=0.999, cr_iters=None, unilateral=None):
     """Alg. 1 (one time step), on an already scaled problem (D, v_f, mu).
 
     Steps per iteration i (hats are the Nesterov-extrapolated iterates, equal to the plain ones
@@ -214,10 +226,11 @@ def padmm(D, v_f, n_bilateral, mu, eta, rho, eps, n_max, x0=None, z0=None, neste
         s = desaxce(z_hat, n_bilateral, mu)
         b = v_f + s - eta * x - rho * y_hat - z_hat
         x_new = solve_x(b, x)
-        y_new = project_cone(x_new - z_hat / rho, n_bilateral, mu)
+        y_new = project_cone(x_new - z_hat / rho, n_bilateral, mu, unilateral)
         z_new = z_hat - rho * (x_new - y_new)
         lin_res = None if cr_iters is None else apply_A(x_new) + b
-        r_p, r_d, r_c = residuals(x_new, x, y_new, y_hat, z_new, eta, rho, n_bilateral, n_contacts, lin_res)
+        r_p, r_d, r_c = residuals(x_new, x, y_new, y_hat, z_new, eta, rho, n_bilateral, n_contacts, lin_res,
+                                  unilateral)
         if nesterov:
             c = float(np.dot(z_new - z_hat, z_new - z_hat) / rho + rho * np.dot(y_new - y_hat, y_new - y_hat))
             if c < restart_factor * c_prev:

@@ -21,6 +21,8 @@ from . import constraints as C
 from . import padmm as PA
 from .rigid import integrate_pose, mass_matrix_block, newton_euler_h, quat_to_rot
 
+DRIVE_PD = 1                    # joint_drive mode whose actuation input is a position target
+
 
 @dataclass
 class SolverParams:
@@ -70,6 +72,8 @@ class WorldInfo:
     p: np.ndarray
     mu: np.ndarray
     u_plus: np.ndarray
+    reg: np.ndarray | None = None   # R of Eq. 4 per row (None: all zero)
+    unilateral: list = field(default_factory=list)  # rows whose set is R+ (joint limits)
 
 
 def build_world(ws, w, q, u, tau, dt, params):
@@ -82,13 +86,16 @@ def build_world(ws, w, q, u, tau, dt, params):
     inertia = ws.body_inertia[bs]
     n = 6 * nb
 
-    # actuation: generalised joint forces J_d^T tau
+    # actuation: generalised joint forces J_d^T tau (joints whose drive is a PD controller take
+    # their input as a position target instead, through a drive row below)
     wrench = np.zeros((nb, 6))
     js = ws.joints(w)
-    for jt, par, ch, fp, fc, act in zip(ws.joint_type[js], ws.joint_parent[js], ws.joint_child[js],
-                                        ws.joint_frame_parent[js], ws.joint_frame_child[js],
-                                        ws.joint_actuator[js]):
-        if act >= 0 and tau is not None:
+    drive = ws.joint_drive[js] if ws.joint_drive is not None else None
+    pd_mode = [drive is not None and int(drive[k, 0]) == DRIVE_PD for k in range(js.stop - js.start)]
+    for k, (jt, par, ch, fp, fc, act) in enumerate(zip(ws.joint_type[js], ws.joint_parent[js], ws.joint_child[js],
+                                                       ws.joint_frame_parent[js], ws.joint_frame_child[js],
+                                                       ws.joint_actuator[js])):
+        if act >= 0 and tau is not None and not pd_mode[k]:
             for b, wr in C.actuation_wrench(int(jt), int(par), int(ch), fp, fc, r, R, float(tau[act])).items():
                 wrench[b] += wr
 
@@ -103,13 +110,57 @@ def build_world(ws, w, q, u, tau, dt, params):
                            force=wrench[i, :3], torque=wrench[i, 3:])
         u_free[6 * i:6 * i + 6] = u[bs.start + i] + dt * (Mi_inv @ h)
 
-    # rows: joints (in joint order), then active contacts (in candidate order)
+    # rows: joints (in joint order), then drive rows, then active joint limits (in joint order,
+    # lower before upper), then active contacts (in candidate order)
     rows, bias = [], []
     for jt, par, ch, fp, fc in zip(ws.joint_type[js], ws.joint_parent[js], ws.joint_child[js],
                                    ws.joint_frame_parent[js], ws.joint_frame_child[js]):
         for row in C.joint_rows(int(jt), int(par), int(ch), fp, fc, r, R):
             rows.append(row)
             bias.append(params.beta / dt * row[4])
+    n_fixed = len(rows)
+    reg = [0.0] * n_fixed
+    uvel = u[bs]
+
+    def coord(k):
+        j = js.start + k
+        par, ch = int(ws.joint_parent[j]), int(ws.joint_child[j])
+        d, Ja, Jb = C.joint_coordinate(int(ws.joint_type[j]), par, ch, ws.joint_frame_parent[j],
+                                       ws.joint_frame_child[j], r, R)
+        d_dot = float(Jb @ uvel[ch]) + (float(Ja @ uvel[par]) if par >= 0 else 0.0)
+        return par, ch, d, d_dot, Ja, Jb
+
+    if drive is not None:
+        for k in range(js.stop - js.start):
+            _, kp, kd, arm, damp = drive[k]
+            if kp == 0.0 and kd == 0.0 and arm == 0.0 and damp == 0.0:
+                continue
+            par, ch, d, d_dot, Ja, Jb = coord(k)
+            act = int(ws.joint_actuator[js.start + k])
+            target = float(tau[act]) if (pd_mode[k] and tau is not None and act >= 0) else d
+            if not pd_mode[k]:
+                kp = kd = 0.0                       # torque mode: the input is applied as a force
+            row = C.drive_row(d, d_dot, target, dt, kp, kd, arm, damp)
+            if row is None:
+                continue
+            rows.append((par, Ja, ch, Jb, 0.0))
+            reg.append(row[0])
+            bias.append(row[1])
+    n_fixed = len(rows)
+    unilateral, limit_ids = [], []
+    if ws.joint_limit is not None:
+        for k in range(js.stop - js.start):
+            lo, hi = ws.joint_limit[js.start + k]
+            if not (np.isfinite(lo) or np.isfinite(hi)):
+                continue
+            par, ch, d, _, Ja, Jb = coord(k)
+            for side, g, sgn in ((0, d - lo, 1.0), (1, hi - d, -1.0)):
+                if np.isfinite(g) and g < params.margin:
+                    unilateral.append(len(rows))
+                    limit_ids.append((k, side))
+                    rows.append((par, sgn * Ja, ch, sgn * Jb, 0.0))
+                    reg.append(0.0)
+                    bias.append(C.unilateral_bias(g, params.beta, dt))
     n_bilateral = len(rows)
     contact_ids = []
     if ws.terrain_kind != 0:
@@ -127,8 +178,10 @@ def build_world(ws, w, q, u, tau, dt, params):
         J[i, 6 * bb:6 * bb + 6] += Jb
     v_star = np.array(bias)
     mu = np.full(len(contact_ids), ws.world_mu[w])
+    reg = np.array(reg + [0.0] * (m - n_bilateral))
     return dict(J=J, Minv=Minv, u_free=u_free, v_star=v_star, n_bilateral=n_bilateral,
-                contact_ids=contact_ids, mu=mu, r=r, R=R, nb=nb)
+                contact_ids=contact_ids, mu=mu, r=r, R=R, nb=nb, n_fixed=n_fixed,
+                reg=reg if reg.any() else None, unilateral=unilateral, limit_ids=limit_ids)
 
 
 def solve_world(ws, w, q, u, tau, dt, params, cache=None):
@@ -136,16 +189,17 @@ def solve_world(ws, w, q, u, tau, dt, params, cache=None):
     B = build_world(ws, w, q, u, tau, dt, params)
     J, Minv, u_free, v_star = B["J"], B["Minv"], B["u_free"], B["v_star"]
     nbil, cids, mu = B["n_bilateral"], B["contact_ids"], B["mu"]
+    reg, uni, n_fixed = B["reg"], B["unilateral"], B["n_fixed"]
     m = J.shape[0]
-    D = PA.delassus(J, Minv)
+    D = PA.delassus(J, Minv, reg)
     v_f = PA.free_velocity(J, u_free, v_star)
     if params.cr_iters is None:
         p = PA.jacobi_scaling(D, nbil, len(cids), params.precond)
         Ds = p[:, None] * D * p[None, :]
         apply_Ds = Ds.__matmul__
     else:                       # the solve sees only the operator and diag(D), never D itself
-        p = PA.jacobi_scaling(PA.delassus_diagonal(J, Minv), nbil, len(cids), params.precond)
-        Ds = apply_Ds = PA.delassus_matrix_free(J, Minv, p)
+        p = PA.jacobi_scaling(PA.delassus_diagonal(J, Minv, reg), nbil, len(cids), params.precond)
+        Ds = apply_Ds = PA.delassus_matrix_free(J, Minv, p, reg)
     vs = p * v_f
     mus = mu.copy()
     for k in range(len(cids)):
@@ -155,7 +209,10 @@ def solve_world(ws, w, q, u, tau, dt, params, cache=None):
     x0 = z0 = None
     if params.warm == "cached" and cache is not None and m:
         lam0 = np.zeros(m)
-        lam0[:nbil] = cache[0]
+        lam0[:n_fixed] = cache[0]
+        limits = cache[2] if len(cache) > 2 else {}
+        for i, key in zip(uni, B["limit_ids"]):
+            lam0[i] = limits.get(key, 0.0)
         for k, cid in enumerate(cids):
             if cid in cache[1]:
                 lam0[nbil + 3 * k:nbil + 3 * k + 3] = cache[1][cid]
@@ -164,13 +221,16 @@ def solve_world(ws, w, q, u, tau, dt, params, cache=None):
         z0 = v0 + PA.desaxce(v0, nbil, mus)
 
     res = PA.padmm(Ds, vs, nbil, mus, params.eta, params.rho, params.eps, params.n_max, x0=x0, z0=z0,
-                   nesterov=params.nesterov, cr_iters=params.cr_iters)
+                   nesterov=params.nesterov, cr_iters=params.cr_iters, unilateral=uni)
     lam = p * res.y
     u_plus = u_free + Minv @ (J.T @ lam)
-    new_cache = (lam[:nbil].copy(), {cid: lam[nbil + 3 * k:nbil + 3 * k + 3].copy() for k, cid in enumerate(cids)})
+    new_cache = (lam[:n_fixed].copy(), {cid: lam[nbil + 3 * k:nbil + 3 * k + 3].copy() for k, cid in enumerate(cids)})
+    if uni:
+        new_cache = new_cache + ({key: float(lam[i]) for i, key in zip(uni, B["limit_ids"])},)
     info = WorldInfo(m=m, n_bilateral=nbil, contact_ids=cids, iterations=res.iterations, r_p=res.r_p,
                      r_d=res.r_d, r_c=res.r_c, converged=res.converged, lam=lam, J=J, v_star=v_star,
-                     u_free=u_free, Minv=Minv, D=D, v_f=v_f, p=p, mu=mu, u_plus=u_plus)
+                     u_free=u_free, Minv=Minv, D=D, v_f=v_f, p=p, mu=mu, u_plus=u_plus, reg=reg,
+                     unilateral=list(uni))
     return u_plus.reshape(-1, 6), info, new_cache
 
 

@@ -161,6 +161,9 @@ class Model:
     """A set of worlds on the device (kamino_model_create)."""
 
     def __init__(self, ws, precision: str = "fp32", params: SolverParams | None = None):
+        if getattr(ws, "joint_drive", None) is not None or getattr(ws, "joint_limit", None) is not None:
+            raise ValueError("joint drives (implicit PD, armature, damping) and joint limits are not "
+                             "implemented by the CUDA step")
         lib = load_library()
         self.precision = {"fp32": FP32, "fp64": FP64, "mixed": MIXED, FP32: FP32, FP64: FP64, MIXED: MIXED}[precision]
         self.ws = ws

@@ -110,3 +110,12 @@ def test_missing_library_fails_loudly(tmp_path):
             kamino.load_library(str(tmp_path / "libkamino_absent.so"))
     finally:
         kamino._lib = saved
+
+
+def test_model_rejects_joint_drives_and_limits():
+    """The CUDA step has no drive or limit rows: worlds that carry them are refused up front rather
+    than stepped without them."""
+    ws = wg.make_pendulum(actuated=True)
+    for w in (wg.with_joint_drives(ws, wg.DRIVE_PD, 10.0, 1.0), wg.with_joint_limits(ws, -1.0, 1.0)):
+        with pytest.raises(ValueError, match="not implemented by the CUDA step"):
+            K.Model(w, "fp32")

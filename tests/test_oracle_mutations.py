@@ -110,7 +110,7 @@ def test_explicit_euler_position_update_is_caught(monkeypatch):
 
 
 def test_delassus_without_inverse_mass_is_caught(monkeypatch):
-    monkeypatch.setattr(PA, "delassus", lambda J, Minv: J @ J.T)
+    monkeypatch.setattr(PA, "delassus", lambda J, Minv, R=None: J @ J.T)
     assert _fails(TP.test_box_resting_on_plane_carries_its_weight)
 
 
@@ -185,8 +185,44 @@ def test_stopping_test_blind_to_the_cr_residual_is_caught(monkeypatch):
 def test_one_sided_scaling_in_matrix_free_delassus_is_caught(monkeypatch):
     import tests.test_oracle_cr as TCR
 
-    def one_sided(J, Minv, p):                              # P J M^-1 J^T v: right-hand P dropped
+    def one_sided(J, Minv, p, R=None):                      # P J M^-1 J^T v: right-hand P dropped
         return lambda v: p * (J @ (Minv @ (J.T @ v)))
 
     monkeypatch.setattr(PA, "delassus_matrix_free", one_sided)
     assert _fails(TCR.test_matrix_free_delassus_is_the_scaled_delassus_matrix)
+
+
+def test_pd_target_with_the_wrong_sign_is_caught(monkeypatch):
+    import tests.test_oracle_drives as TD
+    orig = C.drive_row
+
+    def flipped(d, d_dot, target, dt, kp, kd, armature, damping):     # Kp (d - target)
+        return orig(d, d_dot, 2 * d - target, dt, kp, kd, armature, damping)
+
+    monkeypatch.setattr(C, "drive_row", flipped)
+    assert _fails(TD.test_implicit_pd_follows_the_hinge_recurrence, 50.0, 2.0, 0.0, 0.0)
+
+
+def test_armature_missing_from_the_drive_compliance_is_caught(monkeypatch):
+    import tests.test_oracle_drives as TD
+    orig = C.drive_row
+
+    def no_armature_in_c(d, d_dot, target, dt, kp, kd, armature, damping):
+        R, v = orig(d, d_dot, target, dt, kp, kd, 0.0, damping) if (kp or kd or damping) else (None, None)
+        if R is None:
+            return None
+        return R, v - armature * d_dot * R                              # C without I_a, v* with it
+
+    monkeypatch.setattr(C, "drive_row", no_armature_in_c)
+    assert _fails(TD.test_armature_and_damping_under_a_constant_torque, 0.05, 0.4)
+
+
+def test_limit_rows_treated_as_bilateral_are_caught(monkeypatch):
+    import tests.test_oracle_drives as TD
+    orig = PA.project_cone
+
+    def no_ray(x, n_bilateral, mu, unilateral=None):                    # lambda < 0 allowed
+        return orig(x, n_bilateral, mu)
+
+    monkeypatch.setattr(PA, "project_cone", no_ray)
+    assert _fails(TD.test_active_limit_lets_the_joint_move_away)

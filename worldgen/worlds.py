@@ -11,6 +11,7 @@ exactly; they do no dynamics.
 """
 from __future__ import annotations
 
+import copy
 import math
 from dataclasses import dataclass, field
 
@@ -20,6 +21,7 @@ JOINT_REVOLUTE, JOINT_PRISMATIC, JOINT_UNIVERSAL, JOINT_SPHERICAL, JOINT_FIXED =
 JOINT_ROWS = {JOINT_REVOLUTE: 5, JOINT_PRISMATIC: 5, JOINT_UNIVERSAL: 4, JOINT_SPHERICAL: 3,
               JOINT_FIXED: 6}
 TERRAIN_NONE, TERRAIN_PLANE, TERRAIN_HEIGHTFIELD = 0, 1, 2
+DRIVE_TORQUE, DRIVE_PD = 0, 1
 
 # world-type tags (used for the stream key and for per-type bookkeeping)
 KIND_PIN, KIND_FOURBAR, KIND_BIPED, KIND_STEWART, KIND_EXCAVATOR = 0, 1, 2, 3, 4
@@ -53,6 +55,12 @@ class WorldSet:
     hf_nx: int = 0
     hf_ny: int = 0
     hf_heights: np.ndarray = field(default_factory=lambda: np.zeros(0))  # f64 [ny*nx] row-major (j, i)
+    # Joint-space dynamics (optional; None = none anywhere).  joint_drive[j] = (mode, Kp, Kd,
+    # armature, damping): mode DRIVE_TORQUE takes the actuation input as a joint torque/force,
+    # DRIVE_PD as the position target of an implicit PD controller (zero velocity target).
+    # joint_limit[j] = (lower, upper) on the joint coordinate, +-inf for no bound.
+    joint_drive: np.ndarray | None = None   # f64 [J,5]
+    joint_limit: np.ndarray | None = None   # f64 [J,2]
 
     @property
     def n_act_max(self) -> int:
@@ -243,8 +251,31 @@ def _assemble(worlds, gravity=(0.0, 0.0, -9.81), terrain=None):
     return ws
 
 
+def with_joint_drives(ws, mode, kp=0.0, kd=0.0, armature=0.0, damping=0.0, joints=None):
+    """A copy of ``ws`` whose joints (default: every actuated joint) carry the given drive."""
+    out = copy.copy(ws)
+    drive = np.zeros((len(ws.joint_type), 5)) if ws.joint_drive is None else ws.joint_drive.copy()
+    sel = np.flatnonzero(ws.joint_actuator >= 0) if joints is None else np.asarray(joints)
+    drive[sel] = (mode, kp, kd, armature, damping)
+    out.joint_drive = drive
+    return out
+
+
+def with_joint_limits(ws, lower, upper, joints=None):
+    """A copy of ``ws`` whose joints (default: every revolute and prismatic joint) have bounds."""
+    out = copy.copy(ws)
+    lim = np.tile([-np.inf, np.inf], (len(ws.joint_type), 1)) if ws.joint_limit is None else ws.joint_limit.copy()
+    if joints is None:
+        joints = np.flatnonzero(np.isin(ws.joint_type, (JOINT_REVOLUTE, JOINT_PRISMATIC)))
+    lim[np.asarray(joints)] = (lower, upper)
+    out.joint_limit = lim
+    return out
+
+
 def concat(sets):
     """Concatenate world sets (same gravity and terrain) into one heterogeneous set."""
+    if any(s.joint_drive is not None or s.joint_limit is not None for s in sets):
+        raise NotImplementedError("concat of worlds with joint drives or limits")
     base = sets[0]
     out = {}
     W = sum(s.num_worlds for s in sets)
@@ -273,15 +304,16 @@ def _rng(seed, kind, w):
 
 
 # ----------------------------------------------------------------------------- pin cases
-def make_pendulum(theta0=0.5, length=0.5, mass=1.0, width=0.02, num_worlds=1):
+def make_pendulum(theta0=0.5, length=0.5, mass=1.0, width=0.02, num_worlds=1, actuated=False):
     """Compound pendulum: a rod hinged at the world origin about +y, released at rest at ``theta0``
-    from the hanging position."""
+    from the hanging position (the hinge coordinate is 0 there and grows as the rod swings
+    towards hanging).  ``actuated`` gives the hinge actuation slot 0."""
     worlds = []
     for _ in range(num_worlds):
         wd = _World(KIND_PIN)
         d = np.array([math.sin(theta0), 0.0, -math.cos(theta0)])
         rod = wd.body(mass, (length, width, width), pos=0.5 * length * d, rot=frame_x(d, up=(0, 1, 0)))
-        wd.joint(JOINT_REVOLUTE, -1, rod, (0, 0, 0), frame_z((0, 1, 0)))
+        wd.joint(JOINT_REVOLUTE, -1, rod, (0, 0, 0), frame_z((0, 1, 0)), actuated=actuated)
         worlds.append(wd)
     return _assemble(worlds)
 
