@@ -78,7 +78,8 @@ def test_joint_coordinate_row_is_its_time_derivative(maker, jtype):
 def test_implicit_pd_follows_the_hinge_recurrence(kp, kd, armature, damping):
     """Position target d_t, zero velocity target: the row's impulse makes
     (I_p + I_a) d-dot+ = (I_p + I_a) d-dot- + dt Kp (d_t - d - dt d-dot+) - dt (Kd + b) d-dot+ and
-    d+ = d + dt d-dot+.  Also with Kp dt^2 a million times I_p (no blow-up: implicit)."""
+    d+ = d + dt d-dot+.  Also with Kp dt^2 = 120 I_p, far past the explicit PD's stability limit
+    dt < 2 sqrt(I_p / Kp) = 0.18 ms (no blow-up: implicit)."""
     ws = _free_hinge(wg.DRIVE_PD, kp, kd, armature, damping)
     st = T.initial_state(ws)
     target = 0.02
