@@ -23,6 +23,8 @@ What it computes, in the paper's order (Kamino, arXiv 2603.16536):
                      the cached warm start; semi-implicit Euler or the Moreau-Jean midpoint scheme.
 * ``audit``       -- independent checks: the direct KKT solve of Eq. 2 for bilateral-only worlds
                      and the natural-map NCP residual of a returned (lambda, u+).
+* ``kinematics``  -- Sec. 6.3: Gauss-Newton forward kinematics, consistent poses from joint
+                     coordinates for resets of mechanisms with loops.
 * ``mlp``         -- the warm-start network (3 GELU layers) forward, loss and backward in FP64,
                      the reference for the GPU kernels' gradients.
 

@@ -226,3 +226,26 @@ def test_limit_rows_treated_as_bilateral_are_caught(monkeypatch):
 
     monkeypatch.setattr(PA, "project_cone", no_ray)
     assert _fails(TD.test_active_limit_lets_the_joint_move_away)
+
+
+def test_fk_coordinate_rows_with_the_wrong_sign_are_caught(monkeypatch):
+    import oracle.kinematics as K
+    import tests.test_oracle_kinematics as TK
+    orig = K.residual_and_jacobian
+
+    def flipped(ws, w, q, joints, targets, free):
+        F, Jf = orig(ws, w, q, joints, targets, free)
+        Jf = Jf.copy()
+        if len(joints):
+            Jf[-len(joints):] *= -1.0
+        return F, Jf
+
+    monkeypatch.setattr(K, "residual_and_jacobian", flipped)
+    assert _fails(TK.test_fourbar_fk_matches_the_position_analysis)
+
+
+def test_fk_update_in_the_body_frame_is_caught(monkeypatch):
+    import oracle.kinematics as K
+    import tests.test_oracle_kinematics as TK
+    monkeypatch.setattr(K, "quat_mul", lambda a, b: rigid.quat_mul(b, a))   # q (x) exp(dw)
+    assert _fails(TK.test_biped_fk_round_trip, 0)
