@@ -60,9 +60,13 @@ enum { KAMINO_JOINT_REVOLUTE = 0, KAMINO_JOINT_PRISMATIC = 1, KAMINO_JOINT_UNIVE
        KAMINO_JOINT_SPHERICAL = 3, KAMINO_JOINT_FIXED = 4 };
 enum { KAMINO_TERRAIN_NONE = 0, KAMINO_TERRAIN_PLANE = 1, KAMINO_TERRAIN_HEIGHTFIELD = 2 };
 /* Arithmetic of a model.  KAMINO_FP32: FP32 storage and arithmetic, the swept FP32 inverse applied
- * with FP32 FMA.  KAMINO_MIXED: FP32 storage; the inverse is re-stored as BF16 tiles and applied on
- * tensor cores (FP32 accumulation), and every iteration refines against the FP32 matrix-free
- * residual.  KAMINO_FP64: FP64 throughout. */
+ * with FP32 FMA.  KAMINO_MIXED: FP32 storage; the factorisation's rank-16 updates are TF32 tensor-
+ * core products with FP32 accumulation (tcgen05 into the matrix held in tensor memory for worlds of
+ * up to 256 padded rows run by a whole CTA, mma.sync otherwise); the inverse is applied in FP32
+ * from tensor memory, or, for larger worlds and sub-CTA groups, as BF16 tiles on tensor cores
+ * (FP32 accumulation); every iteration refines against the FP32 matrix-free residual.
+ * KAMINO_FP64: FP64 throughout.  In every mode the reduced-precision inverse only preconditions
+ * that refinement step. */
 enum { KAMINO_FP32 = 0, KAMINO_FP64 = 1, KAMINO_MIXED = 2 };
 /* warm start of Alg. 1 (Sec. 4.1): zero, the impulses cached by the previous step, or impulses
  * supplied by the caller through KAMINO_BUF_WARM (e.g. a learned predictor). */
@@ -255,8 +259,9 @@ kamino_status kamino_graph_destroy(kamino_graph_t graph);
 /* ---- Learned warm start (one MLP per world type): features of a world (per body the position
  * relative to the first body, quaternion and twist; the first body's height; the actuation; per
  * contact candidate the signed distance and terrain normal; the state's impulse cache, i.e. the
- * previous step's solution) -> initial impulses in the impulse-cache layout.  L = 3 hidden layers of width `hidden`, GELU, BF16 weights and activations, FP32
- * accumulation on tensor cores (mma.sync m16n8k16), FP32 master weights and Adam.  Features and
+ * previous step's solution) -> initial impulses in the impulse-cache layout.  L = 3 hidden layers
+ * of width `hidden`, GELU, BF16 weights and activations, FP32 accumulation on tensor cores
+ * (mma.sync m16n8k16), FP32 master weights and Adam.  Features and
  * targets are normalised per column (kamino_mlp_fit_normalization).  The network only supplies
  * the starting point of Alg. 1 (KAMINO_WARM_EXTERNAL); the solver's convergence test decides. */
 typedef struct kamino_mlp_s *kamino_mlp_t;
