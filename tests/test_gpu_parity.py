@@ -210,10 +210,11 @@ def test_biped_in_the_air_has_no_contacts(K):
 
 
 def test_heterogeneous_worlds_one_launch(K):
-    """Four world types with 20 to 228 rows, ragged sizes, one launch."""
+    """Four world types, ragged sizes, one launch.  The set has no terrain, so the bipeds hang in
+    the air: 20 to 180 active rows, in buckets sized for every candidate active (up to 228)."""
     sets = [wg.make_fourbar(3, seed=4), wg.make_stewart(3, seed=4), wg.make_excavator(3, seed=4),
             wg.make_biped(3, seed=4)]
-    ws = wg.concat(sets)
+    ws = wg.concat(sets, terrain=wg.TERRAIN_NONE)
     q, u = rnd(ws.body_q0), rnd(ws.body_u0)
     tau = wg.actuation(ws, 4, 0)
     dt = 2e-3
@@ -330,8 +331,9 @@ def test_frictionless_box_keeps_sliding(K):
 
 # ----------------------------------------------------------------------------- heterogeneous plan
 def _hetero(n=4, seed=7):
+    """The four world types without terrain (bipeds in the air, joint rows only)."""
     return wg.concat([wg.make_fourbar(n, seed=seed), wg.make_stewart(n, seed=seed),
-                      wg.make_excavator(n, seed=seed), wg.make_biped(n, seed=seed)])
+                      wg.make_excavator(n, seed=seed), wg.make_biped(n, seed=seed)], terrain=wg.TERRAIN_NONE)
 
 
 def test_persistent_plan_matches_single_launch(K):

@@ -272,11 +272,24 @@ def with_joint_limits(ws, lower, upper, joints=None):
     return out
 
 
-def concat(sets):
-    """Concatenate world sets (same gravity and terrain) into one heterogeneous set."""
+def concat(sets, terrain="auto"):
+    """Concatenate world sets (same gravity) into one heterogeneous set.
+
+    ``terrain="auto"`` takes the terrain of the sets whose worlds have contact candidates (they
+    must agree; worlds without candidates never touch it), else the first set's.  An explicit
+    TERRAIN_NONE or TERRAIN_PLANE overrides it for every world."""
     if any(s.joint_drive is not None or s.joint_limit is not None for s in sets):
         raise NotImplementedError("concat of worlds with joint drives or limits")
-    base = sets[0]
+    with_contacts = [s for s in sets if int(s.world_contact_offset[-1]) > 0]
+    base = with_contacts[0] if with_contacts else sets[0]
+    for s in with_contacts[1:]:
+        if s.terrain_kind != base.terrain_kind or not np.array_equal(s.hf_heights, base.hf_heights):
+            raise ValueError("concat of sets with contact candidates on different terrains")
+    kind = base.terrain_kind
+    if terrain != "auto":
+        if terrain not in (TERRAIN_NONE, TERRAIN_PLANE):
+            raise ValueError(f"terrain override must be TERRAIN_NONE or TERRAIN_PLANE, not {terrain!r}")
+        kind = terrain
     out = {}
     W = sum(s.num_worlds for s in sets)
 
@@ -294,7 +307,7 @@ def concat(sets):
                  "joint_parent", "joint_child", "joint_actuator", "joint_frame_parent", "joint_frame_child",
                  "contact_body", "contact_point", "body_q0", "body_u0"):
         out[name] = np.concatenate([getattr(s, name) for s in sets])
-    return WorldSet(num_worlds=W, gravity=base.gravity.copy(), terrain_kind=base.terrain_kind,
+    return WorldSet(num_worlds=W, gravity=base.gravity.copy(), terrain_kind=kind,
                     hf_origin=base.hf_origin, hf_cell=base.hf_cell, hf_nx=base.hf_nx, hf_ny=base.hf_ny,
                     hf_heights=base.hf_heights, **out)
 
