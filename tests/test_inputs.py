@@ -4,6 +4,7 @@ Gaussian scale, the biped's masses, friction and standing contact geometry are a
 heightfield grid is the stated one, and worlds stepped together equal worlds stepped apart (the
 batch only concatenates independent problems)."""
 import numpy as np
+import pytest
 
 import worldgen as wg
 from oracle import rigid, timestep as T
@@ -84,6 +85,5 @@ def test_concat_takes_the_terrain_of_the_worlds_with_contacts():
     assert wg.concat([four, biped]).terrain_kind == wg.TERRAIN_PLANE           # four-bars have no candidates
     assert wg.concat([four, biped], terrain=wg.TERRAIN_NONE).terrain_kind == wg.TERRAIN_NONE
     assert wg.concat([four, wg.make_stewart(2, seed=1)]).terrain_kind == wg.TERRAIN_NONE
-    import pytest
     with pytest.raises(ValueError):
         wg.concat([biped, wg.make_biped_heightfield(2, seed=1)])               # two different grounds
