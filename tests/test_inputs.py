@@ -62,6 +62,8 @@ def test_heightfield_recipe():
     assert ws.hf_heights.min() >= 0.0 and ws.hf_heights.max() <= 0.05
     assert all(ws.contacts(w).stop - ws.contacts(w).start == 32 for w in range(4))
     assert ws.bilateral_rows(0) + 3 * 32 == 276
+    flat = wg.make_biped(num_worlds=4, seed=0)
+    assert abs(ws.body_q0[0, 2] - flat.body_q0[0, 2] - 0.05) < 1e-12            # pelvis raised 5 cm
 
 
 def test_worlds_stepped_together_equal_worlds_stepped_apart():
