@@ -89,3 +89,5 @@ def test_concat_takes_the_terrain_of_the_worlds_with_contacts():
     assert wg.concat([four, wg.make_stewart(2, seed=1)]).terrain_kind == wg.TERRAIN_NONE
     with pytest.raises(ValueError):
         wg.concat([biped, wg.make_biped_heightfield(2, seed=1)])               # two different grounds
+    with pytest.raises(ValueError):
+        wg.concat([four, wg.make_free_body()])                                 # zero gravity

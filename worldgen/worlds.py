@@ -273,13 +273,15 @@ def with_joint_limits(ws, lower, upper, joints=None):
 
 
 def concat(sets, terrain="auto"):
-    """Concatenate world sets (same gravity) into one heterogeneous set.
+    """Concatenate world sets (same gravity, else ValueError) into one heterogeneous set.
 
     ``terrain="auto"`` takes the terrain of the sets whose worlds have contact candidates (they
     must agree; worlds without candidates never touch it), else the first set's.  An explicit
     TERRAIN_NONE or TERRAIN_PLANE overrides it for every world."""
     if any(s.joint_drive is not None or s.joint_limit is not None for s in sets):
         raise NotImplementedError("concat of worlds with joint drives or limits")
+    if any(not np.array_equal(s.gravity, sets[0].gravity) for s in sets[1:]):
+        raise ValueError("concat of sets with different gravity")
     with_contacts = [s for s in sets if int(s.world_contact_offset[-1]) > 0]
     base = with_contacts[0] if with_contacts else sets[0]
     for s in with_contacts[1:]:
