@@ -22,6 +22,11 @@ anchors p_A, p_B, lever arms c_A = p_A - r_A, c_B = p_B - r_B):
 
 Contacts (Sec. 3, Signorini-Coulomb-Newton): rows (t1, t2, n) with the branchless orthonormal
 basis of Duff et al. 2017 built from the terrain normal n; J_b = [d, c x d] for d in (t1, t2, n).
+
+Joint-space dynamics (Sec. 3, Eq. 2's R and v*): the joint coordinate d(q) of a revolute or
+prismatic joint and its row J_d (J_d u = d-dot), one regularised row per driven joint for
+implicit PD, armature and viscous damping (``drive_row``), and unilateral joint-limit rows whose
+bias follows the contact normal's (``unilateral_bias``).
 """
 from __future__ import annotations
 
