@@ -4,12 +4,15 @@ Test infrastructure only (see ``oracle/__init__``).
 
 Per world, in the paper's order:
   1. body kinematics, M (Eq. 1), h, u_free = u^- + dt M^-1 h
-  2. contacts with the terrain (candidates with phi below the margin) and joint rows: J, v*
-  3. D and v_f (Eq. 4), Jacobi scaling P (Sec. 4.1)
+  2. contacts with the terrain (candidates with phi below the margin) and joint rows: J, v*;
+     when the world carries them, drive rows (R, v*) and the active joint limits
+  3. D = J M^-1 J^T + R and v_f (Eq. 4), Jacobi scaling P (Sec. 4.1)
   4. warm start from the cached lambda* (Sec. 4.1), matched by row for joints and by
      (body, candidate point) for contacts
-  5. Proximal-ADMM, Alg. 1, returning lambda = P y~
-  6. u+ = u_free + M^-1 J^T lambda (the solution of Eq. 2), then poses by the exponential map.
+  5. Proximal-ADMM, Alg. 1, returning lambda = P y~ (dense factorisation, or the matrix-free
+     operator with Conjugate Residual x-steps of Sec. 5.1)
+  6. u+ = u_free + M^-1 J^T lambda (the solution of Eq. 2), then poses by the exponential map
+     (semi-implicit Euler, or the Moreau-Jean midpoint scheme: see ``step``).
 """
 from __future__ import annotations
 
