@@ -115,13 +115,15 @@ def test_armature_and_damping_under_a_constant_torque(armature, damping):
         assert abs(_hinge_angle(st) - d) < 1e-6 * d
 
 
-def test_drives_on_a_bilateral_world_match_the_direct_kkt_solve():
+@pytest.mark.parametrize("cr_iters", [None, 9])
+def test_drives_on_a_bilateral_world_match_the_direct_kkt_solve(cr_iters):
     """Excavator (hinges and slides in closed loops) with implicit PD on its actuated joints: PADMM
-    reaches the solution of Eq. 2 with R solved directly."""
+    reaches the solution of Eq. 2 with R solved directly, with the dense factorisation and with the
+    matrix-free operator (which adds P R P to its chain of products)."""
     ws = wg.with_joint_drives(wg.make_excavator(num_worlds=2, seed=4), wg.DRIVE_PD, 400.0, 20.0, 0.02, 1.0)
     st = T.initial_state(ws)
     tau = 0.05 * wg.actuation(ws, 4, 0) / 5.0
-    st, infos = T.step(ws, st, tau, 2e-3, T.SolverParams(eps=1e-12, n_max=50000, rho=0.1))
+    st, infos = T.step(ws, st, tau, 2e-3, T.SolverParams(eps=1e-12, n_max=50000, rho=0.1, cr_iters=cr_iters))
     for i in infos:
         assert i.converged and i.reg is not None
         M = np.linalg.inv(i.Minv)

@@ -249,3 +249,10 @@ def test_fk_update_in_the_body_frame_is_caught(monkeypatch):
     import tests.test_oracle_kinematics as TK
     monkeypatch.setattr(K, "quat_mul", lambda a, b: rigid.quat_mul(b, a))   # q (x) exp(dw)
     assert _fails(TK.test_biped_fk_round_trip, 0)
+
+
+def test_matrix_free_operator_without_r_is_caught(monkeypatch):
+    import tests.test_oracle_drives as TD
+    orig = PA.delassus_matrix_free
+    monkeypatch.setattr(PA, "delassus_matrix_free", lambda J, Minv, p, R=None: orig(J, Minv, p))
+    assert _fails(TD.test_drives_on_a_bilateral_world_match_the_direct_kkt_solve, 9)
