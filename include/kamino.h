@@ -167,9 +167,10 @@ typedef struct kamino_model_s *kamino_model_t;
 typedef struct kamino_state_s *kamino_state_t;
 
 /* Validate a world description and copy it to the device.  Host-side checks (offsets monotone,
- * indices in range, parent != child, positive masses and inertias, unit-normalisable frame
- * quaternions, supported sizes, valid parameters) run first and return KAMINO_E_TOPOLOGY,
- * KAMINO_E_INVALID_ARG or KAMINO_E_UNSUPPORTED without touching the GPU. */
+ * indices in range, parent != child, positive masses and inertias, unit-normalisable frame and
+ * initial-pose quaternions, finite frames, contact points, gravity and initial state, supported
+ * sizes, valid parameters) run first and return KAMINO_E_TOPOLOGY, KAMINO_E_INVALID_ARG or
+ * KAMINO_E_UNSUPPORTED without touching the GPU. */
 kamino_status kamino_model_create(const kamino_model_desc *desc, kamino_model_t *out);
 kamino_status kamino_model_destroy(kamino_model_t model);
 kamino_status kamino_model_get_info(kamino_model_t model, kamino_model_info *out);

@@ -461,9 +461,8 @@ kamino_status kamino_model_create(const kamino_model_desc *d, kamino_model_t *ou
     kamino_status s = check_params(d->params);
     if (s) return s;
     const int W = d->num_worlds;
-    for (int k = 0; k < 3; ++k)
-        if (d->world_body_offset[0] != 0 || d->world_joint_offset[0] != 0 || d->world_contact_offset[0] != 0)
-            return fail(KAMINO_E_TOPOLOGY, "world offsets must start at 0");
+    if (d->world_body_offset[0] != 0 || d->world_joint_offset[0] != 0 || d->world_contact_offset[0] != 0)
+        return fail(KAMINO_E_TOPOLOGY, "world offsets must start at 0");
     for (int w = 0; w < W; ++w) {
         if (d->world_body_offset[w + 1] <= d->world_body_offset[w])
             return fail(KAMINO_E_TOPOLOGY, "world %d has no bodies (offsets must increase)", w);
@@ -487,6 +486,21 @@ kamino_status kamino_model_create(const kamino_model_desc *d, kamino_model_t *ou
         for (int k = 0; k < 3; ++k)
             if (!(d->body_inertia[3 * b + k] > 0.0) || !std::isfinite(d->body_inertia[3 * b + k]))
                 return fail(KAMINO_E_TOPOLOGY, "body %d: inertia must be finite and > 0", b);
+    }
+    for (int k = 0; k < 3; ++k)
+        if (!std::isfinite(d->gravity[k])) return fail(KAMINO_E_INVALID_ARG, "gravity must be finite");
+    for (int b = 0; b < B; ++b) {
+        if (d->body_q0) {
+            const double *q = d->body_q0 + 7 * (size_t)b;
+            for (int k = 0; k < 7; ++k)
+                if (!std::isfinite(q[k])) return fail(KAMINO_E_TOPOLOGY, "body %d: initial pose not finite", b);
+            if (!(q[3] * q[3] + q[4] * q[4] + q[5] * q[5] + q[6] * q[6] > 1e-24))
+                return fail(KAMINO_E_TOPOLOGY, "body %d: initial quaternion is not normalisable", b);
+        }
+        if (d->body_u0)
+            for (int k = 0; k < 6; ++k)
+                if (!std::isfinite(d->body_u0[6 * (size_t)b + k]))
+                    return fail(KAMINO_E_TOPOLOGY, "body %d: initial twist not finite", b);
     }
     if (d->terrain_kind < KAMINO_TERRAIN_NONE || d->terrain_kind > KAMINO_TERRAIN_HEIGHTFIELD)
         return fail(KAMINO_E_INVALID_ARG, "terrain_kind %d is not a KAMINO_TERRAIN_* value", d->terrain_kind);
@@ -539,6 +553,10 @@ kamino_status kamino_model_create(const kamino_model_desc *d, kamino_model_t *ou
                     delete m;
                     return fail(KAMINO_E_TOPOLOGY, "joint %d: frame quaternion is not normalisable", j);
                 }
+                if (!std::isfinite(f[0]) || !std::isfinite(f[1]) || !std::isfinite(f[2])) {
+                    delete m;
+                    return fail(KAMINO_E_TOPOLOGY, "joint %d: frame position not finite", j);
+                }
                 double *o = frames.data() + 14 * (size_t)j + 7 * side;
                 for (int k = 0; k < 3; ++k) o[k] = f[k];
                 for (int k = 3; k < 7; ++k) o[k] = f[k] / n;
@@ -547,11 +565,17 @@ kamino_status kamino_model_create(const kamino_model_desc *d, kamino_model_t *ou
             jrow[j] = row;
             row += rows_of(t);
         }
-        for (int c = c0; c < c0 + nc; ++c)
+        for (int c = c0; c < c0 + nc; ++c) {
             if (d->contact_body[c] < 0 || d->contact_body[c] >= nb) {
                 delete m;
                 return fail(KAMINO_E_TOPOLOGY, "contact candidate %d: body %d out of range [0, %d)", c, d->contact_body[c], nb);
             }
+            const double *pt = d->contact_point + 3 * (size_t)c;
+            if (!std::isfinite(pt[0]) || !std::isfinite(pt[1]) || !std::isfinite(pt[2])) {
+                delete m;
+                return fail(KAMINO_E_TOPOLOGY, "contact candidate %d: point not finite", c);
+            }
+        }
         if (nc > kMaxCandidates) {
             delete m;
             return fail(KAMINO_E_UNSUPPORTED, "world %d has %d contact candidates (max %d)", w, nc, kMaxCandidates);

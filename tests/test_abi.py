@@ -58,11 +58,23 @@ def _mutated(fn):
     (lambda ws: ws.joint_frame_parent.__setitem__((0, slice(3, 7)), 0.0), 2),  # null quaternion
     (lambda ws: ws.joint_actuator.__setitem__(0, 3), 2),                       # no such actuator slot
     (lambda ws: ws.world_mu.__setitem__(0, np.nan), 2),                        # bad friction
+    (lambda ws: ws.joint_frame_child.__setitem__((1, 0), np.nan), 2),          # anchor not finite
+    (lambda ws: ws.body_q0.__setitem__((2, 1), np.inf), 2),                    # initial pose not finite
+    (lambda ws: ws.body_q0.__setitem__((0, slice(3, 7)), 0.0), 2),             # null initial quaternion
+    (lambda ws: ws.body_u0.__setitem__((1, 4), np.nan), 2),                    # initial twist not finite
+    (lambda ws: setattr(ws, "gravity", np.array([0.0, 0.0, np.inf])), 1),      # gravity not finite
 ])
 def test_host_validation_rejects_bad_descriptions(lib, mutate, status):
     got, msg = _create(_mutated(mutate))
     assert got == status, msg
     assert lib.kamino_last_error().decode()
+
+
+def test_non_finite_contact_point_is_rejected(lib):
+    ws = wg.make_box(num_worlds=2)
+    ws.contact_point[11, 2] = np.nan
+    got, msg = _create(ws)
+    assert got == 2 and "point not finite" in msg, msg
 
 
 def test_bad_parameters_are_invalid_arg(lib):
