@@ -157,6 +157,27 @@ def _ptr(a):
     return a.ctypes.data_as(C.c_void_p) if a is not None and a.size else None
 
 
+def _tau_ptr(tau, dtype, need):
+    """Device pointer of an actuation tensor, after checking what the library cannot: a contiguous
+    CUDA tensor of the state's element type with at least `need` elements (None passes through)."""
+    if tau is None:
+        return None
+    if not (tau.is_cuda and tau.dtype == dtype and tau.is_contiguous() and tau.numel() >= need):
+        raise ValueError(f"actuation must be a contiguous CUDA {dtype} tensor of >= {need} elements "
+                         f"(got {tau.dtype}, {tau.numel()} elements, cuda={tau.is_cuda}, contiguous={tau.is_contiguous()})")
+    return C.c_void_p(tau.data_ptr())
+
+
+def _host_ptr(which, host, elem_dtype):
+    """Pointer and element count of a host array for upload/download: the library copies `count`
+    elements of the buffer's own type, so the array must be C-contiguous and of exactly that type
+    (kamino_residual records for BUF_RESIDUAL) or it would read or write past the array."""
+    want = RESIDUAL_DTYPE if which == BUF_RESIDUAL else np.dtype(elem_dtype)
+    if not isinstance(host, np.ndarray) or host.dtype != want or not host.flags.c_contiguous:
+        raise ValueError(f"host array must be a C-contiguous numpy array of {want}")
+    return host.ctypes.data_as(C.c_void_p), host.size
+
+
 class Model:
     """A set of worlds on the device (kamino_model_create)."""
 
@@ -248,6 +269,8 @@ class State:
         self.handle = C.c_void_p()
         _check(lib.kamino_state_alloc(model.handle, C.c_void_p(base + self._off), nbytes.value, C.byref(self.handle)))
         self.dtype = torch.float64 if model.precision == FP64 else torch.float32
+        self._np_dtype = np.float64 if model.precision == FP64 else np.float32
+        self._tau_len = model.ws.num_worlds * max(model.info.n_act_max, 0)
         self.body_q = self._view(BUF_BODY_Q, self.dtype).view(-1, 7)
         self.body_u = self._view(BUF_BODY_U, self.dtype).view(-1, 6)
         self.cache = self._view(BUF_CACHE, self.dtype)
@@ -269,11 +292,7 @@ class State:
         import torch
         if stream is None:
             stream = torch.cuda.current_stream()
-        tptr = None
-        if tau is not None:
-            assert tau.is_cuda and tau.dtype == self.dtype and tau.is_contiguous()
-            assert tau.numel() >= self.model.ws.num_worlds * max(self.model.info.n_act_max, 0)
-            tptr = C.c_void_p(tau.data_ptr())
+        tptr = _tau_ptr(tau, self.dtype, self._tau_len)
         _check(load_library().kamino_step(self.handle, float(dt), int(iters), float(tol), tptr,
                                           C.c_void_p(stream.cuda_stream)))
 
@@ -281,7 +300,7 @@ class State:
         """Time every feasible per-bucket configuration on this state's worlds (state unchanged)."""
         import torch
         stream = stream or torch.cuda.current_stream()
-        tptr = None if tau is None else C.c_void_p(tau.data_ptr())
+        tptr = _tau_ptr(tau, self.dtype, self._tau_len)
         _check(load_library().kamino_autotune(self.handle, float(dt), int(iters), float(tol), tptr,
                                               C.c_void_p(stream.cuda_stream)))
 
@@ -289,7 +308,7 @@ class State:
         """Capture one step into a CUDA graph (returns a StepGraph)."""
         import torch
         stream = stream or torch.cuda.current_stream()
-        tptr = None if tau is None else C.c_void_p(tau.data_ptr())
+        tptr = _tau_ptr(tau, self.dtype, self._tau_len)
         h = C.c_void_p()
         _check(load_library().kamino_graph_create(self.handle, float(dt), int(iters), float(tol), tptr,
                                                   C.c_void_p(stream.cuda_stream), C.byref(h)))
@@ -298,14 +317,14 @@ class State:
     def upload(self, which, host: np.ndarray, stream=None):
         import torch
         s = (stream or torch.cuda.current_stream()).cuda_stream
-        _check(load_library().kamino_state_upload(self.handle, which, host.ctypes.data_as(C.c_void_p), host.size,
-                                                  C.c_void_p(s)))
+        ptr, n = _host_ptr(which, host, self._np_dtype)
+        _check(load_library().kamino_state_upload(self.handle, which, ptr, n, C.c_void_p(s)))
 
     def download(self, which, host: np.ndarray, stream=None):
         import torch
         s = (stream or torch.cuda.current_stream()).cuda_stream
-        _check(load_library().kamino_state_download(self.handle, which, host.ctypes.data_as(C.c_void_p), host.size,
-                                                    C.c_void_p(s)))
+        ptr, n = _host_ptr(which, host, self._np_dtype)
+        _check(load_library().kamino_state_download(self.handle, which, ptr, n, C.c_void_p(s)))
 
     def residuals(self) -> np.ndarray:
         """Per-world reports as a numpy structured array (synchronises the current stream)."""

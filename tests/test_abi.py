@@ -131,3 +131,20 @@ def test_model_rejects_joint_drives_and_limits():
     for w in (wg.with_joint_drives(ws, wg.DRIVE_PD, 10.0, 1.0), wg.with_joint_limits(ws, -1.0, 1.0)):
         with pytest.raises(ValueError, match="not implemented by the CUDA step"):
             K.Model(w, "fp32")
+
+
+def test_binding_checks_what_the_library_cannot():
+    """Actuation tensors and host arrays are checked in the binding (the library sees raw pointers):
+    a wrong element type, a non-contiguous or short buffer, or a CPU tensor raise ValueError."""
+    import torch
+    with pytest.raises(ValueError):
+        K._tau_ptr(torch.zeros(24, dtype=torch.float32), torch.float32, 24)          # not on the GPU
+    assert K._tau_ptr(None, torch.float32, 24) is None
+    good = np.zeros(10, np.float32)
+    assert K._host_ptr(K.BUF_BODY_Q, good, np.float32)[1] == 10
+    for bad in (np.zeros(10, np.float64), np.zeros((10, 2), np.float32)[:, 0], [0.0] * 10):
+        with pytest.raises(ValueError):
+            K._host_ptr(K.BUF_BODY_Q, bad, np.float32)
+    assert K._host_ptr(K.BUF_RESIDUAL, np.zeros(3, K.RESIDUAL_DTYPE), np.float32)[1] == 3
+    with pytest.raises(ValueError):
+        K._host_ptr(K.BUF_RESIDUAL, np.zeros(24, np.int32), np.float32)
