@@ -359,6 +359,22 @@ def _dptr(t):
     return None if t is None else C.c_void_p(t.data_ptr())
 
 
+def _dev(t, dtype, name, cols=None, min_numel=0):
+    """Device pointer of a tensor the library will read or write through a raw pointer, after the
+    checks it cannot make: a contiguous CUDA tensor of `dtype`, `cols` columns when given, and at
+    least `min_numel` elements (None passes through; the library rejects it where it is required)."""
+    if t is None:
+        return None
+    ok = t.is_cuda and t.dtype == dtype and t.is_contiguous() and t.numel() >= min_numel
+    if ok and cols is not None:
+        ok = t.dim() == 2 and t.shape[1] == cols
+    if not ok:
+        raise ValueError(f"{name} must be a contiguous CUDA {dtype} tensor"
+                         + (f" with {cols} columns" if cols is not None else "")
+                         + f" and >= {min_numel} elements (got {t.dtype}, shape {tuple(t.shape)})")
+    return C.c_void_p(t.data_ptr())
+
+
 def _sptr(stream):
     import torch
     return C.c_void_p((stream or torch.cuda.current_stream()).cuda_stream)
@@ -378,53 +394,73 @@ class Mlp:
         _check(load_library().kamino_mlp_get_info(self.handle, C.byref(info)))
         self.info = info
 
+    def _xy(self, X, Y):
+        import torch
+        xp = _dev(X, torch.float32, "X", cols=self.info.d_in)
+        yp = _dev(Y, torch.float32, "Y", cols=self.info.d_out)
+        if X is not None and Y is not None and X.shape[0] != Y.shape[0]:
+            raise ValueError(f"X and Y must have the same rows (got {X.shape[0]} and {Y.shape[0]})")
+        return xp, yp
+
     def features(self, state: State, tau=None, out=None, stream=None):
         import torch
         if out is None:
             out = torch.empty((self.info.num_worlds, self.info.d_in), dtype=torch.float32, device=state._raw.device)
-        _check(load_library().kamino_mlp_features(self.handle, state.handle, _dptr(tau), _dptr(out), _sptr(stream)))
+        op = _dev(out, torch.float32, "out", min_numel=self.info.num_worlds * self.info.d_in)
+        _check(load_library().kamino_mlp_features(self.handle, state.handle, _tau_ptr(tau, state.dtype, state._tau_len),
+                                                  op, _sptr(stream)))
         return out
 
     def targets(self, state: State, out=None, stream=None):
         import torch
         if out is None:
             out = torch.empty((self.info.num_worlds, self.info.d_out), dtype=torch.float32, device=state._raw.device)
-        _check(load_library().kamino_mlp_targets(self.handle, state.handle, _dptr(out), _sptr(stream)))
+        op = _dev(out, torch.float32, "out", min_numel=self.info.num_worlds * self.info.d_out)
+        _check(load_library().kamino_mlp_targets(self.handle, state.handle, op, _sptr(stream)))
         return out
 
     def fit_normalization(self, X, Y, stream=None):
-        _check(load_library().kamino_mlp_fit_normalization(self.handle, _dptr(X), _dptr(Y), X.shape[0], _sptr(stream)))
+        xp, yp = self._xy(X, Y)
+        _check(load_library().kamino_mlp_fit_normalization(self.handle, xp, yp, X.shape[0], _sptr(stream)))
 
     def train_step(self, X, Y, rows=None, lr=1e-3, loss=None, stream=None):
+        import torch
+        xp, yp = self._xy(X, Y)
         batch = self.info.num_worlds if rows is None and X is None else (rows.numel() if rows is not None else X.shape[0])
-        _check(load_library().kamino_mlp_train_step(self.handle, _dptr(X), _dptr(Y), _dptr(rows), int(batch),
-                                                    float(lr), _dptr(loss), _sptr(stream)))
+        _check(load_library().kamino_mlp_train_step(self.handle, xp, yp, _dev(rows, torch.int32, "rows"), int(batch),
+                                                    float(lr), _dev(loss, torch.float32, "loss", min_numel=1),
+                                                    _sptr(stream)))
 
     def gradients(self, X, Y, rows=None, stream=None):
         import torch
+        xp, yp = self._xy(X, Y)
         batch = rows.numel() if rows is not None else X.shape[0]
         g = torch.empty(self.info.num_params, dtype=torch.float32, device=X.device)
         loss = torch.zeros(1, dtype=torch.float32, device=X.device)
-        _check(load_library().kamino_mlp_gradients(self.handle, _dptr(X), _dptr(Y), _dptr(rows), int(batch), _dptr(g),
-                                                   _dptr(loss), _sptr(stream)))
+        _check(load_library().kamino_mlp_gradients(self.handle, xp, yp, _dev(rows, torch.int32, "rows"), int(batch),
+                                                   _dptr(g), _dptr(loss), _sptr(stream)))
         return g, loss
 
     def predict(self, X, stream=None):
         import torch
+        xp = _dev(X, torch.float32, "X", cols=self.info.d_in)
         y = torch.empty((X.shape[0], self.info.d_out), dtype=torch.float32, device=X.device)
-        _check(load_library().kamino_mlp_predict(self.handle, _dptr(X), X.shape[0], _dptr(y), _sptr(stream)))
+        _check(load_library().kamino_mlp_predict(self.handle, xp, X.shape[0], _dptr(y), _sptr(stream)))
         return y
 
     def predict_static(self, X, out=None, stream=None):
         """kamino_mlp_predict without allocation: activations in the library's static scratch."""
         import torch
+        xp = _dev(X, torch.float32, "X", cols=self.info.d_in)
         y = out if out is not None else torch.empty((X.shape[0], self.info.d_out), dtype=torch.float32,
                                                     device=X.device)
-        _check(load_library().kamino_mlp_predict_static(self.handle, _dptr(X), X.shape[0], _dptr(y), _sptr(stream)))
+        yp = _dev(y, torch.float32, "out", min_numel=X.shape[0] * self.info.d_out)
+        _check(load_library().kamino_mlp_predict_static(self.handle, xp, X.shape[0], yp, _sptr(stream)))
         return y
 
     def warm_start(self, state: State, tau=None, stream=None):
-        _check(load_library().kamino_mlp_warm_start(self.handle, state.handle, _dptr(tau), _sptr(stream)))
+        _check(load_library().kamino_mlp_warm_start(self.handle, state.handle, _tau_ptr(tau, state.dtype, state._tau_len),
+                                                    _sptr(stream)))
 
     def get_params(self) -> np.ndarray:
         out = np.empty(self.info.num_params, np.float32)
@@ -442,6 +478,9 @@ class Mlp:
 
     def set_normalization(self, v: np.ndarray):
         v = np.ascontiguousarray(v, np.float32)
+        if v.size != 2 * (self.info.d_in + self.info.d_out):
+            raise ValueError(f"normalisation vector must have 2 (d_in + d_out) = "
+                             f"{2 * (self.info.d_in + self.info.d_out)} entries (got {v.size})")
         _check(load_library().kamino_mlp_set_normalization(self.handle, v.ctypes.data_as(C.c_void_p)))
 
     def layer_params(self, p: np.ndarray | None = None):

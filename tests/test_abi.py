@@ -140,6 +140,9 @@ def test_binding_checks_what_the_library_cannot():
     with pytest.raises(ValueError):
         K._tau_ptr(torch.zeros(24, dtype=torch.float32), torch.float32, 24)          # not on the GPU
     assert K._tau_ptr(None, torch.float32, 24) is None
+    assert K._dev(None, torch.float32, "X") is None
+    with pytest.raises(ValueError, match="X must be a contiguous CUDA"):
+        K._dev(torch.zeros((4, 3)), torch.float32, "X", cols=3)                     # not on the GPU
     good = np.zeros(10, np.float32)
     assert K._host_ptr(K.BUF_BODY_Q, good, np.float32)[1] == 10
     for bad in (np.zeros(10, np.float64), np.zeros((10, 2), np.float32)[:, 0], [0.0] * 10):
