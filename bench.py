@@ -245,6 +245,18 @@ def step_kernel_traffic(workload, worlds):
     return entry["dram_bytes"] * worlds / entry["worlds"]
 
 
+def hbm_roofline(traffic, launch_ms, peaks):
+    """The step kernel against the HBM roofline: its DRAM bytes per launch (ncu, scaled to the
+    launch's worlds) over the CUDA-event launch time, as a fraction of the measured copy bandwidth.
+    None when either the bytes or the peak is unknown."""
+    peak = peaks.get("hbm_gbs")
+    if traffic is None or not peak or not launch_ms:
+        return None
+    gbs = traffic / (launch_ms / 1e3) / 1e9
+    return {"achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+            "bytes_per_launch": traffic, "peak_note": "measured copy bandwidth (MEASURED_PEAKS hbm_gbs)"}
+
+
 def build_workload(args, seed):
     import worldgen as wg
     if args.workload == "biped":
@@ -506,7 +518,8 @@ def run_gpu(args, rank, world):
                      "frac": achieved / alu_peak, "traffic": traffic,
                      "kernel": "kamino step kernel (one launch per step)",
                      "launch_ms": sum(ms_step_h) / len(ms_step_h),
-                     "peak_note": f"derived FP32 FMA peak: {SM_COUNT} SMs x {FP32_LANES} lanes x 2 x {smax:.0f} MHz"},
+                     "peak_note": f"derived FP32 FMA peak: {SM_COUNT} SMs x {FP32_LANES} lanes x 2 x {smax:.0f} MHz",
+                     "hbm": hbm_roofline(traffic, sum(ms_step_h) / len(ms_step_h), peaks)},
         "clocks": clocks,
     }
     if train_report:

@@ -37,3 +37,17 @@ def test_recorded_step_kernel_traffic_is_current():
     assert entry["source_sha256"] == bench.kernel_source_hash()
     assert bench.step_kernel_traffic("biped", 4096) == entry["dram_bytes"] * 4096 / entry["worlds"]
     assert bench.step_kernel_traffic("biped", 4096) / 4096 < 16384       # bytes per world-step, on chip
+
+
+def test_hbm_roofline_of_the_step_kernel():
+    """The bench line's HBM entry: DRAM bytes per launch over the launch time against the measured
+    copy bandwidth; absent when either is unknown."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_module", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    h = bench.hbm_roofline(30.9e6, 21.06, {"hbm_gbs": 6701.2})
+    assert abs(h["achieved"] - 30.9e6 / 0.02106 / 1e9) < 1e-9 and h["unit"] == "GB/s"
+    assert abs(h["frac"] - h["achieved"] / 6701.2) < 1e-15 and h["frac"] < 1e-3     # far from the HBM bound
+    assert bench.hbm_roofline(None, 21.06, {"hbm_gbs": 6701.2}) is None
+    assert bench.hbm_roofline(30.9e6, 21.06, {}) is None
