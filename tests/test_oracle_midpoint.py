@@ -110,3 +110,20 @@ def test_unknown_integrator_is_rejected():
     ws = wg.make_free_body()
     with pytest.raises(ValueError):
         T.step(ws, T.initial_state(ws), None, 1e-3, T.SolverParams(integrator="rk4"))
+
+
+def test_midpoint_sliding_box_follows_the_exact_parabola():
+    """Coulomb sliding under the midpoint scheme: the speed falls by mu g dt per step as before,
+    and the position, advanced with the mean of the old and new speeds, is exactly
+    x0 + v0 t - mu g t^2 / 2 while the box slides (semi-implicit Euler is off by mu g dt t / 2)."""
+    mu, v0, dt = 0.4, 0.5, 1e-3
+    ws = wg.make_box(mass=1.0, mu=mu, v0=(v0, 0.0, 0.0))
+    st = T.initial_state(ws)
+    x0 = st.q[0, 0]
+    params = T.SolverParams(eps=1e-10, n_max=20000, rho=0.1, integrator="midpoint")
+    for k in range(1, 101):
+        st, _ = T.step(ws, st, None, dt, params)
+        t = k * dt
+        assert abs(st.q[0, 0] - (x0 + v0 * t - 0.5 * mu * 9.81 * t * t)) < 1e-11
+        assert abs(st.u[0, 0] - (v0 - mu * 9.81 * t)) < 2e-6
+    assert abs(st.q[0, 2] - 0.025) < 1e-12 and np.abs(st.u[0, 1:]).max() < 1e-9
