@@ -171,6 +171,13 @@ def conjugate_residual(apply_A, c, x0, iters):
     return x
 
 
+def nesterov_coefficient(a):
+    """Sec. 4.1's Nesterov step (Goldstein et al. 2014): the next momentum parameter
+    a' = (1 + sqrt(1 + 4 a^2)) / 2 and the extrapolation weight (a - 1) / a'."""
+    a_next = 0.5 * (1.0 + math.sqrt(1.0 + 4.0 * a * a))
+    return a_next, (a - 1.0) / a_next
+
+
 def padmm(D, v_f, n_bilateral, mu, eta, rho, eps, n_max, x0=None, z0=None, nesterov=True,
           restart_factor=0.999, cr_iters=None, unilateral=None):
     """Alg. 1 (one time step), on an already scaled problem (D, v_f, mu).
@@ -234,8 +241,7 @@ def padmm(D, v_f, n_bilateral, mu, eta, rho, eps, n_max, x0=None, z0=None, neste
         if nesterov:
             c = float(np.dot(z_new - z_hat, z_new - z_hat) / rho + rho * np.dot(y_new - y_hat, y_new - y_hat))
             if c < restart_factor * c_prev:
-                a_next = 0.5 * (1.0 + math.sqrt(1.0 + 4.0 * a * a))
-                beta = (a - 1.0) / a_next
+                a_next, beta = nesterov_coefficient(a)
                 y_hat_next = y_new + beta * (y_new - y)
                 z_hat_next = z_new + beta * (z_new - z)
                 a = a_next

@@ -256,3 +256,28 @@ def test_matrix_free_operator_without_r_is_caught(monkeypatch):
     orig = PA.delassus_matrix_free
     monkeypatch.setattr(PA, "delassus_matrix_free", lambda J, Minv, p, R=None: orig(J, Minv, p))
     assert _fails(TD.test_drives_on_a_bilateral_world_match_the_direct_kkt_solve, 9)
+
+
+def test_wrong_nesterov_weight_is_caught(monkeypatch):
+    orig = PA.nesterov_coefficient
+
+    def shifted(a):                             # a / a' instead of (a - 1) / a'
+        a_next, _ = orig(a)
+        return a_next, a / a_next
+
+    monkeypatch.setattr(PA, "nesterov_coefficient", shifted)
+    assert _fails(TP.test_nesterov_sequence_matches_hand_recurrence)
+
+
+def test_restart_test_that_always_fires_is_caught(monkeypatch):
+    """A restart test whose comparison never holds (every iteration restarts, so there is no
+    acceleration at all) changes the sequence from the second iteration on."""
+    src = PA.padmm
+
+    def no_reset(*a, **k):
+        k = dict(k)
+        k["restart_factor"] = 1e-300            # every iteration restarts
+        return src(*a, **k)
+
+    monkeypatch.setattr(PA, "padmm", no_reset)
+    assert _fails(TP.test_nesterov_sequence_matches_hand_recurrence)

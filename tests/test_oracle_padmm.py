@@ -266,3 +266,34 @@ def test_approaching_box_lands_on_the_surface_and_stops():
     st, _ = T.step(ws, st, None, dt, params)
     assert abs(st.q[0, 2] - 0.025) < 1e-12
     assert np.abs(st.u[0]).max() < 1e-10
+
+
+# One bilateral row with D = d, v_f = v, eta = 0: z stays 0 (the projection is the identity, so
+# x - y = z^/rho and z = z^ - rho z^/rho = 0) and y = x, so Alg. 1 reduces to the scalar recurrence
+#   x_i = (-v + rho y^_{i-1}) / (d + rho),  c_i = rho (x_i - y^_{i-1})^2,
+#   c_i < 0.999 c_{i-1}: a' = (1 + sqrt(1 + 4 a^2)) / 2,  y^_i = x_i + (a - 1) / a' (x_i - x_{i-1}),
+#   otherwise a = 1, y^_i = x_{i-1}, c_i = c_{i-1} / 0.999.
+# The values below were worked out from that recurrence with 40-digit decimal arithmetic.
+_FAST = [(1, 0.5, 0.5), (2, 0.75, 0.8204383812813302), (3, 0.9102191906406651, 0.9797611740011472),
+         (4, 0.9898805870005736, 1.0321858712953011)]
+_SLOW_X = {10: 0.181497699038228, 20: 0.510415621930859, 36: 0.9818578599895553, 37: 1.0006365656364018,
+           38: 1.017839886484623, 39: 1.0006302630063384, 40: 1.000624022778553}
+
+
+def _scalar(d, v, n):
+    D = np.array([[d]])
+    return PA.padmm(D, np.array([v]), 1, [], eta=0.0, rho=1.0, eps=0.0, n_max=n)
+
+
+def test_nesterov_sequence_matches_hand_recurrence():
+    """Sec. 4.1's acceleration, pinned by the hand-worked scalar recurrence above: the momentum
+    weights (a - 1)/a' of the first iterations (d = 1, v = -1) and, on a slow problem (d = 0.01,
+    v = -0.01, solution 1), the first adaptive restart, which comes at iteration 38 when the
+    extrapolated iterate overshoots and the combined residual grows."""
+    for i, x, yh in _FAST:
+        res = _scalar(1.0, -1.0, i)
+        assert res.x[0] == pytest.approx(x, rel=1e-13) and res.restarts == 0
+    for i, x in _SLOW_X.items():
+        res = _scalar(0.01, -0.01, i)
+        assert res.x[0] == pytest.approx(x, rel=1e-12), i
+        assert res.restarts == (1 if i >= 38 else 0), i
