@@ -220,6 +220,26 @@ def algorithmic_flops(rows, iters):
     return m ** 3 / 3.0 + it * (2.0 * m * m + 20.0 * m) + 2.0 * 12.0 * m * 8.0
 
 
+def ncp_report(ncp, status, its, tol, n_max, rate):
+    """The metric's qualifying condition over every world-step of a variant: the device's
+    natural-map NCP residual of the returned (lambda, u+) (kamino_residual.r_ncp) against the
+    tolerance; the world-steps that meet it per second; and, for the world-steps that ran to N_max
+    without meeting the ADMM test, their residuals and their share of the PADMM iterations (of the
+    step's SM time, since one iteration costs the same in every world of the batch)."""
+    import numpy as np
+    ok = ncp <= tol
+    capped = (status & 1) != 0
+    out = {"ncp_le_tol_fraction": float(ok.mean()), "ncp_qualified_value": float(rate * ok.mean()),
+           "ncp_median": float(np.median(ncp)), "ncp_p99": float(np.quantile(ncp, 0.99)),
+           "capped_fraction": float(capped.mean()),
+           "capped_iteration_share": float(its[capped].sum() / max(its.sum(), 1))}
+    if capped.any():
+        c = ncp[capped]
+        out["capped_ncp"] = {"median": float(np.median(c)), "p90": float(np.quantile(c, 0.9)), "max": float(c.max()),
+                             "le_tol_fraction": float(np.mean(c <= tol))}
+    return out
+
+
 def kernel_source_hash():
     """SHA-256 of the step kernel's sources: DRAM counters taken from another version are stale."""
     import hashlib
@@ -404,7 +424,7 @@ def run_gpu(args, rank, world):
         torch.cuda.synchronize()
         barrier()
         torch.cuda.synchronize()
-        ms, ms_step, rows, its, conv = [], [], [], [], []
+        ms, ms_step, rows, its, conv, ncp, status = [], [], [], [], [], [], []
         torch.cuda.nvtx.range_push(f"timed_{name}")
         for k in range(args.warmup, total_steps):
             flush.zero_()
@@ -420,10 +440,13 @@ def run_gpu(args, rank, world):
             rows.append(rep["num_rows"].copy())
             its.append(rep["iterations"].copy())
             conv.append(float(np.mean(rep["status"] == 0)))
+            ncp.append(rep["r_ncp"].copy())
+            status.append(rep["status"].copy())
         torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
         barrier()
-        return st, ms, np.concatenate(rows), np.concatenate(its), conv, ms_step
+        return st, ms, np.concatenate(rows), np.concatenate(its), conv, ms_step, np.concatenate(ncp), \
+            np.concatenate(status)
 
     def reduce_max(v):
         return max_over_ranks(v, world, dev)
@@ -439,12 +462,13 @@ def run_gpu(args, rank, world):
     clocks = sampler.stop()
     units = job_units(W, args.steps, world)
     variants = {}
-    for name, (_, ms, rows, its, conv, _) in results.items():
+    for name, (_, ms, rows, its, conv, _, ncp, status) in results.items():
         t = reduce_max(sum(ms) / 1e3)
         variants[name] = {"value": units / t, "ms_per_step": 1e3 * t / args.steps,
-                          "mean_iterations": float(its.mean()), "converged_fraction": float(np.mean(conv))}
+                          "mean_iterations": float(its.mean()), "converged_fraction": float(np.mean(conv)),
+                          **ncp_report(ncp, status, its, args.tol, args.iters, units / t)}
     head = "mixed_learned_warm" if nets else "mixed_cached_warm"
-    st_h, ms_h, rows_h, its_h, _, ms_step_h = results[head]
+    st_h, ms_h, rows_h, its_h, _, ms_step_h, _, _ = results[head]
     v_head = variants[head]["value"]
     t_head = units / v_head
 

@@ -51,8 +51,8 @@ typedef enum {
     KAMINO_E_TOPOLOGY = 2,      /* inconsistent world description (indices, offsets, masses)   */
     KAMINO_E_NOMEM = 3,         /* device allocation failed or caller buffer too small        */
     KAMINO_E_CUDA = 4,          /* a CUDA runtime call failed (also: no device present)       */
-    KAMINO_E_NONFINITE = 5,     /* reserved for per-world status words (see kamino_residual)   */
-    KAMINO_E_TIMEOUT = 6,       /* reserved: every device loop of this library is bounded     */
+    KAMINO_E_NONFINITE = 5,     /* not returned: per-world failures are status bits (kamino_residual) */
+    KAMINO_E_TIMEOUT = 6,       /* not returned: a device wait that expires sets KAMINO_WORLD_TIMEOUT */
     KAMINO_E_UNSUPPORTED = 7    /* a size this build does not support (e.g. too many rows)     */
 } kamino_status;
 
@@ -72,8 +72,11 @@ enum { KAMINO_FP32 = 0, KAMINO_FP64 = 1, KAMINO_MIXED = 2 };
  * supplied by the caller through KAMINO_BUF_WARM (e.g. a learned predictor). */
 enum { KAMINO_WARM_COLD = 0, KAMINO_WARM_CACHED = 1, KAMINO_WARM_EXTERNAL = 2 };
 
-/* per-world status bits in kamino_residual.status */
-enum { KAMINO_WORLD_NOT_CONVERGED = 1, KAMINO_WORLD_NONFINITE = 2 };
+/* per-world status bits in kamino_residual.status.  NONFINITE: the step produced a non-finite
+ * velocity; the world's state and impulse cache are left as they were before the step.  TIMEOUT: a
+ * bounded device wait (the tensor cores' completion signal in the mixed-precision factorisation)
+ * expired twice; the world is abandoned for this step, its state left as it was. */
+enum { KAMINO_WORLD_NOT_CONVERGED = 1, KAMINO_WORLD_NONFINITE = 2, KAMINO_WORLD_TIMEOUT = 4 };
 
 typedef struct {
     double eta;        /* proximal regularisation, Alg. 1 (scaled units), >= 0              */
@@ -84,10 +87,24 @@ typedef struct {
     int32_t precond;   /* 1: Jacobi preconditioning P = diag(D)^-1/2 (Sec. 4.1)              */
     int32_t warm_mode; /* KAMINO_WARM_*                                                       */
     int32_t refine64;  /* 1: when tol < KAMINO_REFINE64_BELOW, once r_p and r_d fall below that
-                        * level the right-hand side and the refinement residual b + A x of every
-                        * PADMM solve are formed in FP64 (FP32 and MIXED precision; FP64 worlds
-                        * always are).  0: FP32 throughout.                                       */
+                        * level the PADMM iteration finishes in FP64 refinement: the right-hand
+                        * side (from the FP64 free velocity), the refinement residual b + A x and
+                        * the iterates x, y, z are FP64, the correction still comes from the
+                        * reduced-precision inverse (FP32 and MIXED precision; FP64 worlds always
+                        * are FP64).  0: FP32 throughout.                                         */
+    int32_t integrator; /* KAMINO_INTEGRATOR_*: time stepping of Sec. 3                            */
+    int32_t cr_iters;  /* 0: dense formulation (the Delassus matrix assembled and factorised once
+                        * per step, Sec. 5.1).  k >= 1: sparse formulation (Sec. 5.1): D applied
+                        * matrix-free from the rows, each PADMM x-step k Conjugate Residual
+                        * iterations warm-started at the previous x (the paper uses 9)         */
 } kamino_solver_params;
+
+/* Time stepping (Sec. 3).  EULER: semi-implicit Euler, everything evaluated at the start-of-step
+ * pose q-, then q+ = q- (+) dt u+.  MIDPOINT: Moreau-Jean, kinematics, rows, contacts and biases
+ * evaluated at the half-step pose q_m = q- (+) (dt/2) u-, then q+ = q_m (+) (dt/2) u+.  (+) moves
+ * positions along v and orientations by the exponential map of the world-frame angular velocity. */
+enum { KAMINO_INTEGRATOR_EULER = 0, KAMINO_INTEGRATOR_MIDPOINT = 1 };
+#define KAMINO_MAX_CR_ITERS 64
 
 /* Scaled-unit residual level below which refine64 switches the refinement residual to FP64: the
  * FP32 residual's own rounding (~1e-6 on the closed-loop bipeds) is then no longer small beside it. */
@@ -123,7 +140,26 @@ typedef struct {
     const double *body_q0;              /* [B*7] initial poses (NULL: origin, identity)         */
     const double *body_u0;              /* [B*6] initial twists (NULL: zero)                    */
     kamino_solver_params params;
+    /* Joint-space dynamics on the joint coordinate d of revolute and prismatic joints (Sec. 3; Eq. 2's
+     * R and v*, Eq. 4's D = J M^-1 J^T + R).  NULL: none.
+     * joint_drive[j*5] = (mode, Kp, Kd, armature, damping), all >= 0 and finite.  mode
+     * KAMINO_DRIVE_PD: the joint's actuation value is the position target of an implicit PD
+     * controller (zero velocity target) and is not applied as a torque; KAMINO_DRIVE_TORQUE: the
+     * actuation stays a torque/force and the row carries armature and damping only.  A joint with a
+     * nonzero drive gets one regularised row after the joint rows, whose impulse over the step is
+     * lambda = I_a (d'- - d'+) + dt Kp (target - d - dt d'+) - dt (Kd + b) d'+, i.e. R = 1/C and
+     * v* = -(I_a d'- + dt Kp (target - d)) / C with C = I_a + dt^2 Kp + dt (Kd + b).
+     * joint_limit[j*2] = (lower, upper) on d, +-INFINITY for none: every finite bound is a unilateral
+     * row 0 <= lambda ⟂ g >= 0 (g = d - lower, upper - d), active when g < params.margin, with the
+     * contact normal's bias (g/dt while g > 0, beta g/dt once violated).  Constraint rows of a world
+     * are then: joint rows, drive rows (joint order), active limit rows (joint order, lower before
+     * upper), contact triples; the impulse cache holds the joint and drive rows, one impulse per
+     * finite bound, then 3 per contact candidate. */
+    const double *joint_drive;          /* [J*5] or NULL                                        */
+    const double *joint_limit;          /* [J*2] or NULL                                        */
 } kamino_model_desc;
+
+enum { KAMINO_DRIVE_TORQUE = 0, KAMINO_DRIVE_PD = 1 };
 
 typedef struct {
     int32_t num_worlds;
@@ -146,7 +182,11 @@ typedef struct {
     float r_primal;            /* ||x - y||_inf   (scaled units)                              */
     float r_dual;              /* ||eta (x - x_prev) + rho (y - y_hat_prev)||_inf             */
     float r_compl;             /* max over contacts |y_k . z_k|                               */
-    float reserved;
+    float r_ncp;               /* natural-map NCP residual of the returned (lambda, u+) on the
+                                  contact blocks (Eq. 3), scaled units: with v~ = P (J u+ + v*)
+                                  and lambda~ = P^-1 lambda, max over contacts k of
+                                  || lambda~_k - Pi_K(lambda~_k - (v~_k + Gamma(v~_k))) ||_inf
+                                  (0 without contacts)                                          */
 } kamino_residual;
 
 /* Buffers of a state, for zero-copy access (kamino_state_get). Element type is float for
@@ -155,8 +195,9 @@ typedef enum {
     KAMINO_BUF_BODY_Q = 0,     /* [B*7]  poses                                               */
     KAMINO_BUF_BODY_U = 1,     /* [B*6]  twists                                              */
     KAMINO_BUF_CACHE = 2,      /* [cache_len] impulses lambda* of the last step, physical units:
-                                  world w's joint rows, then 3 per contact CANDIDATE (zero for
-                                  candidates that were not active)                          */
+                                  world w's joint and drive rows, one per joint-limit bound, then
+                                  3 per contact CANDIDATE (zero for limits and candidates that
+                                  were not active)                                           */
     KAMINO_BUF_WARM = 3,       /* [cache_len] caller-supplied initial impulses (warm_mode 2)  */
     KAMINO_BUF_RESIDUAL = 4,   /* [W] kamino_residual                                         */
     KAMINO_BUF_TAU = 5         /* [W*n_act_max] actuation staging buffer: fill it (upload or

@@ -56,6 +56,11 @@ kamino_status check_params(const kamino_solver_params &p) {
     if (!(p.margin >= 0.0) || !std::isfinite(p.margin)) return fail(KAMINO_E_INVALID_ARG, "params.margin must be >= 0");
     if (p.warm_mode < KAMINO_WARM_COLD || p.warm_mode > KAMINO_WARM_EXTERNAL)
         return fail(KAMINO_E_INVALID_ARG, "params.warm_mode %d is not a KAMINO_WARM_* value", p.warm_mode);
+    if (p.integrator != KAMINO_INTEGRATOR_EULER && p.integrator != KAMINO_INTEGRATOR_MIDPOINT)
+        return fail(KAMINO_E_INVALID_ARG, "params.integrator %d is not a KAMINO_INTEGRATOR_* value", p.integrator);
+    if (p.cr_iters < 0 || p.cr_iters > KAMINO_MAX_CR_ITERS)
+        return fail(KAMINO_E_INVALID_ARG, "params.cr_iters must be in [0, %d] (got %d)", KAMINO_MAX_CR_ITERS, p.cr_iters);
+    if (p.cr_iters > 0) return fail(KAMINO_E_UNSUPPORTED, "the sparse formulation (params.cr_iters > 0) is not built yet");
     return KAMINO_OK;
 }
 
@@ -82,8 +87,11 @@ struct kamino_model_s {
     kamino_solver_params params{};
     // device arrays
     std::vector<void *> allocs;
-    int4 *world_a = nullptr, *world_b = nullptr, *joint_meta = nullptr;
-    int *joint_row = nullptr, *contact_body = nullptr;
+    int4 *world_a = nullptr, *world_b = nullptr, *world_c = nullptr, *joint_meta = nullptr;
+    int *joint_row = nullptr, *contact_body = nullptr, *joint_drow = nullptr, *joint_lslot = nullptr;
+    double *joint_dyn = nullptr;
+    int nl_max = 0;                        // joint-limit candidates of one world
+    std::vector<int> world_cache;          // impulse-cache length of every world
     void *world_mu = nullptr, *body_mass = nullptr, *body_inertia = nullptr, *joint_frames = nullptr;
     void *contact_point = nullptr, *hf_heights = nullptr, *q0 = nullptr, *u0 = nullptr;
     int terrain_kind = 0, hf_nx = 0, hf_ny = 0;
@@ -141,13 +149,26 @@ std::vector<T> convert(const double *src, size_t n) {
     return v;
 }
 
+// Host arrays of the joint-space dynamics (empty when the model has none).
+struct JointDyn {
+    std::vector<int4> wc;       // per world (limit candidates, 0, 0, 0)
+    std::vector<int> drow, lslot;
+    std::vector<double> dyn;    // [J*8]
+};
+
 template <typename T>
 kamino_status build_device(kamino_model_s *m, const kamino_model_desc *d, const std::vector<int4> &wa,
                            const std::vector<int4> &wb, const std::vector<int4> &jm, const std::vector<int> &jrow,
-                           const std::vector<double> &frames, const std::vector<double> &q0) {
+                           const std::vector<double> &frames, const std::vector<double> &q0, const JointDyn &jd) {
     kamino_status s;
     if ((s = upload<T>(m, (void **)&m->world_a, wa.data(), wa.size() * sizeof(int4)))) return s;
     if ((s = upload<T>(m, (void **)&m->world_b, wb.data(), wb.size() * sizeof(int4)))) return s;
+    if (!jd.dyn.empty()) {
+        if ((s = upload<T>(m, (void **)&m->world_c, jd.wc.data(), jd.wc.size() * sizeof(int4)))) return s;
+        if ((s = upload<T>(m, (void **)&m->joint_drow, jd.drow.data(), jd.drow.size() * sizeof(int)))) return s;
+        if ((s = upload<T>(m, (void **)&m->joint_lslot, jd.lslot.data(), jd.lslot.size() * sizeof(int)))) return s;
+        if ((s = upload<T>(m, (void **)&m->joint_dyn, jd.dyn.data(), jd.dyn.size() * sizeof(double)))) return s;
+    }
     auto mu = convert<T>(d->world_mu, m->W);
     if ((s = upload<T>(m, &m->world_mu, mu.data(), mu.size() * sizeof(T)))) return s;
     auto mass = convert<T>(d->body_mass, m->B);
@@ -180,6 +201,10 @@ ModelView<T> view(const kamino_model_s *m) {
     v.n_act_max = m->n_act_max;
     v.world_a = m->world_a;
     v.world_b = m->world_b;
+    v.world_c = m->world_c;
+    v.joint_drow = m->joint_drow;
+    v.joint_lslot = m->joint_lslot;
+    v.joint_dyn = m->joint_dyn;
     v.world_mu = (const T *)m->world_mu;
     v.body_mass = (const T *)m->body_mass;
     v.body_inertia = (const T *)m->body_inertia;
@@ -209,8 +234,8 @@ size_t persistent_smem(const kamino_model_s *m, const Bucket &b, int group, int 
     if (b.units > kSlots * group) return 0;
     const int mp = std::max(((b.rows + 15) / 16) * 16, 16);
     if (mp > kMaxRowsPad) return 0;
-    const Layout L = esize(m) == sizeof(double) ? make_layout<double>(b.nb, b.nj, b.nc, mp, nbp)
-                                                : make_layout<float>(b.nb, b.nj, b.nc, mp, nbp);
+    const Layout L = esize(m) == sizeof(double) ? make_layout<double>(b.nb, b.nj, b.nc, mp, nbp, m->nl_max)
+                                                : make_layout<float>(b.nb, b.nj, b.nc, mp, nbp, m->nl_max);
     const size_t sl = align_up(L.total, 16);
     const int per = kThreads / group;
     const size_t total = per * sl + align_up(per * sizeof(int), 16);
@@ -296,6 +321,7 @@ StepArgs<T> make_args(kamino_state_s *st, double dt, int iters, double tol, cons
     a.nesterov = m->params.nesterov ? 1 : 0;
     a.precond = m->params.precond ? 1 : 0;
     a.mixed = m->precision == KAMINO_MIXED ? 1 : 0;
+    a.midpoint = m->params.integrator == KAMINO_INTEGRATOR_MIDPOINT ? 1 : 0;
     a.refine64 = m->params.refine64 ? 1 : 0;
     // the inverse may live in tensor memory when a world's shared memory keeps a second CTA off the SM
     // (the 512-column allocation then never waits for another CTA)
@@ -305,6 +331,7 @@ StepArgs<T> make_args(kamino_state_s *st, double dt, int iters, double tol, cons
     a.nj_max = m->nj_max;
     a.nc_max = m->nc_max;
     a.mp_max = m->mp_max;
+    a.nl_max = m->nl_max;
     return a;
 }
 
@@ -523,6 +550,14 @@ kamino_status kamino_model_create(const kamino_model_desc *d, kamino_model_t *ou
     std::vector<int4> wa(W), wb(W), jm(J);
     std::vector<int> jrow(J);
     std::vector<double> frames(14 * (size_t)J);
+    const bool has_dyn = J > 0 && (d->joint_drive != nullptr || d->joint_limit != nullptr);
+    JointDyn jd;
+    if (has_dyn) {
+        jd.wc.assign(W, make_int4(0, 0, 0, 0));
+        jd.drow.assign(J, -1);
+        jd.lslot.assign(J, -1);
+        jd.dyn.assign(8 * (size_t)J, 0.0);
+    }
     int cache = 0;
     for (int w = 0; w < W; ++w) {
         const int b0 = d->world_body_offset[w], nb = d->world_body_offset[w + 1] - b0;
@@ -565,6 +600,59 @@ kamino_status kamino_model_create(const kamino_model_desc *d, kamino_model_t *ou
             jrow[j] = row;
             row += rows_of(t);
         }
+        // joint-space dynamics: a drive row per driven joint after the joint rows, then one limit
+        // candidate per finite bound
+        int nlc = 0;
+        if (has_dyn) {
+            for (int j = j0; j < j0 + nj; ++j) {
+                const int t = d->joint_type[j];
+                const bool coord = t == KAMINO_JOINT_REVOLUTE || t == KAMINO_JOINT_PRISMATIC;
+                double *o = jd.dyn.data() + 8 * (size_t)j;
+                o[5] = -INFINITY; o[6] = INFINITY;
+                if (d->joint_drive) {
+                    const double *dr = d->joint_drive + 5 * (size_t)j;
+                    if (dr[0] != KAMINO_DRIVE_TORQUE && dr[0] != KAMINO_DRIVE_PD) {
+                        delete m;
+                        return fail(KAMINO_E_TOPOLOGY, "joint %d: drive mode %g is not a KAMINO_DRIVE_* value", j, dr[0]);
+                    }
+                    for (int k = 1; k < 5; ++k)
+                        if (!(dr[k] >= 0.0) || !std::isfinite(dr[k])) {
+                            delete m;
+                            return fail(KAMINO_E_TOPOLOGY, "joint %d: drive gains must be finite and >= 0", j);
+                        }
+                    const bool pd = dr[0] == KAMINO_DRIVE_PD;
+                    const bool any = dr[1] > 0.0 || dr[2] > 0.0 || dr[3] > 0.0 || dr[4] > 0.0;
+                    if (any && !coord) {
+                        delete m;
+                        return fail(KAMINO_E_TOPOLOGY, "joint %d: only revolute and prismatic joints carry drives", j);
+                    }
+                    for (int k = 0; k < 5; ++k) o[k] = dr[k];
+                    // torque mode applies the actuation as a force: its row holds armature and damping only
+                    if (pd ? any : (dr[3] > 0.0 || dr[4] > 0.0)) jd.drow[j] = row++;
+                }
+            }
+            for (int j = j0; j < j0 + nj; ++j) {
+                if (!d->joint_limit) break;
+                const double lo = d->joint_limit[2 * (size_t)j], hi = d->joint_limit[2 * (size_t)j + 1];
+                if (std::isnan(lo) || std::isnan(hi) || lo > hi || lo == INFINITY || hi == -INFINITY) {
+                    delete m;
+                    return fail(KAMINO_E_TOPOLOGY, "joint %d: limits (%g, %g) must satisfy lower <= upper", j, lo, hi);
+                }
+                const int nf = (std::isfinite(lo) ? 1 : 0) + (std::isfinite(hi) ? 1 : 0);
+                if (nf == 0) continue;
+                const int t = d->joint_type[j];
+                if (t != KAMINO_JOINT_REVOLUTE && t != KAMINO_JOINT_PRISMATIC) {
+                    delete m;
+                    return fail(KAMINO_E_TOPOLOGY, "joint %d: only revolute and prismatic joints carry limits", j);
+                }
+                double *o = jd.dyn.data() + 8 * (size_t)j;
+                o[5] = lo; o[6] = hi;
+                jd.lslot[j] = nlc;
+                nlc += nf;
+            }
+            jd.wc[w] = make_int4(nlc, 0, 0, 0);
+            m->nl_max = std::max(m->nl_max, nlc);
+        }
         for (int c = c0; c < c0 + nc; ++c) {
             if (d->contact_body[c] < 0 || d->contact_body[c] >= nb) {
                 delete m;
@@ -583,7 +671,7 @@ kamino_status kamino_model_create(const kamino_model_desc *d, kamino_model_t *ou
         wa[w] = make_int4(b0, j0, c0, cache);
         wb[w] = make_int4(nb, nj, nc, row);
         {
-            const int rows = row + 3 * nc;
+            const int rows = row + nlc + 3 * nc;
             const int rp = std::max(32, ((rows + 31) / 32) * 32);
             Bucket *bk = nullptr;
             for (auto &b : m->buckets)
@@ -595,13 +683,14 @@ kamino_status kamino_model_create(const kamino_model_desc *d, kamino_model_t *ou
             bk->nj = std::max(bk->nj, nj);
             bk->nc = std::max(bk->nc, nc);
             bk->rows = std::max(bk->rows, rows);
-            bk->units = std::max(bk->units, row + nc);
+            bk->units = std::max(bk->units, row + nlc + nc);
         }
-        cache += row + 3 * nc;
+        cache += row + nlc + 3 * nc;
+        m->world_cache.push_back(row + nlc + 3 * nc);
         m->nb_max = std::max(m->nb_max, nb);
         m->nj_max = std::max(m->nj_max, nj);
         m->nc_max = std::max(m->nc_max, nc);
-        m->max_rows = std::max(m->max_rows, row + 3 * nc);
+        m->max_rows = std::max(m->max_rows, row + nlc + 3 * nc);
         m->n_act_max = std::max(m->n_act_max, nact);
     }
     m->cache_len = cache;
@@ -610,8 +699,8 @@ kamino_status kamino_model_create(const kamino_model_desc *d, kamino_model_t *ou
     for (int nbp : {16, 8}) {
         const int mp = std::max(((m->max_rows + 15) / 16) * 16, 16);
         if (mp > kMaxRowsPad) continue;
-        const Layout L = esz == sizeof(double) ? make_layout<double>(m->nb_max, m->nj_max, m->nc_max, mp, nbp)
-                                               : make_layout<float>(m->nb_max, m->nj_max, m->nc_max, mp, nbp);
+        const Layout L = esz == sizeof(double) ? make_layout<double>(m->nb_max, m->nj_max, m->nc_max, mp, nbp, m->nl_max)
+                                               : make_layout<float>(m->nb_max, m->nj_max, m->nc_max, mp, nbp, m->nl_max);
         if (L.total <= kMaxSmem) {
             m->nb_panel = nbp;
             m->mp_max = mp;
@@ -643,8 +732,8 @@ kamino_status kamino_model_create(const kamino_model_desc *d, kamino_model_t *ou
             q0[7 * b + 6] = 1.0;
         }
     }
-    kamino_status st = d->precision == KAMINO_FP64 ? build_device<double>(m, d, wa, wb, jm, jrow, frames, q0)
-                                                   : build_device<float>(m, d, wa, wb, jm, jrow, frames, q0);
+    kamino_status st = d->precision == KAMINO_FP64 ? build_device<double>(m, d, wa, wb, jm, jrow, frames, q0, jd)
+                                                   : build_device<float>(m, d, wa, wb, jm, jrow, frames, q0, jd);
     if (st) { delete m; return st; }
     for (auto &b : m->buckets) {
         if ((st = upload<float>(m, (void **)&b.d_worlds, b.worlds.data(), b.worlds.size() * sizeof(int)))) {
@@ -1054,7 +1143,8 @@ kamino_status kamino_mlp_create(kamino_model_t m, const int32_t *worlds, int32_t
     const int4 ref = wb[worlds[0]];
     for (int i = 1; i < count; ++i) {
         const int4 c = wb[worlds[i]];
-        if (c.x != ref.x || c.y != ref.y || c.z != ref.z || c.w != ref.w)
+        if (c.x != ref.x || c.y != ref.y || c.z != ref.z || c.w != ref.w ||
+            m->world_cache[worlds[i]] != m->world_cache[worlds[0]])
             return fail(KAMINO_E_TOPOLOGY, "world %d does not match the sizes of world %d", worlds[i], worlds[0]);
     }
     auto *n = new kamino_mlp_s();
@@ -1062,7 +1152,7 @@ kamino_status kamino_mlp_create(kamino_model_t m, const int32_t *worlds, int32_t
     n->count = count;
     n->hidden = hidden;
     n->nact = m->n_act_max;
-    n->dout = ref.w + 3 * ref.z;
+    n->dout = m->world_cache[worlds[0]];   // the world's impulse-cache layout
     n->din = 13 * ref.x + 1 + n->nact + 4 * ref.z + n->dout;   // ... + the previous step's impulses
     n->max_batch = std::max(max_batch, count);
     n->dims[0] = n->din;

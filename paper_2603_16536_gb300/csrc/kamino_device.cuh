@@ -67,6 +67,29 @@ __device__ __forceinline__ void symvec3d(const T *S, const double *v, double *o)
     o[2] = s4 * v[0] + s5 * v[1] + s2 * v[2];
 }
 
+// Pose advanced along a twist for a time h (Sec. 3, FP64): r + h v and exp(h w) (x) q, with w in
+// the world frame (hence the left product) and the result renormalised.  q = (r[3], quat xyzw[4]).
+__device__ __forceinline__ void pose_advance(const double *q, const double *v, const double *w, double h,
+                                             double *out) {
+    const double th[3] = {h * w[0], h * w[1], h * w[2]};
+    const double ang = sqrt(th[0] * th[0] + th[1] * th[1] + th[2] * th[2]);
+    double dq[4];
+    if (ang > 0.0) {
+        const double s = sin(0.5 * ang) / ang;
+        dq[0] = s * th[0]; dq[1] = s * th[1]; dq[2] = s * th[2]; dq[3] = cos(0.5 * ang);
+    } else {
+        dq[0] = dq[1] = dq[2] = 0.0; dq[3] = 1.0;
+    }
+    const double qx = q[3], qy = q[4], qz = q[5], qw = q[6];
+    const double qn[4] = {dq[3] * qx + dq[0] * qw + dq[1] * qz - dq[2] * qy,
+                          dq[3] * qy - dq[0] * qz + dq[1] * qw + dq[2] * qx,
+                          dq[3] * qz + dq[0] * qy - dq[1] * qx + dq[2] * qw,
+                          dq[3] * qw - dq[0] * qx - dq[1] * qy - dq[2] * qz};
+    const double nrm = 1.0 / sqrt(qn[0] * qn[0] + qn[1] * qn[1] + qn[2] * qn[2] + qn[3] * qn[3]);
+    for (int k = 0; k < 3; ++k) out[k] = q[k] + h * v[k];
+    for (int k = 0; k < 4; ++k) out[3 + k] = qn[k] * nrm;
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -23,12 +23,17 @@ struct ModelView {
     int num_worlds;
     int n_act_max;
     const int4 *world_a;       // (body_offset, joint_offset, contact_offset, cache_offset)
-    const int4 *world_b;       // (num_bodies, num_joints, num_candidates, num_bilateral_rows)
+    const int4 *world_b;       // (num_bodies, num_joints, num_candidates, fixed rows: joint + drive rows)
+    const int4 *world_c;       // (limit candidates, 0, 0, 0); nullptr when no world has joint limits
     const T *world_mu;         // [W]
     const T *body_mass;        // [B]
     const T *body_inertia;     // [B*3]
     const int4 *joint_meta;    // (type, parent, child, actuator)
     const int *joint_row;      // first row of the joint inside its world
+    // joint-space dynamics (Sec. 3, Eq. 2's R and v*); nullptr when the model has none
+    const int *joint_drow;        // [J] row of the joint's drive row inside its world, or -1
+    const int *joint_lslot;       // [J] first limit candidate of the joint inside its world, or -1
+    const double *joint_dyn;      // [J*8] (mode, Kp, Kd, armature, damping, lower, upper, 0)
     // position-level data stays FP64 whatever T is: joint errors and contact distances are
     // multiplied by beta / dt in the bias, which would amplify FP32 rounding of anchors by 100-200
     const double *joint_frames;   // [J*14]: parent pos3 quat4, child pos3 quat4
@@ -53,10 +58,11 @@ struct StepArgs {
     T dt, tol, eta, rho, beta, margin;
     int iters, nesterov, precond, warm_mode;
     int mixed;                 // 1: BF16 tiles of the inverse on tensor cores (KAMINO_MIXED)
+    int midpoint;              // 1: Moreau-Jean midpoint scheme (KAMINO_INTEGRATOR_MIDPOINT)
     int refine64;              // 1: FP64 right-hand side and refinement residual near convergence
     int tmem;                  // 1: keep the swept inverse in tensor memory (FP32, whole-CTA groups, mp <= 256)
     // shared-memory layout bounds (maxima over the launched worlds)
-    int nb_max, nj_max, nc_max, mp_max;
+    int nb_max, nj_max, nc_max, mp_max, nl_max;
 };
 
 // Persistent launch over one bucket of worlds (see step_persistent).
@@ -70,8 +76,9 @@ struct PersistentArgs {
 
 // Byte offsets of the per-world shared-memory working set.
 struct Layout {
-    size_t bq, bu, bR, bRd, bI, bIinv, bminv, bufree, jwr, cid, cslot, rbody, rJ, rvs;
-    size_t vf, p, x, xn, y, z, yh, zh, b, mut, mui, wv, fb, bro, brow, X, A, red, misc, total;
+    size_t bq, bu, bRd, bI, bIinv, bminv, bufree, jwr, cid, cslot, rbody, rJ, rvs, rreg;
+    size_t lgap, lJ, lrank, lcid;
+    size_t vfd, p, x, xn, y, z, yh, zh, b, mut, mui, wv, fb, bro, brow, X, A, red, misc, total;
 };
 
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -81,15 +88,15 @@ __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a -
 // non-decreasing in mp, so a layout sized for the largest world fits every smaller one.
 __host__ __device__ inline int panel_ld(int mp) { return mp + (mp % 32 == 0 ? 8 : 24); }
 
+// nl: joint-limit candidates per world (0 when no world has limits).
 template <typename T>
-__host__ __device__ inline Layout make_layout(int nb, int nj, int nc, int mp, int nb_panel) {
+__host__ __device__ inline Layout make_layout(int nb, int nj, int nc, int mp, int nb_panel, int nl = 0) {
     Layout L{};
     size_t o = 0;
     auto take = [&](size_t &field, size_t bytes) { field = o; o = align_up(o + bytes, 16); };
     const size_t s = sizeof(T);
-    take(L.bq, nb * 7 * s);
+    take(L.bq, nb * 7 * sizeof(double));   // the pose the step is evaluated at, FP64
     take(L.bu, nb * 6 * s);
-    take(L.bR, nb * 9 * s);
     take(L.bRd, nb * 9 * sizeof(double));
     take(L.bI, nb * 3 * s);
     take(L.bIinv, nb * 6 * s);
@@ -100,8 +107,16 @@ __host__ __device__ inline Layout make_layout(int nb, int nj, int nc, int mp, in
     take(L.cslot, nc * sizeof(int));
     take(L.rbody, mp * 2 * sizeof(int));
     take(L.rJ, mp * 12 * s);
-    take(L.rvs, mp * s);
-    take(L.vf, mp * s);
+    // the bias v* and the free velocity v_f are also kept in FP64: v_f has components outside the
+    // range of J (redundant loop rows, contacts tied together by the joints) to which the dual
+    // problem's solution is very sensitive, so its FP32 rounding alone moves u+ by up to ~2e-4
+    take(L.rvs, mp * sizeof(double));
+    take(L.rreg, mp * s);                  // R of Eq. 4 per row (drive rows; zero elsewhere)
+    take(L.lgap, nl * sizeof(double));     // joint-limit candidates: gap, row blocks, rank, and the
+    take(L.lJ, nl * 12 * s);               // candidate of every active limit row
+    take(L.lrank, nl * sizeof(int));
+    take(L.lcid, nl * sizeof(int));
+    take(L.vfd, mp * sizeof(double));
     take(L.p, mp * s);
     take(L.x, mp * s);
     take(L.xn, mp * s);

@@ -59,13 +59,13 @@ __device__ __forceinline__ int pidx(int i, int j, int mp) {  // requires i >= j
 __device__ __forceinline__ int sidx(int i, int j, int mp) { return i >= j ? pidx(i, j, mp) : pidx(j, i, mp); }
 
 template <typename T>
-__device__ __forceinline__ void put_row(int *rbody, T *rJ, T *rvs, int row, int ba, int bb, const double *Ja,
+__device__ __forceinline__ void put_row(int *rbody, T *rJ, double *rvs, int row, int ba, int bb, const double *Ja,
                                         const double *Jb, double vstar) {
     rbody[2 * row] = ba;
     rbody[2 * row + 1] = bb;
     T *J = rJ + 12 * row;
     for (int k = 0; k < 6; ++k) { J[k] = T(Ja[k]); J[6 + k] = T(Jb[k]); }
-    rvs[row] = T(vstar);
+    rvs[row] = vstar;
 }
 
 // Joint rows of one joint (Sec. 3): positional rows along world axes, angular rows along the
@@ -73,14 +73,14 @@ __device__ __forceinline__ void put_row(int *rbody, T *rJ, T *rvs, int row, int 
 // position-level quantities (anchors, frame axes, errors f) are formed in FP64 from the stored
 // pose, then J and the bias are rounded to T.
 template <typename T>
-__device__ void joint_rows(int type, int par, int ch, const double *fr, const T *bq, const double *bRd, int row0,
-                           double kbias, int *rbody, T *rJ, T *rvs, bool actuated, T value, T *wr) {
+__device__ void joint_rows(int type, int par, int ch, const double *fr, const double *bq, const double *bRd, int row0,
+                           double kbias, int *rbody, T *rJ, double *rvs, bool actuated, T value, T *wr) {
     double rA[3] = {0.0, 0.0, 0.0}, RA[9] = {1.0, 0.0, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0, 1.0};
     if (par >= 0) {
-        for (int k = 0; k < 3; ++k) rA[k] = (double)bq[7 * par + k];
+        for (int k = 0; k < 3; ++k) rA[k] = bq[7 * par + k];
         for (int k = 0; k < 9; ++k) RA[k] = bRd[9 * par + k];
     }
-    const double rB[3] = {(double)bq[7 * ch], (double)bq[7 * ch + 1], (double)bq[7 * ch + 2]};
+    const double rB[3] = {bq[7 * ch], bq[7 * ch + 1], bq[7 * ch + 2]};
     const double *RB = bRd + 9 * ch;
     double cA[3], cB[3], pA[3], pB[3], QA[9], QB[9], FA[9], FB[9];
     matvec3(RA, fr, cA);
@@ -154,6 +154,48 @@ __device__ void joint_rows(int type, int par, int ch, const double *fr, const T 
             cross3(cB, a[2], t);
             for (int r = 0; r < 3; ++r) { wr[6 + r] = T(v * a[2][r]); wr[9 + r] = T(v * t[r]); }
         }
+    }
+}
+
+// The joint coordinate d(q) and its row J_d (J_d u = d-dot) of a revolute or prismatic joint
+// (Sec. 3, the coordinate drives and limits act on), in FP64: for a revolute the angle of the child
+// frame's e1 about the hinge a3, measured from a1 towards a2, d = atan2(a2.b1, a1.b1),
+// J_d = [0, -a3 | 0, a3]; for a prismatic the slide d = a3.(p_B - p_A),
+// J_d = [-a3, -(p_B - r_A) x a3 | a3, c_B x a3].
+__device__ void joint_coordinate(int type, int par, int ch, const double *fr, const double *bq, const double *bRd,
+                                 double *d, double *Ja, double *Jb) {
+    double rA[3] = {0.0, 0.0, 0.0}, RA[9] = {1.0, 0.0, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0, 1.0};
+    if (par >= 0) {
+        for (int k = 0; k < 3; ++k) rA[k] = bq[7 * par + k];
+        for (int k = 0; k < 9; ++k) RA[k] = bRd[9 * par + k];
+    }
+    const double *RB = bRd + 9 * ch;
+    double QA[9], QB[9], FA[9], FB[9], cA[3], cB[3];
+    quat_rot(fr + 3, QA);
+    quat_rot(fr + 10, QB);
+    matmul3(RA, QA, FA);
+    matmul3(RB, QB, FB);
+    const double a1[3] = {FA[0], FA[3], FA[6]}, a2[3] = {FA[1], FA[4], FA[7]}, a3[3] = {FA[2], FA[5], FA[8]};
+    for (int k = 0; k < 6; ++k) { Ja[k] = 0.0; Jb[k] = 0.0; }
+    if (type == KAMINO_JOINT_REVOLUTE) {
+        const double b1[3] = {FB[0], FB[3], FB[6]};
+        *d = atan2(dot3(a2, b1), dot3(a1, b1));
+        for (int k = 0; k < 3; ++k) { Ja[3 + k] = -a3[k]; Jb[3 + k] = a3[k]; }
+    } else {
+        matvec3(RA, fr, cA);
+        matvec3(RB, fr + 7, cB);
+        double pA[3], pB[3], lev[3], t[3];
+        for (int k = 0; k < 3; ++k) {
+            pA[k] = rA[k] + cA[k];
+            pB[k] = bq[7 * ch + k] + cB[k];
+            lev[k] = pB[k] - rA[k];
+        }
+        const double dp[3] = {pB[0] - pA[0], pB[1] - pA[1], pB[2] - pA[2]};
+        *d = dot3(a3, dp);
+        cross3(lev, a3, t);
+        for (int k = 0; k < 3; ++k) { Ja[k] = -a3[k]; Ja[3 + k] = -t[k]; }
+        cross3(cB, a3, t);
+        for (int k = 0; k < 3; ++k) { Jb[k] = a3[k]; Jb[3 + k] = t[k]; }
     }
 }
 
@@ -706,7 +748,9 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
     return false;
 }
 
-__device__ void sweep_inverse_tmem(const float *A, int mp, float *X, uint32_t tbase, int *misc, const Group &g) {
+// Returns false (uniformly over the CTA) when the tensor cores' completion did not arrive within two
+// bounded waits; the world is then abandoned (KAMINO_WORLD_TIMEOUT) and its state left unchanged.
+__device__ bool sweep_inverse_tmem(const float *A, int mp, float *X, uint32_t tbase, int *misc, const Group &g) {
     constexpr int NB = 16;
     float *PT = X;                 // K-major [256 rows][16]: the panel P
     float *TN = X + 256 * 16;      // K-major [256 rows][16]: -T
@@ -839,9 +883,11 @@ __device__ void sweep_inverse_tmem(const float *A, int mp, float *X, uint32_t tb
                          :: "r"(mbar) : "memory");
         }
         bool ok = mbar_wait(mbar, (uint32_t)(panel & 1));
-        if (!ok) {
-            if (tid == 0) misc[1] = 1;                          // reported as a failed world
-            ok = mbar_wait(mbar, (uint32_t)(panel & 1));        // let the products finish before going on
+        if (!ok) ok = mbar_wait(mbar, (uint32_t)(panel & 1));  // a second bounded wait for the products
+        if (__syncthreads_or(!ok)) {                            // whole-CTA group: a uniform decision
+            if (tid == 0) misc[1] |= 2;
+            tmem_fence_after();
+            return false;
         }
         tmem_fence_after();
         // -- column block K := T on the rows outside K, A_KK^-1 negated on K (every warp, its rows)
@@ -880,6 +926,203 @@ __device__ void sweep_inverse_tmem(const float *A, int mp, float *X, uint32_t tb
         g.sync();
         tmem_fence_after();
     }
+    return true;
+}
+
+// ----------------------------------------------------------------------------- PADMM owner phases
+// FP64 iterates of the refinement end game (x, y, z, y^, z^ and the new y, z of an iteration across
+// its reduction barrier: 7 mp doubles) in shared memory that is
+// dead during the PADMM loop: the packed matrix region once the inverse lives in tensor memory, the
+// part of that region the BF16 tiles leave free, else the sweep scratch past the mat-vec partials
+// and the FP64 refinement vectors.  nullptr when none has room (the iterates then stay in FP32).
+template <typename T>
+__device__ __forceinline__ double *fp64_iterates(unsigned char *smem, const Layout &L, bool in_tmem, bool bf16_tiles,
+                                                 int mp, int nb, T *X) {
+    if constexpr (sizeof(T) != 4) {
+        return nullptr;
+    } else {
+        const size_t need = (size_t)7 * mp * sizeof(double);
+        const size_t a_bytes = L.red - L.A;
+        if (in_tmem && need <= a_bytes) return reinterpret_cast<double *>(smem + L.A);
+        if (bf16_tiles) {
+            const int nt = mp / 16;
+            const size_t tiles = align_up((size_t)nt * (nt + 1) / 2 * 512, 16);
+            if (tiles + need <= a_bytes) return reinterpret_cast<double *>(smem + L.A + tiles);
+        }
+        const size_t used = ((size_t)kWarps * mp + 2 * (size_t)mp + 12 * (size_t)nb) * sizeof(float);
+        if (used + need <= L.A - L.X) return reinterpret_cast<double *>(reinterpret_cast<unsigned char *>(X) + used);
+        return nullptr;
+    }
+}
+
+// Owner phase of a PADMM iteration (Alg. 1) for the units of this thread, with the iterates of type
+// V (T, or FP64 in the refinement end game): x^i = x^{i-1} + xn (the refined x-step),
+// y^i = Pi_K(x^i - z^/rho) (identity on joint rows, the Coulomb cone on contacts),
+// z^i = z^ - rho (x^i - y^i), and this thread's terms of the residuals r_p = ||x - y||,
+// r_d = ||eta (x^i - x^{i-1}) + rho (y^i - y^)||, r_c = |y_k . z_k| and of Nesterov's combined
+// residual.  The new iterates stay in registers; x^i and P x^i go to shared memory at once.
+template <typename V, typename T, int S>
+__device__ __forceinline__ void owner_update(const Group &g, int nunits, int nfix, int nbil, V *x, const T *xn, const V *yh,
+                                             const V *zh, const T *mut, const T *mui, const T *p, T *wv, T eta_, T rho_,
+                                             T irho_, V (&xnew)[S][3], V (&ynew)[S][3], V (&znew)[S][3], T &lrp,
+                                             T &lrd, T &lrc, T &lc) {
+    const V eta = V(eta_), rho = V(rho_), irho = V(irho_);
+#pragma unroll
+    for (int sl = 0; sl < S; ++sl)
+#pragma unroll
+        for (int t = 0; t < 3; ++t) xnew[sl][t] = ynew[sl][t] = znew[sl][t] = V(0);
+#pragma unroll
+    for (int sl = 0; sl < S; ++sl) {
+        const int u = g.tid + sl * g.size;
+        if (u >= nunits) continue;
+        if (u < nbil) {
+            // joint and drive rows: the identity; joint-limit rows (u >= nfix): the ray R+ (Sec. 3)
+            const V xv = x[u] + V(xn[u]);
+            V yv = xv - zh[u] * irho;
+            if (u >= nfix) yv = fmax(yv, V(0));
+            const V zv = zh[u] - rho * (xv - yv);
+            lrp = fmax(lrp, T(fabs(xv - yv)));
+            lrd = fmax(lrd, T(fabs(eta * (xv - x[u]) + rho * (yv - yh[u]))));
+            lc += T((zv - zh[u]) * (zv - zh[u]) * irho + rho * (yv - yh[u]) * (yv - yh[u]));
+            if (u >= nfix) lrc = fmax(lrc, T(fabs(yv * zv)));
+            xnew[sl][0] = xv; ynew[sl][0] = yv; znew[sl][0] = zv;
+            x[u] = xv;
+            wv[u] = T(V(p[u]) * xv);
+        } else {
+            const int k = u - nbil, r0 = nbil + 3 * k;
+            const V mu = V(mut[k]);
+            V v[3], yv[3], xv[3];
+#pragma unroll
+            for (int t = 0; t < 3; ++t) {
+                xv[t] = x[r0 + t] + V(xn[r0 + t]);
+                v[t] = xv[t] - zh[r0 + t] * irho;
+            }
+            const V tn = sqrt(v[0] * v[0] + v[1] * v[1]);
+            if (tn <= mu * v[2]) {
+                yv[0] = v[0]; yv[1] = v[1]; yv[2] = v[2];
+            } else if (mu * tn <= -v[2]) {
+                yv[0] = yv[1] = yv[2] = V(0);
+            } else {
+                const V nn = (mu * tn + v[2]) * V(mui[k]);
+                const V sc = mu * nn / tn;
+                yv[0] = sc * v[0]; yv[1] = sc * v[1]; yv[2] = nn;
+            }
+            V ydz = V(0);
+#pragma unroll
+            for (int t = 0; t < 3; ++t) {
+                const V zv = zh[r0 + t] - rho * (xv[t] - yv[t]);
+                lrp = fmax(lrp, T(fabs(xv[t] - yv[t])));
+                lrd = fmax(lrd, T(fabs(eta * (xv[t] - x[r0 + t]) + rho * (yv[t] - yh[r0 + t]))));
+                lc += T((zv - zh[r0 + t]) * (zv - zh[r0 + t]) * irho + rho * (yv[t] - yh[r0 + t]) * (yv[t] - yh[r0 + t]));
+                ydz += yv[t] * zv;
+                xnew[sl][t] = xv[t]; ynew[sl][t] = yv[t]; znew[sl][t] = zv;
+            }
+            lrc = fmax(lrc, T(fabs(ydz)));
+#pragma unroll
+            for (int t = 0; t < 3; ++t) {
+                x[r0 + t] = xv[t];
+                wv[r0 + t] = T(V(p[r0 + t]) * xv[t]);
+            }
+        }
+    }
+}
+
+// The rows of this thread's units from registers into a row vector and back.
+template <int S>
+__device__ __forceinline__ void stash_rows(const Group &g, int nunits, int nbil, const double (&v)[S][3], double *dst) {
+#pragma unroll
+    for (int sl = 0; sl < S; ++sl) {
+        const int u = g.tid + sl * g.size;
+        if (u >= nunits) continue;
+        const int r0 = u < nbil ? u : nbil + 3 * (u - nbil), cnt = u < nbil ? 1 : 3;
+        for (int t = 0; t < cnt; ++t) dst[r0 + t] = v[sl][t];
+    }
+}
+template <int S>
+__device__ __forceinline__ void unstash_rows(const Group &g, int nunits, int nbil, const double *src, double (&v)[S][3]) {
+#pragma unroll
+    for (int sl = 0; sl < S; ++sl) {
+        const int u = g.tid + sl * g.size;
+#pragma unroll
+        for (int t = 0; t < 3; ++t) v[sl][t] = 0.0;
+        if (u >= nunits) continue;
+        const int r0 = u < nbil ? u : nbil + 3 * (u - nbil), cnt = u < nbil ? 1 : 3;
+        for (int t = 0; t < cnt; ++t) v[sl][t] = src[r0 + t];
+    }
+}
+
+// Commit of a PADMM iteration by the owners: Nesterov's extrapolation (or restart) of (y, z) into
+// (y^, z^) (Sec. 4.1), the new y, z, y^, z^, and the next iteration's right-hand side
+// b = v_f + Gamma(z^) - eta x - rho y^ - z^ (in FP64 from the FP64 v_f when `hp`).  `init64`, when
+// set, is the FP64 iterate block (x, y, z, y^, z^ of mp each) that takes over from this commit on.
+template <typename V, typename T, int S>
+__device__ __forceinline__ void owner_commit(const Group &g, int nunits, int nbil, V *y, V *z, V *yh, V *zh,
+                                             const double *vfd, const T *mut, T eta_, T rho_,
+                                             bool nesterov, bool restart, T beta_, const V (&xnew)[S][3],
+                                             const V (&ynew)[S][3], const V (&znew)[S][3], bool hp, T *bb, double *bbd,
+                                             double *init64, int mp) {
+    const V beta_n = V(beta_);
+#pragma unroll
+    for (int sl = 0; sl < S; ++sl) {
+        const int u = g.tid + sl * g.size;
+        if (u >= nunits) continue;
+        const int r0 = u < nbil ? u : nbil + 3 * (u - nbil);
+        const int cnt = u < nbil ? 1 : 3;
+        // all loads first and every new value kept in registers: the vectors share one
+        // shared-memory buffer, so a value stored and read back would wait for the store
+        V yo[3], zo[3], yhv[3], zhv[3];
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+            const bool on = t < cnt;
+            yo[t] = on ? y[r0 + t] : V(0);
+            zo[t] = on ? z[r0 + t] : V(0);
+        }
+        const T mu = cnt == 3 ? mut[u - nbil] : T(0);
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+            const V yv = ynew[sl][t], zv = znew[sl][t];
+            if (!nesterov) { yhv[t] = yv; zhv[t] = zv; }
+            else if (restart) { yhv[t] = yo[t]; zhv[t] = zo[t]; }
+            else { yhv[t] = yv + beta_n * (yv - yo[t]); zhv[t] = zv + beta_n * (zv - zo[t]); }
+        }
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+            if (t >= cnt) break;
+            const int r = r0 + t;
+            yh[r] = yhv[t]; zh[r] = zhv[t];
+            y[r] = ynew[sl][t]; z[r] = znew[sl][t];
+        }
+        if (init64) {
+#pragma unroll
+            for (int t = 0; t < 3; ++t) {
+                if (t >= cnt) break;
+                const int r = r0 + t;
+                init64[r] = (double)xnew[sl][t];
+                init64[mp + r] = (double)ynew[sl][t];
+                init64[2 * mp + r] = (double)znew[sl][t];
+                init64[3 * mp + r] = (double)yhv[t];
+                init64[4 * mp + r] = (double)zhv[t];
+            }
+        }
+        if (hp) {
+            const double z0 = (double)zhv[0], z1 = (double)zhv[1];
+            const double sd = cnt == 3 ? (double)mu * sqrt(z0 * z0 + z1 * z1) : 0.0;
+#pragma unroll
+            for (int t = 0; t < 3; ++t) {
+                if (t >= cnt) break;
+                bbd[r0 + t] = vfd[r0 + t] + (t == 2 ? sd : 0.0) - (double)eta_ * (double)xnew[sl][t] -
+                              (double)rho_ * (double)yhv[t] - (double)zhv[t];
+            }
+        } else {
+            const V eta = V(eta_), rho = V(rho_);
+            const V sv = cnt == 3 ? V(mu) * sqrt(zhv[0] * zhv[0] + zhv[1] * zhv[1]) : V(0);
+#pragma unroll
+            for (int t = 0; t < 3; ++t) {
+                if (t >= cnt) break;
+                bb[r0 + t] = T(V(vfd[r0 + t]) + (t == 2 ? sv : V(0)) - eta * xnew[sl][t] - rho * yhv[t] - zhv[t]);
+            }
+        }
+    }
 }
 
 // ----------------------------------------------------------------------------- the step kernel
@@ -893,15 +1136,20 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
     const ModelView<T> &M = a.m;
     const int4 wa = M.world_a[w], wb = M.world_b[w];
     const int b0 = wa.x, j0 = wa.y, c0 = wa.z, k0 = wa.w;
-    const int nb = wb.x, nj = wb.y, nc = wb.z, nbil = wb.w;
-    const Layout L = make_layout<T>(a.nb_max, a.nj_max, a.nc_max, a.mp_max, NB);
-    T *bq = (T *)(smem + L.bq), *bu = (T *)(smem + L.bu), *bR = (T *)(smem + L.bR), *bI = (T *)(smem + L.bI);
+    const int nb = wb.x, nj = wb.y, nc = wb.z, nfix = wb.w;
+    const int nlc = M.world_c ? M.world_c[w].x : 0;       // joint-limit candidates
+    const Layout L = make_layout<T>(a.nb_max, a.nj_max, a.nc_max, a.mp_max, NB, a.nl_max);
+    double *bq = (double *)(smem + L.bq);
+    T *bu = (T *)(smem + L.bu), *bI = (T *)(smem + L.bI);
     double *bRd = (double *)(smem + L.bRd);
     T *bIinv = (T *)(smem + L.bIinv), *bminv = (T *)(smem + L.bminv), *bufree = (T *)(smem + L.bufree);
     T *jwr = (T *)(smem + L.jwr);
     int *cid = (int *)(smem + L.cid), *cslot = (int *)(smem + L.cslot), *rbody = (int *)(smem + L.rbody);
-    T *rJ = (T *)(smem + L.rJ), *rvs = (T *)(smem + L.rvs);
-    T *vf = (T *)(smem + L.vf), *p = (T *)(smem + L.p), *x = (T *)(smem + L.x), *xn = (T *)(smem + L.xn);
+    T *rJ = (T *)(smem + L.rJ);
+    double *rvs = (double *)(smem + L.rvs), *vfd = (double *)(smem + L.vfd), *lgap = (double *)(smem + L.lgap);
+    T *rreg = (T *)(smem + L.rreg), *lJ = (T *)(smem + L.lJ);
+    int *lrank = (int *)(smem + L.lrank), *lcid = (int *)(smem + L.lcid);
+    T *p = (T *)(smem + L.p), *x = (T *)(smem + L.x), *xn = (T *)(smem + L.xn);
     T *y = (T *)(smem + L.y), *z = (T *)(smem + L.z), *yh = (T *)(smem + L.yh), *zh = (T *)(smem + L.zh);
     T *bb = (T *)(smem + L.b), *mut = (T *)(smem + L.mut), *X = (T *)(smem + L.X), *A = (T *)(smem + L.A);
     T *mui = (T *)(smem + L.mui);
@@ -911,21 +1159,31 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
     int *bro = (int *)(smem + L.bro), *brow = (int *)(smem + L.brow);
     const T dt = a.dt, kbias = a.beta / a.dt;
     const double dtd = (double)a.dt, kbiasd = (double)a.beta / (double)a.dt;
-    if (tid == 0) misc[1] = 0;   // non-finite flag of this world
+    if (tid == 0) misc[1] = 0;   // failure bits of this world: 1 non-finite result, 2 tensor-core timeout
+    for (int r = tid; r < a.mp_max; r += nthr) rreg[r] = T(0);
     // ---- 1. body kinematics
     for (int i = tid; i < nb; i += nthr) {
         const T *gq = a.body_q + 7 * (size_t)(b0 + i);
         const T *gu = a.body_u + 6 * (size_t)(b0 + i);
-        double qd[4] = {(double)gq[3], (double)gq[4], (double)gq[5], (double)gq[6]};
-        const double qn = 1.0 / sqrt(qd[0] * qd[0] + qd[1] * qd[1] + qd[2] * qd[2] + qd[3] * qd[3]);
-        for (int k = 0; k < 4; ++k) qd[k] *= qn;
-        for (int k = 0; k < 3; ++k) bq[7 * i + k] = gq[k];
-        for (int k = 0; k < 4; ++k) bq[7 * i + 3 + k] = T(qd[k]);
+        double pose[7] = {(double)gq[0], (double)gq[1], (double)gq[2], (double)gq[3], (double)gq[4], (double)gq[5],
+                          (double)gq[6]};
+        const double qn = 1.0 / sqrt(pose[3] * pose[3] + pose[4] * pose[4] + pose[5] * pose[5] + pose[6] * pose[6]);
+        for (int k = 3; k < 7; ++k) pose[k] *= qn;
+        if (a.midpoint) {
+            // Moreau-Jean (Sec. 3): the step is evaluated at the half-step pose q_m = q (+) (dt/2) u-
+            const double v[3] = {(double)gu[0], (double)gu[1], (double)gu[2]};
+            const double om[3] = {(double)gu[3], (double)gu[4], (double)gu[5]};
+            double pm[7];
+            pose_advance(pose, v, om, 0.5 * dtd, pm);
+            for (int k = 0; k < 7; ++k) pose[k] = pm[k];
+        }
+        for (int k = 0; k < 7; ++k) bq[7 * i + k] = pose[k];
+        const double *qd = pose + 3;
         for (int k = 0; k < 6; ++k) bu[6 * i + k] = gu[k];
         double Rd[9];
         quat_rot(qd, Rd);
         T R[9];
-        for (int k = 0; k < 9; ++k) { bRd[9 * i + k] = Rd[k]; R[k] = T(Rd[k]); bR[9 * i + k] = R[k]; }
+        for (int k = 0; k < 9; ++k) { bRd[9 * i + k] = Rd[k]; R[k] = T(Rd[k]); }
         const T m = M.body_mass[b0 + i];
         T inv[3];
         for (int k = 0; k < 3; ++k) {
@@ -934,23 +1192,89 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
             inv[k] = T(1) / Ik;
         }
         // R diag(1/I) R^T, symmetric (xx, yy, zz, xy, xz, yz)
-        T *S = bIinv + 6 * i;
+        T *Sw = bIinv + 6 * i;
         const int rr[6] = {0, 1, 2, 0, 0, 1}, cc[6] = {0, 1, 2, 1, 2, 2};
         for (int k = 0; k < 6; ++k) {
             const int r = rr[k], c = cc[k];
-            S[k] = R[3 * r] * inv[0] * R[3 * c] + R[3 * r + 1] * inv[1] * R[3 * c + 1] + R[3 * r + 2] * inv[2] * R[3 * c + 2];
+            Sw[k] = R[3 * r] * inv[0] * R[3 * c] + R[3 * r + 1] * inv[1] * R[3 * c + 1] + R[3 * r + 2] * inv[2] * R[3 * c + 2];
         }
         bminv[i] = T(1) / m;
     }
     g.sync();
 
-    // ---- 2. joint rows and actuation wrenches (thread per joint); 3. contacts (last warp)
+    // ---- 2. joint rows and actuation wrenches (thread per joint), then the joint-space dynamics:
+    // a drive row per driven joint, the gap of every joint-limit candidate; 3. contacts (last warp,
+    // concurrently with the joints unless limit rows must be placed first)
     for (int j = tid; j < nj; j += nthr) {
         const int4 meta = M.joint_meta[j0 + j];
-        const bool act = meta.w >= 0 && a.tau != nullptr;
+        const double *dyn = M.joint_dyn ? M.joint_dyn + 8 * (size_t)(j0 + j) : nullptr;
+        const bool pd = dyn != nullptr && dyn[0] == 1.0;         // the actuation is this drive's target
+        const bool act = meta.w >= 0 && a.tau != nullptr && !pd;
         const T val = act ? a.tau[(size_t)w * M.n_act_max + meta.w] : T(0);
-        joint_rows(meta.x, meta.y, meta.z, M.joint_frames + 14 * (size_t)(j0 + j), bq, bRd, M.joint_row[j0 + j], kbiasd,
-                   rbody, rJ, rvs, act, val, jwr + 12 * j);
+        const double *fr = M.joint_frames + 14 * (size_t)(j0 + j);
+        joint_rows(meta.x, meta.y, meta.z, fr, bq, bRd, M.joint_row[j0 + j], kbiasd, rbody, rJ, rvs, act, val,
+                   jwr + 12 * j);
+        const int drow = M.joint_drow ? M.joint_drow[j0 + j] : -1;
+        int ls = M.joint_lslot ? M.joint_lslot[j0 + j] : -1;
+        if (drow >= 0 || ls >= 0) {
+            double d, Ja[6], Jb[6];
+            joint_coordinate(meta.x, meta.y, meta.z, fr, bq, bRd, &d, Ja, Jb);
+            if (drow >= 0) {
+                // implicit PD, armature and damping as one regularised row (Sec. 3, Eq. 2's R and v*):
+                // lambda = I_a (d'- - d'+) + dt Kp (target - d - dt d'+) - dt (Kd + b) d'+
+                double ddot = 0.0;
+                for (int k = 0; k < 6; ++k) {
+                    ddot += Jb[k] * (double)bu[6 * meta.z + k];
+                    if (meta.y >= 0) ddot += Ja[k] * (double)bu[6 * meta.y + k];
+                }
+                const double kp = pd ? dyn[1] : 0.0, kd = pd ? dyn[2] : 0.0, arm = dyn[3], damp = dyn[4];
+                const double target = (pd && a.tau != nullptr && meta.w >= 0)
+                                          ? (double)a.tau[(size_t)w * M.n_act_max + meta.w] : d;
+                const double C = arm + dtd * dtd * kp + dtd * (kd + damp);
+                put_row(rbody, rJ, rvs, drow, meta.y, meta.z, Ja, Jb, -(arm * ddot + dtd * kp * (target - d)) / C);
+                rreg[drow] = T(1.0 / C);
+            }
+            if (ls >= 0) {
+                // unilateral rows g = d - lower >= 0 and g = upper - d >= 0 on the joint coordinate
+                for (int side = 0; side < 2; ++side) {
+                    const double bound = dyn[5 + side];
+                    if (!isfinite(bound)) continue;
+                    const double sg = side == 0 ? 1.0 : -1.0;
+                    lgap[ls] = sg * (d - bound);
+                    for (int k = 0; k < 6; ++k) { lJ[12 * ls + k] = T(sg * Ja[k]); lJ[12 * ls + 6 + k] = T(sg * Jb[k]); }
+                    lrank[ls] = j;
+                    ++ls;
+                }
+            }
+        }
+    }
+    int nbil = nfix;                 // rows before the contacts: fixed rows, then the active limits
+    if (nlc > 0) {
+        g.sync();
+        if (warp == 0) {             // active limit candidates (gap below the margin), in candidate order
+            int count = 0;
+            for (int cb = 0; cb < nlc; cb += 32) {
+                const int s = cb + lane;
+                const double gap = s < nlc ? lgap[s] : 0.0;
+                const bool active = s < nlc && gap < (double)a.margin;
+                const unsigned mask = __ballot_sync(0xffffffffu, active);
+                const int rank = count + __popc(mask & ((1u << lane) - 1u));
+                if (active) {
+                    const int4 meta = M.joint_meta[j0 + lrank[s]];
+                    double Ja[6], Jb[6];
+                    for (int k = 0; k < 6; ++k) { Ja[k] = (double)lJ[12 * s + k]; Jb[k] = (double)lJ[12 * s + 6 + k]; }
+                    // the gap may close within the step (g/dt while g > 0); a violation goes at
+                    // Baumgarte's rate (beta g/dt), as a contact's normal row
+                    put_row(rbody, rJ, rvs, nfix + rank, meta.y, meta.z, Ja, Jb, gap > 0.0 ? gap / dtd : kbiasd * gap);
+                    lcid[rank] = s;
+                }
+                if (s < nlc) lrank[s] = active ? rank : -1;
+                count += __popc(mask);
+            }
+            if (lane == 0) misc[5] = count;
+        }
+        g.sync();
+        nbil = nfix + misc[5];
     }
     if (warp == nwarps - 1) {
         int count = 0;
@@ -964,7 +1288,7 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
                 const double *cp = M.contact_point + 3 * (size_t)(c0 + c);
                 double wc[3];
                 matvec3(bRd + 9 * body, cp, wc);
-                for (int k = 0; k < 3; ++k) { rb[k] = (double)bq[7 * body + k]; pw[k] = rb[k] + wc[k]; }
+                for (int k = 0; k < 3; ++k) { rb[k] = bq[7 * body + k]; pw[k] = rb[k] + wc[k]; }
                 phi = terrain(M, pw, n);
                 active = phi < (double)a.margin;
             }
@@ -1009,9 +1333,11 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
         // gyroscopic: -w x (I_w w), I_w w = R (I o (R^T w))
         const T *om = bu + 6 * i + 3;
         T wbody[3], Iw[3], Iww[3], gy[3];
-        matTvec3(bR + 9 * i, om, wbody);
+        T Ri[9];
+        for (int k = 0; k < 9; ++k) Ri[k] = T(bRd[9 * i + k]);
+        matTvec3(Ri, om, wbody);
         for (int k = 0; k < 3; ++k) Iw[k] = bI[3 * i + k] * wbody[k];
-        matvec3(bR + 9 * i, Iw, Iww);
+        matvec3(Ri, Iw, Iww);
         cross3(om, Iww, gy);
         for (int k = 0; k < 3; ++k) tq[k] -= gy[k];
         T dw[3];
@@ -1028,7 +1354,8 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
     for (int r = tid; r < m; r += nthr) {
         const int ba = rbody[2 * r], bbd = rbody[2 * r + 1];
         const T *J = rJ + 12 * r;
-        T d = T(0), v = rvs[r];
+        T d = T(0);
+        double v = rvs[r];       // v_f in FP64 (see the layout): J u_free + v*
         for (int s = 0; s < 2; ++s) {
             const int body = s == 0 ? ba : bbd;
             T *o = MJ + 12 * r + 6 * s;
@@ -1036,10 +1363,10 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
             const T *Js = J + 6 * s;
             for (int k = 0; k < 3; ++k) o[k] = bminv[body] * Js[k];
             symvec3(bIinv + 6 * body, Js + 3, o + 3);
-            for (int k = 0; k < 6; ++k) { d += Js[k] * o[k]; v += Js[k] * bufree[6 * body + k]; }
+            for (int k = 0; k < 6; ++k) { d += Js[k] * o[k]; v = fma((double)Js[k], (double)bufree[6 * body + k], v); }
         }
-        x[r] = d;      // diag(D), temporarily
-        vf[r] = v;
+        x[r] = d + rreg[r];      // diag(D + R) of Eq. 4, temporarily
+        vfd[r] = v;
     }
     g.sync();
     // ---- 5b. Jacobi scaling (tangent rows of a contact share one scale), scaled mu, scaled v_f
@@ -1058,7 +1385,7 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
     }
     g.sync();
     for (int r = tid; r < mp; r += nthr) {
-        vf[r] = r < m ? p[r] * vf[r] : T(0);
+        vfd[r] = r < m ? (double)p[r] * vfd[r] : 0.0;
         bb[r] = T(0);
     }
     for (int k = tid; k < nact; k += nthr) {
@@ -1066,7 +1393,7 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
         mut[k] = M.world_mu[w] * p[rt + 2] / p[rt];
         mui[k] = T(1) / (T(1) + mut[k] * mut[k]);
     }
-    // ---- 5c. A = P D P + (eta + rho) I in packed storage (identity on the padding rows)
+    // ---- 5c. A = P (D + R) P + (eta + rho) I in packed storage (identity on the padding rows)
     const T shift = a.eta + a.rho;
     for (int j = warp; j < mp; j += nwarps) {
         T *col = A + col_start(j, mp) - j;
@@ -1084,7 +1411,7 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
                 if (ia >= 0 && ia == jb) for (int k = 0; k < 6; ++k) s += Ji[k] * Mj[6 + k];
                 if (ib == ja) for (int k = 0; k < 6; ++k) s += Ji[6 + k] * Mj[k];
                 if (ib == jb) for (int k = 0; k < 6; ++k) s += Ji[6 + k] * Mj[6 + k];
-                v = p[i] * p[j] * s + (i == j ? shift : T(0));
+                v = p[i] * p[j] * s + (i == j ? shift + p[i] * p[i] * rreg[i] : T(0));
             }
             col[i] = v;
         }
@@ -1097,11 +1424,12 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
         T l0 = T(0);
         if (warm && r < m) {
             const T *src = a.warm_mode == KAMINO_WARM_EXTERNAL ? a.warm : a.cache;
-            if (src) {
-                if (r < nbil) l0 = src[k0 + r];
+            if (src) {   // cache layout: fixed rows, limit candidates, 3 per contact candidate
+                if (r < nfix) l0 = src[k0 + r];
+                else if (r < nbil) l0 = src[k0 + nfix + lcid[r - nfix]];
                 else {
                     const int k = (r - nbil) / 3, t = (r - nbil) % 3;
-                    l0 = src[k0 + nbil + 3 * cid[k] + t];
+                    l0 = src[k0 + nfix + nlc + 3 * cid[k] + t];
                 }
             }
         }
@@ -1112,12 +1440,12 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
         symv_packed(A, mp, x, xn, X, g);          // xn = A x0 = D~ x0 + (eta + rho) x0
         for (int u = tid; u < nunits; u += nthr) {
             if (u < nbil) {
-                const T v0 = xn[u] - shift * x[u] + vf[u];
+                const T v0 = xn[u] - shift * x[u] + T(vfd[u]);
                 z[u] = v0;
             } else {
                 const int r0 = nbil + 3 * (u - nbil);
                 T v0[3];
-                for (int t = 0; t < 3; ++t) v0[t] = xn[r0 + t] - shift * x[r0 + t] + vf[r0 + t];
+                for (int t = 0; t < 3; ++t) v0[t] = xn[r0 + t] - shift * x[r0 + t] + T(vfd[r0 + t]);
                 z[r0] = v0[0]; z[r0 + 1] = v0[1];
                 z[r0 + 2] = v0[2] + mut[u - nbil] * sqrt(v0[0] * v0[0] + v0[1] * v0[1]);
             }
@@ -1138,7 +1466,20 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
     if constexpr (sizeof(T) == 4 && NB == 16) {
         // the two K-major panels (256 rows x 16) and the pivot block must fit the scratch X
         if (tm && a.mixed && L.A - L.X >= (size_t)(2 * 256 * 16 + 256) * sizeof(float)) {
-            sweep_inverse_tmem(A, mp, X, tbase, misc, g);
+            if (!sweep_inverse_tmem(A, mp, X, tbase, misc, g)) {
+                // the tensor cores did not complete: report the world, leave its state as it was
+                if (tid == 0) {
+                    kamino_residual rep{};
+                    rep.iterations = 0;
+                    rep.status = KAMINO_WORLD_NOT_CONVERGED | KAMINO_WORLD_TIMEOUT;
+                    rep.num_rows = m;
+                    rep.num_contacts = nact;
+                    rep.r_primal = rep.r_dual = rep.r_compl = rep.r_ncp = INFINITY;
+                    a.res[w] = rep;
+                }
+                g.sync();
+                return;
+            }
             in_tmem = true;
         }
     }
@@ -1171,10 +1512,14 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
     // evaluated matrix-free from the rows (P J M^-1 J^T P x + (eta + rho) x) and A^-1 the swept
     // inverse.  At a fixed point A x = -b holds to the accuracy of the matrix-free product, so the
     // inverse's own rounding (which the nearly singular D~ would amplify) does not move the
-    // solution.  With refine64, once r_p and r_d fall below KAMINO_REFINE64_BELOW the right-hand
-    // side b, the per-body velocities M^-1 J^T P x and the residual b + A x are formed in FP64
-    // (from the FP32 iterates, rows and masses), so the fixed point is no longer limited by the
-    // rounding of an FP32 residual of nearly cancelling terms.
+    // solution.  With refine64, once r_p and r_d fall below KAMINO_REFINE64_BELOW the refinement
+    // end game runs in FP64: the right-hand side b (from the FP64 v_f), the per-body velocities
+    // M^-1 J^T P x and the residual b + A x are formed in FP64, and the iterates x, y, z, y^, z^
+    // themselves are kept in FP64 (in shared memory that is dead during the loop), as in iterative
+    // refinement whose solution is accumulated in the higher precision: an FP32 iterate cannot hold
+    // the solution of these mechanisms closer than ~1e-4 in u+ (u+ is a small difference of large
+    // joint impulses through light bodies).  The correction S (b + A x) stays on the FP32 / BF16
+    // inverse.
     //
     // Unit u (a joint row, or the three rows of a contact) belongs to thread u mod group size for
     // the whole solve: only its owner writes its x, b, y, z, y^, z^ (the residual rows read x and b
@@ -1188,7 +1533,13 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
     // the FP64 end game only matters below the FP32 residual floor, i.e. for tolerances under the
     // switch level
     const bool use64 = sizeof(T) == 4 && a.refine64 && a.tol < T(KAMINO_REFINE64_BELOW);
+    double *x64 = nullptr;
+    if (use64) x64 = fp64_iterates(smem, L, tm, a.mixed && !tm, mp, nb, X);
+    double *y64 = x64 + mp, *z64 = x64 + 2 * mp, *yh64 = x64 + 3 * mp, *zh64 = x64 + 4 * mp;
+    double *yn64 = x64 + 5 * mp, *zn64 = x64 + 6 * mp;
     bool hp = false;     // b of the coming iteration is the FP64 one; set once, uniform over the group
+    bool hpv = false;    // the iterates live in the FP64 vectors (from the commit after hp is set)
+    bool x_in64 = false; // the last owner update wrote x to the FP64 vector
     int LB = 8;          // lanes per body in the gather: a power of two with LB * nb <= group size
     while (LB > 1 && LB * nb > nthr) LB >>= 1;
     T acc_a = T(1), c_prev = T(INFINITY);
@@ -1198,13 +1549,13 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
     // b = v_f + Gamma(z^) - eta x - rho y^ - z^ and w = P x for the first iteration
     for (int u = tid; u < nunits; u += nthr) {
         if (u < nbil) {
-            bb[u] = vf[u] - eta * x[u] - rho * yh[u] - zh[u];
+            bb[u] = T(vfd[u]) - eta * x[u] - rho * yh[u] - zh[u];
             wv[u] = p[u] * x[u];
         } else {
             const int r0 = nbil + 3 * (u - nbil);
             const T s = mut[u - nbil] * sqrt(zh[r0] * zh[r0] + zh[r0 + 1] * zh[r0 + 1]);
             for (int t = 0; t < 3; ++t) {
-                bb[r0 + t] = vf[r0 + t] + (t == 2 ? s : T(0)) - eta * x[r0 + t] - rho * yh[r0 + t] - zh[r0 + t];
+                bb[r0 + t] = T(vfd[r0 + t]) + (t == 2 ? s : T(0)) - eta * x[r0 + t] - rho * yh[r0 + t] - zh[r0 + t];
                 wv[r0 + t] = p[r0 + t] * x[r0 + t];
             }
         }
@@ -1228,7 +1579,7 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
                 if (on) {
                     for (int e = bro[body] + sub; e < bro[body + 1]; e += LB) {
                         const int code = brow[e], r = code >> 1;
-                        const double w = (double)p[r] * (double)x[r];
+                        const double w = (double)p[r] * (x_in64 ? x64[r] : (double)x[r]);
                         const T *J = rJ + 6 * code;                 // 12 r + 6 side
 #pragma unroll
                         for (int k = 0; k < 6; ++k) f[k] = fma((double)J[k], w, f[k]);
@@ -1283,7 +1634,8 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
 #pragma unroll
                     for (int k = 0; k < 6; ++k) acc = fma((double)J[6 + k], gbd[6 * sb + k], acc);
                 }
-                c = T(bbd[r] + (double)p[r] * acc + (double)shift * (double)x[r]);
+                const double xr = x_in64 ? x64[r] : (double)x[r];
+                c = T(bbd[r] + (double)p[r] * acc + ((double)shift + (double)p[r] * (double)p[r] * (double)rreg[r]) * xr);
             } else {
                 T acc = T(0);
                 if (sa >= 0) {
@@ -1294,7 +1646,7 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
 #pragma unroll
                     for (int k = 0; k < 6; ++k) acc = fma(J[6 + k], fb[6 * sb + k], acc);
                 }
-                c = bb[r] + p[r] * acc + shift * x[r];
+                c = bb[r] + p[r] * acc + (shift + p[r] * p[r] * rreg[r]) * x[r];
             }
             if (a.mixed && !tm) {
                 const float v = (float)c;
@@ -1318,62 +1670,20 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
         // [8d] owners: x^i, y^i = Pi_K(x^i - z^/rho), z^i = z^ - rho (x^i - y^i), residual terms; x and
         // P x go to shared memory at once (the reduction's barrier publishes them for [8a])
         T lrp = T(0), lrd = T(0), lrc = T(0), lc = T(0);
-        T xnew[S][3], ynew[S][3], znew[S][3];   // units tid + s * group size
-#pragma unroll
-        for (int sl = 0; sl < S; ++sl)
-#pragma unroll
-            for (int t = 0; t < 3; ++t) xnew[sl][t] = ynew[sl][t] = znew[sl][t] = T(0);
-#pragma unroll
-        for (int sl = 0; sl < S; ++sl) {
-            const int u = tid + sl * nthr;
-            if (u >= nunits) continue;
-            if (u < nbil) {
-                const T xv = x[u] + xn[u];
-                const T yv = xv - zh[u] * irho;
-                const T zv = zh[u] - rho * (xv - yv);
-                lrp = fmax(lrp, fabs(xv - yv));
-                lrd = fmax(lrd, fabs(eta * (xv - x[u]) + rho * (yv - yh[u])));
-                lc += (zv - zh[u]) * (zv - zh[u]) * irho + rho * (yv - yh[u]) * (yv - yh[u]);
-                xnew[sl][0] = xv; ynew[sl][0] = yv; znew[sl][0] = zv;
-                x[u] = xv;
-                wv[u] = p[u] * xv;
-            } else {
-                const int k = u - nbil, r0 = nbil + 3 * k;
-                const T mu = mut[k];
-                T v[3], yv[3], xv[3];
-#pragma unroll
-                for (int t = 0; t < 3; ++t) {
-                    xv[t] = x[r0 + t] + xn[r0 + t];
-                    v[t] = xv[t] - zh[r0 + t] * irho;
-                }
-                const T tn = sqrt(v[0] * v[0] + v[1] * v[1]);
-                if (tn <= mu * v[2]) {
-                    yv[0] = v[0]; yv[1] = v[1]; yv[2] = v[2];
-                } else if (mu * tn <= -v[2]) {
-                    yv[0] = yv[1] = yv[2] = T(0);
-                } else {
-                    const T nn = (mu * tn + v[2]) * mui[k];
-                    const T sc = mu * nn / tn;
-                    yv[0] = sc * v[0]; yv[1] = sc * v[1]; yv[2] = nn;
-                }
-                T ydz = T(0);
-#pragma unroll
-                for (int t = 0; t < 3; ++t) {
-                    const T zv = zh[r0 + t] - rho * (xv[t] - yv[t]);
-                    lrp = fmax(lrp, fabs(xv[t] - yv[t]));
-                    lrd = fmax(lrd, fabs(eta * (xv[t] - x[r0 + t]) + rho * (yv[t] - yh[r0 + t])));
-                    lc += (zv - zh[r0 + t]) * (zv - zh[r0 + t]) * irho + rho * (yv[t] - yh[r0 + t]) * (yv[t] - yh[r0 + t]);
-                    ydz += yv[t] * zv;
-                    xnew[sl][t] = xv[t]; ynew[sl][t] = yv[t]; znew[sl][t] = zv;
-                }
-                lrc = fmax(lrc, fabs(ydz));
-#pragma unroll
-                for (int t = 0; t < 3; ++t) {
-                    x[r0 + t] = xv[t];
-                    wv[r0 + t] = p[r0 + t] * xv[t];
-                }
-            }
+        T xnT[S][3], ynT[S][3], znT[S][3];          // units tid + s * group size
+        if (hpv) {
+            // the new FP64 iterates wait for the commit in shared memory (x^i in x, y^i and z^i in
+            // the two spare vectors), not in registers across the reduction
+            double xnD[S][3], ynD[S][3], znD[S][3];
+            owner_update<double, T, S>(g, nunits, nfix, nbil, x64, xn, yh64, zh64, mut, mui, p, wv, eta, rho, irho, xnD, ynD,
+                                       znD, lrp, lrd, lrc, lc);
+            stash_rows<S>(g, nunits, nbil, ynD, yn64);
+            stash_rows<S>(g, nunits, nbil, znD, zn64);
+        } else {
+            owner_update<T, T, S>(g, nunits, nfix, nbil, x, xn, yh, zh, mut, mui, p, wv, eta, rho, irho, xnT, ynT, znT, lrp,
+                                  lrd, lrc, lc);
         }
+        x_in64 = hpv;
         group_reduce4(lrp, lrd, lrc, lc, red, it & 1, g);
         rp = lrp; rd = lrd; rc = lrc;
         converged = rp < a.tol && rd < a.tol && rc < a.tol;
@@ -1394,54 +1704,19 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
                 c_prev = c_prev / T(0.999);
             }
         }
-#pragma unroll
-        for (int sl = 0; sl < S; ++sl) {
-            const int u = tid + sl * nthr;
-            if (u >= nunits) continue;
-            const int r0 = u < nbil ? u : nbil + 3 * (u - nbil);
-            const int cnt = u < nbil ? 1 : 3;
-            // all loads first and every new value kept in registers: the vectors share one
-            // shared-memory buffer, so a value stored and read back would wait for the store
-            T yo[3], zo[3], vr[3], yhv[3], zhv[3];
-#pragma unroll
-            for (int t = 0; t < 3; ++t) {
-                const bool on = t < cnt;
-                yo[t] = on ? y[r0 + t] : T(0);
-                zo[t] = on ? z[r0 + t] : T(0);
-                vr[t] = on ? vf[r0 + t] : T(0);
-            }
-            const T mu = cnt == 3 ? mut[u - nbil] : T(0);
-#pragma unroll
-            for (int t = 0; t < 3; ++t) {
-                const T yv = ynew[sl][t], zv = znew[sl][t];
-                if (!a.nesterov) { yhv[t] = yv; zhv[t] = zv; }
-                else if (restart) { yhv[t] = yo[t]; zhv[t] = zo[t]; }
-                else { yhv[t] = yv + beta_n * (yv - yo[t]); zhv[t] = zv + beta_n * (zv - zo[t]); }
-            }
-#pragma unroll
-            for (int t = 0; t < 3; ++t) {
-                if (t >= cnt) break;
-                const int r = r0 + t;
-                yh[r] = yhv[t]; zh[r] = zhv[t];
-                y[r] = ynew[sl][t]; z[r] = znew[sl][t];
-            }
-            if (hp) {
-                const double z0 = zhv[0], z1 = zhv[1];
-                const double sd = cnt == 3 ? (double)mu * sqrt(z0 * z0 + z1 * z1) : 0.0;
-#pragma unroll
-                for (int t = 0; t < 3; ++t) {
-                    if (t >= cnt) break;
-                    bbd[r0 + t] = (double)vr[t] + (t == 2 ? sd : 0.0) - (double)eta * (double)xnew[sl][t] -
-                                  (double)rho * (double)yhv[t] - (double)zhv[t];
-                }
-            } else {
-                const T sv = cnt == 3 ? mu * sqrt(zhv[0] * zhv[0] + zhv[1] * zhv[1]) : T(0);
-#pragma unroll
-                for (int t = 0; t < 3; ++t) {
-                    if (t >= cnt) break;
-                    bb[r0 + t] = vr[t] + (t == 2 ? sv : T(0)) - eta * xnew[sl][t] - rho * yhv[t] - zhv[t];
-                }
-            }
+        if (hpv) {
+            double xnD[S][3], ynD[S][3], znD[S][3];
+            unstash_rows<S>(g, nunits, nbil, x64, xnD);
+            unstash_rows<S>(g, nunits, nbil, yn64, ynD);
+            unstash_rows<S>(g, nunits, nbil, zn64, znD);
+            owner_commit<double, T, S>(g, nunits, nbil, y64, z64, yh64, zh64, vfd, mut, eta, rho, a.nesterov != 0,
+                                       restart, beta_n, xnD, ynD, znD, true, bb, bbd, nullptr, mp);
+        } else {
+            // the iterates move to the FP64 vectors at this commit once the end game has started
+            double *init = hp && x64 != nullptr ? x64 : nullptr;
+            owner_commit<T, T, S>(g, nunits, nbil, y, z, yh, zh, vfd, mut, eta, rho, a.nesterov != 0, restart,
+                                  beta_n, xnT, ynT, znT, hp, bb, bbd, init, mp);
+            hpv = init != nullptr;
         }
         if (converged) break;
     }
@@ -1451,7 +1726,7 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
     // ---- 9. lambda = P y; u+ = u_free + M^-1 J^T lambda; integrate; cache; report.  Formed in
     // FP64 (once per step): u+ is a small difference of large joint impulses through light bodies,
     // and the pose update adds a small increment to the stored pose.
-    for (int r = tid; r < m; r += nthr) xn[r] = p[r] * y[r];
+    for (int r = tid; r < m; r += nthr) xn[r] = T((double)p[r] * (hpv ? y64[r] : (double)y[r]));
     // J^T lambda per (body, component), one thread each, into FP64 scratch (the per-body FP64
     // velocities of the refinement for FP32 worlds, the per-body force words for FP64 worlds)
     double *fd = sizeof(T) == 8 ? reinterpret_cast<double *>(fb) : gbd;
@@ -1459,71 +1734,109 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
         const int i = t / 6, k = t - 6 * (t / 6);
         double f = 0.0;
         for (int e = bro[i]; e < bro[i + 1]; ++e) {
-            const int code = brow[e];
-            f = fma((double)rJ[6 * code + k], (double)p[code >> 1] * (double)y[code >> 1], f);   // 12 r + 6 side + k
+            const int code = brow[e], r = code >> 1;
+            const double yr = hpv ? y64[r] : (double)y[r];
+            f = fma((double)rJ[6 * code + k], (double)p[r] * yr, f);   // 12 r + 6 side + k
         }
         fd[t] = f;
     }
     g.sync();
+    // u+ per body (over J^T lambda in fd: each thread reads and writes only its body's words)
     bool bad = false;
     for (int i = tid; i < nb; i += nthr) {
         double f[6];
         for (int k = 0; k < 6; ++k) f[k] = fd[6 * i + k];
-        double up[6], dw[3];
+        double dw[3];
         symvec3d(bIinv + 6 * i, f + 3, dw);
         for (int k = 0; k < 3; ++k) {
-            up[k] = (double)bufree[6 * i + k] + (double)bminv[i] * f[k];
-            up[3 + k] = (double)bufree[6 * i + 3 + k] + dw[k];
+            fd[6 * i + k] = (double)bufree[6 * i + k] + (double)bminv[i] * f[k];
+            fd[6 * i + 3 + k] = (double)bufree[6 * i + 3 + k] + dw[k];
         }
-        const T *q = bq + 7 * i;
-        const double th[3] = {dtd * up[3], dtd * up[4], dtd * up[5]};
-        const double ang = sqrt(th[0] * th[0] + th[1] * th[1] + th[2] * th[2]);
-        double dq[4];
-        if (ang > 0.0) {
-            const double s = sin(0.5 * ang) / ang;
-            dq[0] = s * th[0]; dq[1] = s * th[1]; dq[2] = s * th[2]; dq[3] = cos(0.5 * ang);
-        } else {
-            dq[0] = dq[1] = dq[2] = 0.0; dq[3] = 1.0;
-        }
-        const double qx = q[3], qy = q[4], qz = q[5], qw = q[6];
-        const double qn[4] = {dq[3] * qx + dq[0] * qw + dq[1] * qz - dq[2] * qy,
-                              dq[3] * qy - dq[0] * qz + dq[1] * qw + dq[2] * qx,
-                              dq[3] * qz + dq[0] * qy - dq[1] * qx + dq[2] * qw,
-                              dq[3] * qw - dq[0] * qx - dq[1] * qy - dq[2] * qz};
-        const double nrm = 1.0 / sqrt(qn[0] * qn[0] + qn[1] * qn[1] + qn[2] * qn[2] + qn[3] * qn[3]);
-        T *gq = a.body_q + 7 * (size_t)(b0 + i);
-        T *gu = a.body_u + 6 * (size_t)(b0 + i);
-        for (int k = 0; k < 3; ++k) gq[k] = T((double)q[k] + dtd * up[k]);
-        for (int k = 0; k < 4; ++k) gq[3 + k] = T(qn[k] * nrm);
-        for (int k = 0; k < 6; ++k) {
-            gu[k] = T(up[k]);
-            bad |= !isfinite(up[k]);
-        }
-    }
-    // impulse cache: joint rows, then 3 per candidate (zero when inactive)
-    for (int r = tid; r < nbil; r += nthr) a.cache[k0 + r] = xn[r];
-    for (int e = tid; e < 3 * nc; e += nthr) {
-        const int c = e / 3, t = e % 3;
-        const int s = cslot[c];
-        a.cache[k0 + nbil + e] = s >= 0 ? xn[nbil + 3 * s + t] : T(0);
+        for (int k = 0; k < 6; ++k) bad |= !isfinite(fd[6 * i + k]);
     }
     if (bad) atomicOr(misc + 1, 1);
     g.sync();
-    const int any_bad = misc[1];
+    const bool world_bad = (misc[1] & 1) != 0;
+    // natural-map NCP residual of (lambda, u+) on the contact blocks (Eq. 3), scaled units: with
+    // v~ = P (J u+ + v*) and lambda~ = P^-1 lambda, max_k || lambda~_k - Pi_K(lambda~_k - (v~_k + Gamma(v~_k))) ||_inf;
+    // a joint-limit row (0 <= lambda ⟂ g >= 0) adds |lambda~ - max(lambda~ - v~, 0)|
+    T lncp = T(0);
+    for (int r = nfix + tid; r < nbil; r += nthr) {
+        const int sa = rbody[2 * r], sb = rbody[2 * r + 1];
+        double v = rvs[r];
+        for (int q = 0; q < 6; ++q) {
+            if (sa >= 0) v = fma((double)rJ[12 * r + q], fd[6 * sa + q], v);
+            v = fma((double)rJ[12 * r + 6 + q], fd[6 * sb + q], v);
+        }
+        const double vs = (double)p[r] * v, ls = hpv ? y64[r] : (double)y[r];
+        lncp = fmax(lncp, T(fabs(ls - fmax(ls - vs, 0.0))));
+    }
+    for (int k = tid; k < nact; k += nthr) {
+        const int r0 = nbil + 3 * k;
+        double vs[3], ls[3];
+        for (int t = 0; t < 3; ++t) {
+            const int r = r0 + t, sa = rbody[2 * r], sb = rbody[2 * r + 1];
+            double v = rvs[r];
+            for (int q = 0; q < 6; ++q) {
+                if (sa >= 0) v = fma((double)rJ[12 * r + q], fd[6 * sa + q], v);
+                v = fma((double)rJ[12 * r + 6 + q], fd[6 * sb + q], v);
+            }
+            vs[t] = (double)p[r] * v;
+            ls[t] = hpv ? y64[r] : (double)y[r];
+        }
+        const double mu = (double)mut[k];
+        const double s[3] = {ls[0] - vs[0], ls[1] - vs[1], ls[2] - (vs[2] + mu * sqrt(vs[0] * vs[0] + vs[1] * vs[1]))};
+        const double tn = sqrt(s[0] * s[0] + s[1] * s[1]);
+        double pr[3];
+        if (tn <= mu * s[2]) {
+            pr[0] = s[0]; pr[1] = s[1]; pr[2] = s[2];
+        } else if (mu * tn <= -s[2]) {
+            pr[0] = pr[1] = pr[2] = 0.0;
+        } else {
+            const double nn = (mu * tn + s[2]) / (1.0 + mu * mu);
+            pr[0] = mu * nn * s[0] / tn; pr[1] = mu * nn * s[1] / tn; pr[2] = nn;
+        }
+        for (int t = 0; t < 3; ++t) lncp = fmax(lncp, T(fabs(ls[t] - pr[t])));
+    }
+    {
+        T d0 = T(0), d1 = T(0), d2 = T(0);
+        group_reduce4(lncp, d0, d1, d2, red, (it + 1) & 1, g);
+    }
+    // poses and twists (a non-finite world keeps its state and cache; its report says so)
+    for (int i = tid; i < nb && !world_bad; i += nthr) {
+        // semi-implicit Euler: q+ = q (+) dt u+; Moreau-Jean: q+ = q_m (+) (dt/2) u+ (Sec. 3)
+        const double *up = fd + 6 * i;
+        double qp[7];
+        pose_advance(bq + 7 * i, up, up + 3, a.midpoint ? 0.5 * dtd : dtd, qp);
+        T *gq = a.body_q + 7 * (size_t)(b0 + i);
+        T *gu = a.body_u + 6 * (size_t)(b0 + i);
+        for (int k = 0; k < 7; ++k) gq[k] = T(qp[k]);
+        for (int k = 0; k < 6; ++k) gu[k] = T(up[k]);
+    }
+    // impulse cache: fixed rows, then one per joint-limit candidate and 3 per contact candidate
+    // (zero for candidates that were not active)
+    if (!world_bad) {
+        for (int r = tid; r < nfix; r += nthr) a.cache[k0 + r] = xn[r];
+        for (int e = tid; e < nlc; e += nthr) a.cache[k0 + nfix + e] = lrank[e] >= 0 ? xn[nfix + lrank[e]] : T(0);
+        for (int e = tid; e < 3 * nc; e += nthr) {
+            const int c = e / 3, t = e % 3;
+            const int s = cslot[c];
+            a.cache[k0 + nfix + nlc + e] = s >= 0 ? xn[nbil + 3 * s + t] : T(0);
+        }
+    }
     if (tid == 0) {
         kamino_residual rep;
         rep.iterations = it;
-        rep.status = (converged ? 0 : KAMINO_WORLD_NOT_CONVERGED) | (any_bad ? KAMINO_WORLD_NONFINITE : 0);
+        rep.status = (converged ? 0 : KAMINO_WORLD_NOT_CONVERGED) | (world_bad ? KAMINO_WORLD_NONFINITE : 0);
         rep.num_rows = m;
         rep.num_contacts = nact;
         rep.r_primal = (float)rp;
         rep.r_dual = (float)rd;
         rep.r_compl = (float)rc;
-        rep.reserved = 0.0f;
+        rep.r_ncp = (float)lncp;
         a.res[w] = rep;
     }
 }
-
 
 // One world per CTA (256 threads), grid = number of worlds (or of entries in a.world_order); S = 1
 // when every world has at most 256 PADMM units, else 2 (rows <= kMaxRowsPad = 288).
@@ -1533,7 +1846,7 @@ template <typename T, int NB>
 __device__ __forceinline__ uint32_t cta_tmem_alloc(const StepArgs<T> &a, unsigned char *smem) {
     uint32_t tbase = 0;
     if constexpr (sizeof(T) == 4) {
-        const Layout L = make_layout<T>(a.nb_max, a.nj_max, a.nc_max, a.mp_max, NB);
+        const Layout L = make_layout<T>(a.nb_max, a.nj_max, a.nc_max, a.mp_max, NB, a.nl_max);
         int *slot = (int *)(smem + L.misc) + 2;
         if (threadIdx.x < 32) {
             asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"

@@ -19,7 +19,7 @@ from . import build as _build
 FP32, FP64, MIXED = 0, 1, 2
 WARM_COLD, WARM_CACHED, WARM_EXTERNAL = 0, 1, 2
 BUF_BODY_Q, BUF_BODY_U, BUF_CACHE, BUF_WARM, BUF_RESIDUAL, BUF_TAU = 0, 1, 2, 3, 4, 5
-WORLD_NOT_CONVERGED, WORLD_NONFINITE = 1, 2
+WORLD_NOT_CONVERGED, WORLD_NONFINITE, WORLD_TIMEOUT = 1, 2, 4
 STATUS = {0: "KAMINO_OK", 1: "KAMINO_E_INVALID_ARG", 2: "KAMINO_E_TOPOLOGY", 3: "KAMINO_E_NOMEM",
           4: "KAMINO_E_CUDA", 5: "KAMINO_E_NONFINITE", 6: "KAMINO_E_TIMEOUT", 7: "KAMINO_E_UNSUPPORTED"}
 
@@ -32,12 +32,17 @@ class KaminoError(RuntimeError):
 
 class SolverParams(C.Structure):
     _fields_ = [("eta", C.c_double), ("rho", C.c_double), ("beta", C.c_double), ("margin", C.c_double),
-                ("nesterov", C.c_int32), ("precond", C.c_int32), ("warm_mode", C.c_int32), ("refine64", C.c_int32)]
+                ("nesterov", C.c_int32), ("precond", C.c_int32), ("warm_mode", C.c_int32), ("refine64", C.c_int32),
+                ("integrator", C.c_int32), ("cr_iters", C.c_int32)]
+
+
+INTEGRATOR_EULER, INTEGRATOR_MIDPOINT = 0, 1
 
 
 def make_params(eta=1e-6, rho=0.1, beta=0.2, margin=0.005, nesterov=True, precond=True, warm_mode=WARM_COLD,
-                refine64=True):
-    return SolverParams(eta, rho, beta, margin, int(nesterov), int(precond), int(warm_mode), int(refine64))
+                refine64=True, integrator=INTEGRATOR_EULER, cr_iters=0):
+    return SolverParams(eta, rho, beta, margin, int(nesterov), int(precond), int(warm_mode), int(refine64),
+                        int(integrator), int(cr_iters))
 
 
 _P = C.c_void_p
@@ -51,7 +56,10 @@ class ModelDesc(C.Structure):
                 ("joint_frame_parent", _P), ("joint_frame_child", _P), ("contact_body", _P),
                 ("contact_point", _P), ("gravity", C.c_double * 3), ("terrain_kind", C.c_int32),
                 ("hf_nx", C.c_int32), ("hf_ny", C.c_int32), ("hf_origin", C.c_double * 2), ("hf_cell", C.c_double),
-                ("hf_heights", _P), ("body_q0", _P), ("body_u0", _P), ("params", SolverParams)]
+                ("hf_heights", _P), ("body_q0", _P), ("body_u0", _P), ("params", SolverParams),
+                ("joint_drive", _P), ("joint_limit", _P)]
+
+DRIVE_TORQUE, DRIVE_PD = 0, 1
 
 
 class ModelInfo(C.Structure):
@@ -77,7 +85,7 @@ class MlpInfo(C.Structure):
 
 RESIDUAL_DTYPE = np.dtype([("iterations", np.int32), ("status", np.int32), ("num_rows", np.int32),
                            ("num_contacts", np.int32), ("r_primal", np.float32), ("r_dual", np.float32),
-                           ("r_compl", np.float32), ("reserved", np.float32)])
+                           ("r_compl", np.float32), ("r_ncp", np.float32)])
 
 _lib = None
 
@@ -182,9 +190,6 @@ class Model:
     """A set of worlds on the device (kamino_model_create)."""
 
     def __init__(self, ws, precision: str = "fp32", params: SolverParams | None = None):
-        if getattr(ws, "joint_drive", None) is not None or getattr(ws, "joint_limit", None) is not None:
-            raise ValueError("joint drives (implicit PD, armature, damping) and joint limits are not "
-                             "implemented by the CUDA step")
         lib = load_library()
         self.precision = {"fp32": FP32, "fp64": FP64, "mixed": MIXED, FP32: FP32, FP64: FP64, MIXED: MIXED}[precision]
         self.ws = ws
@@ -208,6 +213,15 @@ class Model:
             "q0": np.ascontiguousarray(ws.body_q0, np.float64).reshape(-1),
             "u0": np.ascontiguousarray(ws.body_u0, np.float64).reshape(-1),
         }
+        drive, limit = getattr(ws, "joint_drive", None), getattr(ws, "joint_limit", None)
+        if drive is not None:
+            keep["drv"] = np.ascontiguousarray(drive, np.float64).reshape(-1)
+            if keep["drv"].size != 5 * len(ws.joint_type):
+                raise ValueError("joint_drive must hold 5 values per joint")
+        if limit is not None:
+            keep["lim"] = np.ascontiguousarray(limit, np.float64).reshape(-1)
+            if keep["lim"].size != 2 * len(ws.joint_type):
+                raise ValueError("joint_limit must hold 2 values per joint")
         d = ModelDesc()
         d.num_worlds = ws.num_worlds
         d.precision = self.precision
@@ -224,6 +238,8 @@ class Model:
         d.hf_cell = float(ws.hf_cell)
         d.hf_heights = _ptr(keep["hh"])
         d.body_q0, d.body_u0 = _ptr(keep["q0"]), _ptr(keep["u0"])
+        d.joint_drive = _ptr(keep["drv"]) if "drv" in keep else None
+        d.joint_limit = _ptr(keep["lim"]) if "lim" in keep else None
         d.params = params if params is not None else make_params()
         self.handle = C.c_void_p()
         _check(lib.kamino_model_create(C.byref(d), C.byref(self.handle)))

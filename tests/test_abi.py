@@ -28,7 +28,7 @@ def test_library_exports_every_declared_function(lib):
 def test_struct_layout_matches_header():
     """The ctypes mirror has the size the C compiler gives (checked through a layout probe on the
     field offsets that the header implies: 8-byte aligned pointers after two int32s)."""
-    assert C.sizeof(K.SolverParams) == 48
+    assert C.sizeof(K.SolverParams) == 56
     assert K.ModelDesc.world_body_offset.offset == 8
     assert K.ModelDesc.gravity.offset == 8 + 15 * 8
     assert C.sizeof(K.ModelInfo) == 40
@@ -124,13 +124,28 @@ def test_missing_library_fails_loudly(tmp_path):
         kamino._lib = saved
 
 
-def test_model_rejects_joint_drives_and_limits():
-    """The CUDA step has no drive or limit rows: worlds that carry them are refused up front rather
-    than stepped without them."""
-    ws = wg.make_pendulum(actuated=True)
-    for w in (wg.with_joint_drives(ws, wg.DRIVE_PD, 10.0, 1.0), wg.with_joint_limits(ws, -1.0, 1.0)):
-        with pytest.raises(ValueError, match="not implemented by the CUDA step"):
-            K.Model(w, "fp32")
+@pytest.mark.parametrize("mutate,status", [
+    (lambda ws: wg.with_joint_drives(ws, 2, 10.0, 1.0), 2),                   # not a KAMINO_DRIVE_* mode
+    (lambda ws: wg.with_joint_drives(ws, wg.DRIVE_PD, -1.0, 1.0), 2),         # negative gain
+    (lambda ws: wg.with_joint_drives(ws, wg.DRIVE_PD, np.inf, 1.0), 2),       # infinite gain
+    (lambda ws: wg.with_joint_limits(ws, 1.0, -1.0), 2),                      # lower above upper
+    (lambda ws: wg.with_joint_limits(ws, np.nan, 1.0), 2),                    # NaN bound
+])
+def test_model_rejects_bad_joint_dynamics(mutate, status):
+    """Drive and limit descriptions are validated on the host before any GPU work."""
+    got, msg = _create(mutate(wg.make_pendulum(actuated=True)))
+    assert got == status, msg
+
+
+def test_drives_and_limits_only_on_joint_coordinates():
+    """Drives and limits act on the coordinate of a revolute or prismatic joint; a spherical joint
+    with either is a topology error."""
+    ws = wg.make_stewart(num_worlds=1, seed=0)
+    sph = int(np.flatnonzero(ws.joint_type == wg.JOINT_SPHERICAL)[0])
+    got, msg = _create(wg.with_joint_drives(ws, wg.DRIVE_TORQUE, armature=0.1, joints=[sph]))
+    assert got == 2 and "drives" in msg, msg
+    got, msg = _create(wg.with_joint_limits(ws, -0.5, 0.5, joints=[sph]))
+    assert got == 2 and "limits" in msg, msg
 
 
 def test_binding_checks_what_the_library_cannot():

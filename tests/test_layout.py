@@ -16,8 +16,8 @@ PROGRAM = r"""
 #include "kamino_internal.h"
 using namespace kamino;
 static size_t field_ok(const Layout &L) {
-    const size_t f[] = {L.bq, L.bu, L.bR, L.bRd, L.bI, L.bIinv, L.bminv, L.bufree, L.jwr, L.cid, L.cslot, L.rbody,
-                        L.rJ, L.rvs, L.vf, L.p, L.x, L.xn, L.y, L.z, L.yh, L.zh, L.b, L.mut, L.mui, L.wv, L.fb,
+    const size_t f[] = {L.bq, L.bu, L.bRd, L.bI, L.bIinv, L.bminv, L.bufree, L.jwr, L.cid, L.cslot, L.rbody,
+                        L.rJ, L.rvs, L.rreg, L.lgap, L.lJ, L.lrank, L.lcid, L.vfd, L.p, L.x, L.xn, L.y, L.z, L.yh, L.zh, L.b, L.mut, L.mui, L.wv, L.fb,
                         L.bro, L.brow, L.X, L.A, L.red, L.misc};
     for (size_t o : f) if (o % 16) return 0;
     return 1;
