@@ -355,9 +355,12 @@ kamino_status kamino_mlp_set_normalization(kamino_mlp_t mlp, const float *host);
  * let memory be allocated for them (another framework owns the allocator, or a real-time loop
  * cannot afford the synchronisation of cudaMalloc).  Every GPU that loads the library holds the
  * array until exit.  The first call on a device looks up the array's device address (make it
- * before any stream capture).  All calls share the array: calls that overlap on the GPU race, so
- * serialise them.  A batch whose activations exceed the array returns KAMINO_E_UNSUPPORTED; this
- * call allocates nothing. */
+ * before any stream capture); the address is kept for the life of the process, so do not call this
+ * on a device after a cudaDeviceReset of it.  The calling thread's current device must be the one
+ * the network was created on (KAMINO_E_INVALID_ARG otherwise).  All calls share the array: calls
+ * that overlap on the GPU race, so serialise them.  A batch whose activations exceed the array
+ * returns KAMINO_E_UNSUPPORTED, whose message names the largest batch that fits; this call
+ * allocates nothing. */
 #define KAMINO_MLP_STATIC_SCRATCH_BYTES (16u * 1024u * 1024u)
 kamino_status kamino_mlp_predict_static(kamino_mlp_t mlp, const float *x_dev, int32_t batch, float *y_dev,
                                         void *stream);

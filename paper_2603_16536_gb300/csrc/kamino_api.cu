@@ -60,7 +60,6 @@ kamino_status check_params(const kamino_solver_params &p) {
         return fail(KAMINO_E_INVALID_ARG, "params.integrator %d is not a KAMINO_INTEGRATOR_* value", p.integrator);
     if (p.cr_iters < 0 || p.cr_iters > KAMINO_MAX_CR_ITERS)
         return fail(KAMINO_E_INVALID_ARG, "params.cr_iters must be in [0, %d] (got %d)", KAMINO_MAX_CR_ITERS, p.cr_iters);
-    if (p.cr_iters > 0) return fail(KAMINO_E_UNSUPPORTED, "the sparse formulation (params.cr_iters > 0) is not built yet");
     return KAMINO_OK;
 }
 
@@ -234,8 +233,9 @@ size_t persistent_smem(const kamino_model_s *m, const Bucket &b, int group, int 
     if (b.units > kSlots * group) return 0;
     const int mp = std::max(((b.rows + 15) / 16) * 16, 16);
     if (mp > kMaxRowsPad) return 0;
-    const Layout L = esize(m) == sizeof(double) ? make_layout<double>(b.nb, b.nj, b.nc, mp, nbp, m->nl_max)
-                                                : make_layout<float>(b.nb, b.nj, b.nc, mp, nbp, m->nl_max);
+    const bool dense = m->params.cr_iters == 0;
+    const Layout L = esize(m) == sizeof(double) ? make_layout<double>(b.nb, b.nj, b.nc, mp, nbp, m->nl_max, dense)
+                                                : make_layout<float>(b.nb, b.nj, b.nc, mp, nbp, m->nl_max, dense);
     const size_t sl = align_up(L.total, 16);
     const int per = kThreads / group;
     const size_t total = per * sl + align_up(per * sizeof(int), 16);
@@ -292,7 +292,7 @@ kamino_status ensure_plan_ready(kamino_model_s *m) {
 template <typename T>
 kamino_status grid_of(kamino_model_s *m, Bucket &b) {
     int per_sm = 0;
-    cudaError_t e = occupancy_persistent<T>(b.panel, b.smem, &per_sm);
+    cudaError_t e = occupancy_persistent<T>(b.panel, b.smem, m->params.cr_iters > 0 ? 1 : 0, &per_sm);
     if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
     const int need = (b.count + b.per_cta - 1) / b.per_cta;
     b.grid = std::max(1, std::min(need, std::max(per_sm, 1) * m->sm_count));
@@ -323,9 +323,10 @@ StepArgs<T> make_args(kamino_state_s *st, double dt, int iters, double tol, cons
     a.mixed = m->precision == KAMINO_MIXED ? 1 : 0;
     a.midpoint = m->params.integrator == KAMINO_INTEGRATOR_MIDPOINT ? 1 : 0;
     a.refine64 = m->params.refine64 ? 1 : 0;
+    a.cr_iters = m->params.cr_iters;
     // the inverse may live in tensor memory when a world's shared memory keeps a second CTA off the SM
-    // (the 512-column allocation then never waits for another CTA)
-    a.tmem = (sizeof(T) == 4 && m->mp_max <= 256 && m->smem > kMaxSmem / 2) ? 1 : 0;
+    // (the 512-column allocation then never waits for another CTA); the sparse formulation has none
+    a.tmem = (sizeof(T) == 4 && a.cr_iters == 0 && m->mp_max <= 256 && m->smem > kMaxSmem / 2) ? 1 : 0;
     a.warm_mode = m->params.warm_mode;
     a.nb_max = m->nb_max;
     a.nj_max = m->nj_max;
@@ -351,7 +352,8 @@ kamino_status launch_bucket(kamino_state_s *st, const StepArgs<T> &base, int bi,
     a.mp_max = std::max(((b.rows + 15) / 16) * 16, 16);
     // tensor memory when one 256-thread group fills the CTA and its shared memory keeps a second
     // CTA off the SM
-    a.tmem = (sizeof(T) == 4 && b.group == kThreads && a.mp_max <= 256 && b.smem > kMaxSmem / 2) ? 1 : 0;
+    a.tmem = (sizeof(T) == 4 && a.cr_iters == 0 && b.group == kThreads && a.mp_max <= 256 && b.smem > kMaxSmem / 2)
+                 ? 1 : 0;
     PersistentArgs p{};
     p.worlds = b.d_worlds;
     p.count = b.count;
@@ -475,6 +477,37 @@ kamino_status autotune(kamino_state_s *st, double dt, int iters, double tol, con
 extern "C" {
 
 const char *kamino_last_error(void) { return g_error.c_str(); }
+
+// Shared-memory working set of the single-launch plan and the persistent configuration of every
+// bucket, for the formulation the parameters select (dense, or sparse with params.cr_iters > 0).
+static kamino_status configure(kamino_model_s *m) {
+    const bool dense = m->params.cr_iters == 0;
+    m->smem = 0;
+    m->prepared = false;
+    for (int nbp : {16, 8}) {
+        const int mp = std::max(((m->max_rows + 15) / 16) * 16, 16);
+        if (mp > kMaxRowsPad) continue;
+        const Layout L = m->precision == KAMINO_FP64
+                             ? make_layout<double>(m->nb_max, m->nj_max, m->nc_max, mp, nbp, m->nl_max, dense)
+                             : make_layout<float>(m->nb_max, m->nj_max, m->nc_max, mp, nbp, m->nl_max, dense);
+        if (L.total <= kMaxSmem) {
+            m->nb_panel = nbp;
+            m->mp_max = mp;
+            m->smem = L.total;
+            break;
+        }
+    }
+    if (m->smem == 0)
+        return fail(KAMINO_E_UNSUPPORTED,
+                    "a world needs %d constraint rows; the shared-memory working set exceeds %zu bytes "
+                    "(max %d padded rows)", m->max_rows, kMaxSmem, kMaxRowsPad);
+    for (auto &b : m->buckets) {
+        b.grid = 0;
+        if (!choose_default(m, b))
+            return fail(KAMINO_E_UNSUPPORTED, "no persistent configuration fits the bucket of %d rows", b.rows_pad);
+    }
+    return KAMINO_OK;
+}
 
 kamino_status kamino_model_create(const kamino_model_desc *d, kamino_model_t *out) {
     if (!d || !out) return fail(KAMINO_E_INVALID_ARG, "desc and out must not be NULL");
@@ -694,35 +727,11 @@ kamino_status kamino_model_create(const kamino_model_desc *d, kamino_model_t *ou
         m->n_act_max = std::max(m->n_act_max, nact);
     }
     m->cache_len = cache;
-    const size_t esz = d->precision == KAMINO_FP64 ? sizeof(double) : sizeof(float);
-    m->smem = 0;
-    for (int nbp : {16, 8}) {
-        const int mp = std::max(((m->max_rows + 15) / 16) * 16, 16);
-        if (mp > kMaxRowsPad) continue;
-        const Layout L = esz == sizeof(double) ? make_layout<double>(m->nb_max, m->nj_max, m->nc_max, mp, nbp, m->nl_max)
-                                               : make_layout<float>(m->nb_max, m->nj_max, m->nc_max, mp, nbp, m->nl_max);
-        if (L.total <= kMaxSmem) {
-            m->nb_panel = nbp;
-            m->mp_max = mp;
-            m->smem = L.total;
-            break;
-        }
-    }
-    if (m->smem == 0) {
-        const int rows = m->max_rows;
-        delete m;
-        return fail(KAMINO_E_UNSUPPORTED,
-                    "a world needs %d constraint rows; the shared-memory working set exceeds %zu bytes "
-                    "(max %d padded rows)", rows, kMaxSmem, kMaxRowsPad);
-    }
     std::sort(m->buckets.begin(), m->buckets.end(),
               [](const Bucket &a, const Bucket &b) { return a.rows_pad > b.rows_pad; });
-    for (auto &b : m->buckets) {
-        if (!choose_default(m, b)) {
-            const int rp = b.rows_pad;
-            delete m;
-            return fail(KAMINO_E_UNSUPPORTED, "no persistent configuration fits the bucket of %d rows", rp);
-        }
+    if (kamino_status st = configure(m)) {
+        delete m;
+        return st;
     }
     std::vector<double> q0(7 * (size_t)B, 0.0);
     for (int b = 0; b < B; ++b) {
@@ -768,7 +777,16 @@ kamino_status kamino_model_set_params(kamino_model_t m, const kamino_solver_para
     if (!m || !p) return fail(KAMINO_E_INVALID_ARG, "model and params must not be NULL");
     kamino_status s = check_params(*p);
     if (s) return s;
+    const bool was_dense = m->params.cr_iters == 0;
+    const kamino_solver_params keep = m->params;
     m->params = *p;
+    if ((p->cr_iters == 0) != was_dense) {        // the other formulation: another working set
+        if ((s = configure(m))) {
+            m->params = keep;
+            configure(m);
+            return s;
+        }
+    }
     return KAMINO_OK;
 }
 
@@ -1015,6 +1033,7 @@ double normal_draw(uint64_t &s) {   // Box-Muller on two uniform draws in (0, 1)
 
 struct kamino_mlp_s {
     kamino_model_t model = nullptr;
+    int device = 0;                        // the device that holds the network's arrays
     int count = 0, din = 0, dout = 0, hidden = 0, nact = 0, max_batch = 0, step = 0;
     int dims[kHiddenLayers + 2] = {0, 0, 0, 0, 0};
     long woff[kHiddenLayers + 1] = {0}, boff[kHiddenLayers + 1] = {0};
@@ -1147,8 +1166,11 @@ kamino_status kamino_mlp_create(kamino_model_t m, const int32_t *worlds, int32_t
             m->world_cache[worlds[i]] != m->world_cache[worlds[0]])
             return fail(KAMINO_E_TOPOLOGY, "world %d does not match the sizes of world %d", worlds[i], worlds[0]);
     }
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return cuda_fail(e, "mlp create (device)");
     auto *n = new kamino_mlp_s();
     n->model = m;
+    n->device = dev;
     n->count = count;
     n->hidden = hidden;
     n->nact = m->n_act_max;
@@ -1376,6 +1398,7 @@ bool kamino::mlp::net_view(const struct kamino_mlp_s *n, NetView *out) {
     out->hidden = n->hidden;
     out->layers = kHiddenLayers;
     out->max_batch = n->max_batch;
+    out->device = n->device;
     out->P = n->P;
     out->PB = n->PB;
     for (int l = 0; l <= kHiddenLayers; ++l) {

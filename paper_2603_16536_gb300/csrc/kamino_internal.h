@@ -60,6 +60,7 @@ struct StepArgs {
     int mixed;                 // 1: BF16 tiles of the inverse on tensor cores (KAMINO_MIXED)
     int midpoint;              // 1: Moreau-Jean midpoint scheme (KAMINO_INTEGRATOR_MIDPOINT)
     int refine64;              // 1: FP64 right-hand side and refinement residual near convergence
+    int cr_iters;              // 0: dense formulation; k >= 1: sparse formulation, k CR iterations per x-step
     int tmem;                  // 1: keep the swept inverse in tensor memory (FP32, whole-CTA groups, mp <= 256)
     // shared-memory layout bounds (maxima over the launched worlds)
     int nb_max, nj_max, nc_max, mp_max, nl_max;
@@ -88,9 +89,14 @@ __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a -
 // non-decreasing in mp, so a layout sized for the largest world fits every smaller one.
 __host__ __device__ inline int panel_ld(int mp) { return mp + (mp % 32 == 0 ? 8 : 24); }
 
-// nl: joint-limit candidates per world (0 when no world has limits).
+// nl: joint-limit candidates per world (0 when no world has limits).  dense: the dense formulation's
+// working set (packed matrix, sweep panels, PADMM vectors in shared memory); otherwise the sparse
+// formulation's, whose PADMM and Conjugate Residual vectors live in the owners' registers and whose
+// scratch X holds, after assembly, the final y (FP64), the published vector w = P v and the per-body
+// gather g (both sized for FP64).
 template <typename T>
-__host__ __device__ inline Layout make_layout(int nb, int nj, int nc, int mp, int nb_panel, int nl = 0) {
+__host__ __device__ inline Layout make_layout(int nb, int nj, int nc, int mp, int nb_panel, int nl = 0,
+                                              bool dense = true) {
     Layout L{};
     size_t o = 0;
     auto take = [&](size_t &field, size_t bytes) { field = o; o = align_up(o + bytes, 16); };
@@ -120,17 +126,29 @@ __host__ __device__ inline Layout make_layout(int nb, int nj, int nc, int mp, in
     take(L.p, mp * s);
     take(L.x, mp * s);
     take(L.xn, mp * s);
-    take(L.y, mp * s);
-    take(L.z, mp * s);
-    take(L.yh, mp * s);
-    take(L.zh, mp * s);
-    take(L.b, mp * s);
+    const int dv = dense ? mp : 0;         // vectors only the dense formulation keeps in shared memory
+    take(L.y, dv * s);
+    take(L.z, dv * s);
+    take(L.yh, dv * s);
+    take(L.zh, dv * s);
+    take(L.b, dv * s);
     take(L.mut, (nc > 0 ? nc : 1) * s);
     take(L.mui, (nc > 0 ? nc : 1) * s);
-    take(L.wv, mp * s);
-    take(L.fb, nb * 6 * s);
+    take(L.wv, dv * s);
+    take(L.fb, (dense ? nb * 6 : 0) * s);
     take(L.bro, (nb + 1) * sizeof(int));
     take(L.brow, 2 * mp * sizeof(int));
+    if (!dense) {
+        size_t xb = (size_t)mp * 12 * s;                                     // M^-1 J^T blocks (assembly)
+        const size_t cr = (2 * (size_t)mp + 6 * (size_t)nb) * sizeof(double);  // y64, w, g
+        if (cr > xb) xb = cr;
+        take(L.X, xb);
+        take(L.A, 0);
+        take(L.red, 2 * 4 * kWarps * sizeof(double));
+        take(L.misc, 16 * sizeof(int));
+        L.total = o;
+        return L;
+    }
     size_t xs = (size_t)mp * 12;
     size_t sweep = (size_t)2 * panel_ld(mp) * nb_panel + (size_t)nb_panel * nb_panel;
     if (sweep > xs) xs = sweep;
@@ -159,6 +177,6 @@ cudaError_t launch_persistent(const StepArgs<T> &args, const PersistentArgs &p, 
 template <typename T>
 cudaError_t prepare_persistent(int nb_panel, size_t smem);
 template <typename T>
-cudaError_t occupancy_persistent(int nb_panel, size_t smem, int *blocks_per_sm);
+cudaError_t occupancy_persistent(int nb_panel, size_t smem, int cr, int *blocks_per_sm);
 
 }  // namespace kamino

@@ -62,6 +62,7 @@ cudaError_t warm_write(const int4 *world_a, const int *worlds, int count, int do
 // Read-only view of a network's parameters and normalisation (defined with the network's host code).
 struct NetView {
     int din, dout, hidden, layers, max_batch;
+    int device;                     // the device that holds the network's arrays
     const float *P;                 // FP32 master parameters
     const __nv_bfloat16 *PB;        // BF16 copy of the weight matrices (same offsets)
     long woff[8], boff[8];          // per layer offsets of W_l and b_l

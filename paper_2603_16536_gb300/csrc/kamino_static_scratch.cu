@@ -10,10 +10,14 @@
 //
 // The array's name is only a host-side stand-in in host code: its device address is fetched once
 // per device with cudaGetSymbolAddress (the first call on a device does this, so make that first
-// call before any stream capture) and passed to the kernels.  All calls share the array, so calls
-// that overlap on the GPU (different streams, or different devices' threads racing on the same
-// device) race on it; serialise them.  Nothing in it needs clearing between calls: every word a
-// call reads was written earlier by the same call.
+// call before any stream capture) and passed to the kernels.  The address is cached per device
+// ordinal for the life of the process: a cudaDeviceReset destroys the context that holds the array,
+// so a process that resets a device must not call this entry point on that device afterwards.  The
+// call runs on the calling thread's current device, which must be the one that holds the network
+// (the device current at kamino_mlp_create).  All calls share the array, so calls that overlap on
+// the GPU (different streams, or several host threads on the same device) race on it; serialise
+// them.  Nothing in it needs clearing between calls: every word a call reads was written earlier
+// by the same call.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -36,6 +40,20 @@ void *g_scratch_addr[kMaxDevices] = {nullptr};
 
 size_t round256(size_t x) { return (x + 255) / 256 * 256; }
 
+// Bytes of the activations of `batch` rows: normalised input (BF16), two ping-pong hidden
+// activations (BF16), output (FP32), each 256-byte aligned.
+size_t scratch_bytes(size_t batch, size_t din, size_t hidden, size_t dout) {
+    return round256(batch * din * 2) + 2 * round256(batch * hidden * 2) + round256(batch * dout * 4);
+}
+
+// The largest batch whose activations fit the array (0 if not even one row does).
+size_t max_rows(size_t din, size_t hidden, size_t dout) {
+    const size_t per = 2 * din + 4 * hidden + 4 * dout;
+    size_t b = kMaxBytes > 4 * 256 ? (kMaxBytes - 4 * 256) / per : 0;   // rounding adds < 4 x 256 bytes
+    while (scratch_bytes(b + 1, din, hidden, dout) <= kMaxBytes) ++b;
+    return b;
+}
+
 }  // namespace
 
 extern "C" kamino_status kamino_mlp_predict_static(kamino_mlp_t net, const float *x_dev, int32_t batch,
@@ -48,18 +66,22 @@ extern "C" kamino_status kamino_mlp_predict_static(kamino_mlp_t net, const float
     // layout: normalised input (BF16), two ping-pong hidden activations (BF16), output (FP32)
     const size_t bx = round256((size_t)batch * v.din * sizeof(__nv_bfloat16));
     const size_t bh = round256((size_t)batch * v.hidden * sizeof(__nv_bfloat16));
-    const size_t by = round256((size_t)batch * v.dout * sizeof(float));
-    const size_t need = bx + 2 * bh + by;
+    const size_t need = scratch_bytes((size_t)batch, v.din, v.hidden, v.dout);
     if (need > kMaxBytes) {
         char msg[256];
         snprintf(msg, sizeof(msg),
                  "batch %d needs %zu bytes of static scratch, the library holds %zu (at most %zu rows for this "
-                 "network)", batch, need, kMaxBytes, (size_t)(kMaxBytes / (need / (size_t)batch + 1)));
+                 "network)", batch, need, kMaxBytes, max_rows(v.din, v.hidden, v.dout));
         return kamino::report_error(KAMINO_E_UNSUPPORTED, msg);
     }
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return kamino::report_error(KAMINO_E_CUDA, cudaGetErrorString(e));
+    if (dev != v.device) {
+        char msg[160];
+        snprintf(msg, sizeof(msg), "the current device is %d but the network lives on device %d", dev, v.device);
+        return kamino::report_error(KAMINO_E_INVALID_ARG, msg);
+    }
     if (dev < 0 || dev >= kMaxDevices) return kamino::report_error(KAMINO_E_UNSUPPORTED, "device ordinal too large");
     unsigned char *base = nullptr;
     {

@@ -1125,11 +1125,332 @@ __device__ __forceinline__ void owner_commit(const Group &g, int nunits, int nbi
     }
 }
 
+// Per-body row lists for the matrix-free products: bro[i] .. bro[i+1] index brow, whose entries are
+// 2 r + side for every row r that has body i on that side (side 0: A, side 1: B).
+__device__ void body_row_lists(const Group &g, int nb, int m, const int *rbody, int *bro, int *brow) {
+    const int tid = g.tid, nthr = g.size;
+    for (int i = tid; i < nb; i += nthr) {
+        int cnt = 0;
+        for (int r = 0; r < m; ++r) cnt += (rbody[2 * r] == i) + (rbody[2 * r + 1] == i);
+        bro[i + 1] = cnt;
+    }
+    g.sync();
+    if (tid == 0) {
+        bro[0] = 0;
+        for (int i = 0; i < nb; ++i) bro[i + 1] += bro[i];
+    }
+    g.sync();
+    for (int i = tid; i < nb; i += nthr) {
+        int e = bro[i];
+        for (int r = 0; r < m; ++r) {
+            if (rbody[2 * r] == i) brow[e++] = 2 * r;
+            if (rbody[2 * r + 1] == i) brow[e++] = 2 * r + 1;
+        }
+    }
+}
+
+// ----------------------------------------------------------------------------- sparse formulation
+// Sec. 5.1: the Delassus matrix is never formed.  A v = P (J M^-1 J^T + R) P v + (eta + rho) v is
+// applied from the rows: the owners of the units publish w = P v, LB lanes per body gather
+// g_b = M_b^-1 sum_r J_rb^T w_r, and every owner forms (A v)_r = p_r J_r (g_A, g_B) +
+// (eta + rho + p_r^2 R_r) v_r for its own rows (the scaling by P is folded into the publication and
+// the row product, which is what pre-scaled P J and M^-1 J^T P rows save).  Each x-step of Alg. 1
+// runs k Conjugate Residual iterations on A x = -b from the previous x; every PADMM and CR vector of a
+// unit stays in its owner's registers and only w and g go through shared memory, so one application
+// of A costs two barriers and one CR iteration three (the dot products of one reduction).
+
+// Group-wide sums of three values (fixed order, so the result does not depend on scheduling),
+// double-buffered by `phase` like group_reduce4.
+template <typename V>
+__device__ __forceinline__ void group_sum3(V &a, V &b, V &c, V *red, int phase, const Group &g) {
+    const int lane = g.lane(), warp = g.warp(), nw = g.warps();
+    a = warp_sum(a); b = warp_sum(b); c = warp_sum(c);
+    V *r = red + phase * 4 * kWarps;
+    if (lane == 0) { r[warp] = a; r[kWarps + warp] = b; r[2 * kWarps + warp] = c; }
+    g.sync();
+    a = r[0]; b = r[kWarps]; c = r[2 * kWarps];
+    for (int k = 1; k < nw; ++k) { a += r[k]; b += r[kWarps + k]; c += r[2 * kWarps + k]; }
+}
+
+// What the sparse x-step needs of the world (shared memory, built by phases 1-5).
+template <typename T>
+struct CrWorld {
+    int nunits, nfix, nbil, nb, LB;
+    const int *bro, *brow, *rbody;
+    const T *rJ, *p, *rreg, *bminv, *bIinv, *mut, *mui;
+    const double *vfd;
+    T shift, eta, rho;
+};
+
+// The PADMM iterates of this thread's units, in registers: slot [s][t] is row t of unit
+// tid + s * group size (a joint row uses t = 0 only); Ax = A x, b the next right-hand side.
+template <typename V, int S>
+struct CrIterates {
+    V x[S][3], y[S][3], z[S][3], yh[S][3], zh[S][3], b[S][3], Ax[S][3];
+};
+
+__device__ __forceinline__ void unit_rows(int u, int nbil, int &r0, int &cnt) {
+    r0 = u < nbil ? u : nbil + 3 * (u - nbil);
+    cnt = u < nbil ? 1 : 3;
+}
+
+// out = A v for the rows of this thread's units (zero on unused slots).  Two barriers; w and g may be
+// reused by the next call at once.
+template <typename V, typename T, int S>
+__device__ __forceinline__ void cr_apply(const CrWorld<T> &c, const Group &g, const V (&v)[S][3], V (&out)[S][3],
+                                         V *w, V *gb) {
+#pragma unroll
+    for (int sl = 0; sl < S; ++sl) {
+        const int u = g.tid + sl * g.size;
+        if (u >= c.nunits) continue;
+        int r0, cnt;
+        unit_rows(u, c.nbil, r0, cnt);
+        for (int t = 0; t < cnt; ++t) w[r0 + t] = V(c.p[r0 + t]) * v[sl][t];
+    }
+    g.sync();
+    const int nthr = g.size, tid = g.tid, LB = c.LB;
+    for (int base = 0; base < c.nb * LB; base += nthr) {
+        if (base + (tid & ~31) >= c.nb * LB) continue;          // the whole warp is past the bodies
+        const int t = base + tid, body = t / LB, sub = t - body * LB;
+        const bool on = t < c.nb * LB;
+        V f[6] = {V(0), V(0), V(0), V(0), V(0), V(0)};
+        if (on) {
+            for (int e = c.bro[body] + sub; e < c.bro[body + 1]; e += LB) {
+                const int code = c.brow[e];
+                const V wr = w[code >> 1];
+                const T *J = c.rJ + 6 * code;                     // 12 r + 6 side
+#pragma unroll
+                for (int k = 0; k < 6; ++k) f[k] = fma(V(J[k]), wr, f[k]);
+            }
+        }
+        for (int o = LB >> 1; o > 0; o >>= 1) {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) f[k] += __shfl_xor_sync(0xffffffffu, f[k], o);
+        }
+        if (on && sub == 0) {
+            const V mi = V(c.bminv[body]);
+            const T *Si = c.bIinv + 6 * body;
+            const V s0 = V(Si[0]), s1 = V(Si[1]), s2 = V(Si[2]), s3 = V(Si[3]), s4 = V(Si[4]), s5 = V(Si[5]);
+            V *o = gb + 6 * body;
+            o[0] = mi * f[0]; o[1] = mi * f[1]; o[2] = mi * f[2];
+            o[3] = s0 * f[3] + s3 * f[4] + s4 * f[5];
+            o[4] = s3 * f[3] + s1 * f[4] + s5 * f[5];
+            o[5] = s4 * f[3] + s5 * f[4] + s2 * f[5];
+        }
+    }
+    g.sync();
+#pragma unroll
+    for (int sl = 0; sl < S; ++sl) {
+        const int u = g.tid + sl * g.size;
+#pragma unroll
+        for (int t = 0; t < 3; ++t) out[sl][t] = V(0);
+        if (u >= c.nunits) continue;
+        int r0, cnt;
+        unit_rows(u, c.nbil, r0, cnt);
+        for (int t = 0; t < cnt; ++t) {
+            const int r = r0 + t, sa = c.rbody[2 * r], sb = c.rbody[2 * r + 1];
+            const T *J = c.rJ + 12 * r;
+            V acc = V(0);
+            if (sa >= 0) {
+#pragma unroll
+                for (int k = 0; k < 6; ++k) acc = fma(V(J[k]), gb[6 * sa + k], acc);
+            }
+            if (sb >= 0) {
+#pragma unroll
+                for (int k = 0; k < 6; ++k) acc = fma(V(J[6 + k]), gb[6 * sb + k], acc);
+            }
+            const V pr = V(c.p[r]);
+            out[sl][t] = pr * acc + (V(c.shift) + pr * pr * V(c.rreg[r])) * v[sl][t];
+        }
+    }
+}
+
+// b = v_f + Gamma(z^) - eta x - rho y^ - z^ for this thread's units (Alg. 1's right-hand side).
+template <typename V, typename T, int S>
+__device__ __forceinline__ void cr_rhs(const CrWorld<T> &c, const Group &g, CrIterates<V, S> &I) {
+#pragma unroll
+    for (int sl = 0; sl < S; ++sl) {
+        const int u = g.tid + sl * g.size;
+        if (u >= c.nunits) continue;
+        int r0, cnt;
+        unit_rows(u, c.nbil, r0, cnt);
+        const V s = cnt == 3 ? V(c.mut[u - c.nbil]) * sqrt(I.zh[sl][0] * I.zh[sl][0] + I.zh[sl][1] * I.zh[sl][1]) : V(0);
+        for (int t = 0; t < cnt; ++t)
+            I.b[sl][t] = V(c.vfd[r0 + t]) + (t == 2 ? s : V(0)) - V(c.eta) * I.x[sl][t] - V(c.rho) * I.yh[sl][t] -
+                         I.zh[sl][t];
+    }
+}
+
+// Nesterov state of Alg. 1 (Sec. 4.1), kept in FP64 whatever the iterates' type.
+struct CrMomentum {
+    double a, c_prev;
+};
+
+// PADMM iterations it ... iters with the sparse x-step (k CR iterations).  Returns true when it stopped
+// because `switch64` is set and r_p, r_d fell below KAMINO_REFINE64_BELOW (the caller continues in
+// FP64); `it` is then the next iteration.  Otherwise `it` is the last iteration run.
+template <typename V, typename T, int S>
+__device__ bool cr_padmm(const CrWorld<T> &c, const Group &g, CrIterates<V, S> &I, V *w, V *gb, V *red, int &ph,
+                         int &it, int iters, int k, double tol, bool nesterov, CrMomentum &mom, double &rp, double &rd,
+                         double &rc, bool &converged, bool switch64) {
+    const V eta = V(c.eta), rho = V(c.rho), irho = V(1) / V(c.rho);
+    for (; it <= iters; ++it) {
+        V xprev[S][3], r[S][3], pd[S][3], Ap[S][3], Ar[S][3];
+        // -- x-step: CR on A x = -b from x^{i-1}: r0 = -b - A x^{i-1}
+#pragma unroll
+        for (int sl = 0; sl < S; ++sl)
+#pragma unroll
+            for (int t = 0; t < 3; ++t) {
+                xprev[sl][t] = I.x[sl][t];
+                r[sl][t] = -I.b[sl][t] - I.Ax[sl][t];
+            }
+        cr_apply<V, T, S>(c, g, r, Ar, w, gb);
+        V s0 = V(0), s1 = V(0), s2 = V(0);
+#pragma unroll
+        for (int sl = 0; sl < S; ++sl)
+#pragma unroll
+            for (int t = 0; t < 3; ++t) {
+                pd[sl][t] = r[sl][t];
+                Ap[sl][t] = Ar[sl][t];
+                s0 = fma(r[sl][t], Ar[sl][t], s0);
+                s1 = fma(Ar[sl][t], Ar[sl][t], s1);
+            }
+        group_sum3<V>(s0, s1, s2, red, ph++ & 1, g);
+        V rAr = s0, ApAp = s1;
+        for (int j = 0; j < k; ++j) {
+            if (!(rAr > V(0)) || !(ApAp > V(0))) break;           // the residual vanished (uniform)
+            const V alpha = rAr / ApAp;
+#pragma unroll
+            for (int sl = 0; sl < S; ++sl)
+#pragma unroll
+                for (int t = 0; t < 3; ++t) {
+                    I.x[sl][t] = fma(alpha, pd[sl][t], I.x[sl][t]);
+                    r[sl][t] = fma(-alpha, Ap[sl][t], r[sl][t]);
+                }
+            if (j == k - 1) break;
+            cr_apply<V, T, S>(c, g, r, Ar, w, gb);
+            s0 = s1 = s2 = V(0);
+#pragma unroll
+            for (int sl = 0; sl < S; ++sl)
+#pragma unroll
+                for (int t = 0; t < 3; ++t) {
+                    s0 = fma(r[sl][t], Ar[sl][t], s0);
+                    s1 = fma(Ar[sl][t], Ar[sl][t], s1);
+                    s2 = fma(Ar[sl][t], Ap[sl][t], s2);
+                }
+            group_sum3<V>(s0, s1, s2, red, ph++ & 1, g);
+            // beta = (r', A r') / (r, A r); A p' = A r' + beta A p, so
+            // (A p', A p') = (A r', A r') + 2 beta (A r', A p) + beta^2 (A p, A p)
+            const V beta = s0 / rAr;
+            rAr = s0;
+            ApAp = s1 + V(2) * beta * s2 + beta * beta * ApAp;
+#pragma unroll
+            for (int sl = 0; sl < S; ++sl)
+#pragma unroll
+                for (int t = 0; t < 3; ++t) {
+                    pd[sl][t] = fma(beta, pd[sl][t], r[sl][t]);
+                    Ap[sl][t] = fma(beta, Ap[sl][t], Ar[sl][t]);
+                }
+        }
+        // -- A x^i, evaluated (not carried by the recurrence): the x-step's residual A x + b enters the
+        // dual residual, and it is the next iteration's starting residual
+        cr_apply<V, T, S>(c, g, I.x, I.Ax, w, gb);
+        // -- owners: y^i = Pi_K(x^i - z^/rho), z^i = z^ - rho (x^i - y^i), residual terms
+        V lrp = V(0), lrd = V(0), lrc = V(0), lc = V(0);
+        V yn[S][3], zn[S][3];
+#pragma unroll
+        for (int sl = 0; sl < S; ++sl) {
+            const int u = g.tid + sl * g.size;
+#pragma unroll
+            for (int t = 0; t < 3; ++t) yn[sl][t] = zn[sl][t] = V(0);
+            if (u >= c.nunits) continue;
+            if (u < c.nbil) {
+                const V xv = I.x[sl][0];
+                V yv = xv - I.zh[sl][0] * irho;
+                if (u >= c.nfix) yv = fmax(yv, V(0));             // joint-limit rows: the ray R+
+                const V zv = I.zh[sl][0] - rho * (xv - yv);
+                const V lin = I.Ax[sl][0] + I.b[sl][0];
+                lrp = fmax(lrp, fabs(xv - yv));
+                lrd = fmax(lrd, fabs(eta * (xv - xprev[sl][0]) + rho * (yv - I.yh[sl][0]) - lin));
+                lc += (zv - I.zh[sl][0]) * (zv - I.zh[sl][0]) * irho + rho * (yv - I.yh[sl][0]) * (yv - I.yh[sl][0]);
+                if (u >= c.nfix) lrc = fmax(lrc, fabs(yv * zv));
+                yn[sl][0] = yv;
+                zn[sl][0] = zv;
+            } else {
+                const int kc = u - c.nbil;
+                const V mu = V(c.mut[kc]);
+                V v[3], yv[3];
+#pragma unroll
+                for (int t = 0; t < 3; ++t) v[t] = I.x[sl][t] - I.zh[sl][t] * irho;
+                const V tn = sqrt(v[0] * v[0] + v[1] * v[1]);
+                if (tn <= mu * v[2]) {
+                    yv[0] = v[0]; yv[1] = v[1]; yv[2] = v[2];
+                } else if (mu * tn <= -v[2]) {
+                    yv[0] = yv[1] = yv[2] = V(0);
+                } else {
+                    const V nn = (mu * tn + v[2]) * V(c.mui[kc]);
+                    const V sc = mu * nn / tn;
+                    yv[0] = sc * v[0]; yv[1] = sc * v[1]; yv[2] = nn;
+                }
+                V ydz = V(0);
+#pragma unroll
+                for (int t = 0; t < 3; ++t) {
+                    const V xv = I.x[sl][t];
+                    const V zv = I.zh[sl][t] - rho * (xv - yv[t]);
+                    const V lin = I.Ax[sl][t] + I.b[sl][t];
+                    lrp = fmax(lrp, fabs(xv - yv[t]));
+                    lrd = fmax(lrd, fabs(eta * (xv - xprev[sl][t]) + rho * (yv[t] - I.yh[sl][t]) - lin));
+                    lc += (zv - I.zh[sl][t]) * (zv - I.zh[sl][t]) * irho + rho * (yv[t] - I.yh[sl][t]) * (yv[t] - I.yh[sl][t]);
+                    ydz += yv[t] * zv;
+                    yn[sl][t] = yv[t];
+                    zn[sl][t] = zv;
+                }
+                lrc = fmax(lrc, fabs(ydz));
+            }
+        }
+        group_reduce4<V>(lrp, lrd, lrc, lc, red, ph++ & 1, g);
+        rp = (double)lrp; rd = (double)lrd; rc = (double)lrc;
+        converged = rp < tol && rd < tol && rc < tol;
+        // -- Nesterov with adaptive restart (uniform decision), commit, next right-hand side
+        double beta_n = 0.0;
+        bool restart = false;
+        if (nesterov) {
+            if ((double)lc < 0.999 * mom.c_prev) {
+                const double an = 0.5 * (1.0 + sqrt(1.0 + 4.0 * mom.a * mom.a));
+                beta_n = (mom.a - 1.0) / an;
+                mom.a = an;
+                mom.c_prev = (double)lc;
+            } else {
+                restart = true;
+                mom.a = 1.0;
+                mom.c_prev = mom.c_prev / 0.999;
+            }
+        }
+        const V bn = V(beta_n);
+#pragma unroll
+        for (int sl = 0; sl < S; ++sl)
+#pragma unroll
+            for (int t = 0; t < 3; ++t) {
+                const V yv = yn[sl][t], zv = zn[sl][t];
+                if (!nesterov) { I.yh[sl][t] = yv; I.zh[sl][t] = zv; }
+                else if (restart) { I.yh[sl][t] = I.y[sl][t]; I.zh[sl][t] = I.z[sl][t]; }
+                else { I.yh[sl][t] = yv + bn * (yv - I.y[sl][t]); I.zh[sl][t] = zv + bn * (zv - I.z[sl][t]); }
+                I.y[sl][t] = yv;
+                I.z[sl][t] = zv;
+            }
+        cr_rhs<V, T, S>(c, g, I);
+        if (converged) return false;
+        if (switch64 && fmax(rp, rd) < KAMINO_REFINE64_BELOW) { ++it; return true; }
+    }
+    it = iters;
+    return false;
+}
+
 // ----------------------------------------------------------------------------- the step kernel
 // S: PADMM units per thread (units <= S * group size).  tbase: tensor-memory columns of the CTA
 // (tm_cta: allocated by the kernel, whole-CTA group) that hold the inverse of worlds of up to 256
 // padded rows.
-template <typename T, int NB, int S>
+template <typename T, int NB, int S, bool CR>
 __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, const Group &g, uint32_t tbase,
                            bool tm_cta) {
     const int tid = g.tid, lane = g.lane(), warp = g.warp(), nthr = g.size, nwarps = g.warps();
@@ -1138,7 +1459,7 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
     const int b0 = wa.x, j0 = wa.y, c0 = wa.z, k0 = wa.w;
     const int nb = wb.x, nj = wb.y, nc = wb.z, nfix = wb.w;
     const int nlc = M.world_c ? M.world_c[w].x : 0;       // joint-limit candidates
-    const Layout L = make_layout<T>(a.nb_max, a.nj_max, a.nc_max, a.mp_max, NB, a.nl_max);
+    const Layout L = make_layout<T>(a.nb_max, a.nj_max, a.nc_max, a.mp_max, NB, a.nl_max, !CR);
     double *bq = (double *)(smem + L.bq);
     T *bu = (T *)(smem + L.bu), *bI = (T *)(smem + L.bI);
     double *bRd = (double *)(smem + L.bRd);
@@ -1386,356 +1707,455 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
     g.sync();
     for (int r = tid; r < mp; r += nthr) {
         vfd[r] = r < m ? (double)p[r] * vfd[r] : 0.0;
-        bb[r] = T(0);
+        if constexpr (!CR) bb[r] = T(0);
     }
     for (int k = tid; k < nact; k += nthr) {
         const int rt = nbil + 3 * k;
         mut[k] = M.world_mu[w] * p[rt + 2] / p[rt];
         mui[k] = T(1) / (T(1) + mut[k] * mut[k]);
     }
-    // ---- 5c. A = P (D + R) P + (eta + rho) I in packed storage (identity on the padding rows)
-    const T shift = a.eta + a.rho;
-    for (int j = warp; j < mp; j += nwarps) {
-        T *col = A + col_start(j, mp) - j;
-        const int ja = j < m ? rbody[2 * j] : -2, jb = j < m ? rbody[2 * j + 1] : -2;
-        for (int i = j + lane; i < mp; i += 32) {
-            T v;
-            if (i >= m || j >= m) {
-                v = i == j ? T(1) : T(0);
-            } else {
-                const int ia = rbody[2 * i], ib = rbody[2 * i + 1];
-                const T *Ji = rJ + 12 * i;
-                const T *Mj = MJ + 12 * j;
-                T s = T(0);
-                if (ia >= 0 && ia == ja) for (int k = 0; k < 6; ++k) s += Ji[k] * Mj[k];
-                if (ia >= 0 && ia == jb) for (int k = 0; k < 6; ++k) s += Ji[k] * Mj[6 + k];
-                if (ib == ja) for (int k = 0; k < 6; ++k) s += Ji[6 + k] * Mj[k];
-                if (ib == jb) for (int k = 0; k < 6; ++k) s += Ji[6 + k] * Mj[6 + k];
-                v = p[i] * p[j] * s + (i == j ? shift + p[i] * p[i] * rreg[i] : T(0));
-            }
-            col[i] = v;
-        }
-    }
-    g.sync();
-
-    // ---- 6. warm start: x0 = y0 = P^-1 lambda0, z0 = v0 + Gamma(v0), v0 = D~ x0 + v~_f
-    const bool warm = a.warm_mode != KAMINO_WARM_COLD;
-    for (int r = tid; r < mp; r += nthr) {
-        T l0 = T(0);
-        if (warm && r < m) {
-            const T *src = a.warm_mode == KAMINO_WARM_EXTERNAL ? a.warm : a.cache;
-            if (src) {   // cache layout: fixed rows, limit candidates, 3 per contact candidate
-                if (r < nfix) l0 = src[k0 + r];
-                else if (r < nbil) l0 = src[k0 + nfix + lcid[r - nfix]];
-                else {
-                    const int k = (r - nbil) / 3, t = (r - nbil) % 3;
-                    l0 = src[k0 + nfix + nlc + 3 * cid[k] + t];
-                }
-            }
-        }
-        x[r] = l0 / p[r];
-    }
-    g.sync();
-    if (warm) {
-        symv_packed(A, mp, x, xn, X, g);          // xn = A x0 = D~ x0 + (eta + rho) x0
-        for (int u = tid; u < nunits; u += nthr) {
-            if (u < nbil) {
-                const T v0 = xn[u] - shift * x[u] + T(vfd[u]);
-                z[u] = v0;
-            } else {
-                const int r0 = nbil + 3 * (u - nbil);
-                T v0[3];
-                for (int t = 0; t < 3; ++t) v0[t] = xn[r0 + t] - shift * x[r0 + t] + T(vfd[r0 + t]);
-                z[r0] = v0[0]; z[r0 + 1] = v0[1];
-                z[r0 + 2] = v0[2] + mut[u - nbil] * sqrt(v0[0] * v0[0] + v0[1] * v0[1]);
-            }
-        }
-    }
-    for (int r = tid; r < mp; r += nthr) {
-        if (!warm || r >= m) z[r] = T(0);
-        y[r] = x[r]; yh[r] = x[r]; zh[r] = z[r];
-    }
-    g.sync();
-
-    // ---- 7. A <- -A^-1 (blocked sweep): in tensor memory (mixed mode, whole CTA, mp <= 256), else
-    // on the packed triangle in shared memory, then stored into tensor memory (FP32 mode, whole
-    // CTA) or re-stored as BF16 tiles (mixed mode otherwise); per-body row lists for the
-    // matrix-free products
-    const bool tm = tm_cta && mp <= 256;
-    bool in_tmem = false;                 // the inverse is already in tensor memory
-    if constexpr (sizeof(T) == 4 && NB == 16) {
-        // the two K-major panels (256 rows x 16) and the pivot block must fit the scratch X
-        if (tm && a.mixed && L.A - L.X >= (size_t)(2 * 256 * 16 + 256) * sizeof(float)) {
-            if (!sweep_inverse_tmem(A, mp, X, tbase, misc, g)) {
-                // the tensor cores did not complete: report the world, leave its state as it was
-                if (tid == 0) {
-                    kamino_residual rep{};
-                    rep.iterations = 0;
-                    rep.status = KAMINO_WORLD_NOT_CONVERGED | KAMINO_WORLD_TIMEOUT;
-                    rep.num_rows = m;
-                    rep.num_contacts = nact;
-                    rep.r_primal = rep.r_dual = rep.r_compl = rep.r_ncp = INFINITY;
-                    a.res[w] = rep;
-                }
-                g.sync();
-                return;
-            }
-            in_tmem = true;
-        }
-    }
-    if (!in_tmem) sweep_inverse<T, NB>(A, mp, X, a.mixed != 0, g);
-    if constexpr (sizeof(T) == 4) {
-        if (tm && !in_tmem) tmem_store_inverse(A, mp, tbase, g);
-    }
-    if (a.mixed && !tm) pack_bf16_tiles(A, mp, X, g);
-    for (int i = tid; i < nb; i += nthr) {
-        int cnt = 0;
-        for (int r = 0; r < m; ++r) cnt += (rbody[2 * r] == i) + (rbody[2 * r + 1] == i);
-        bro[i + 1] = cnt;
-    }
-    g.sync();
-    if (tid == 0) {
-        bro[0] = 0;
-        for (int i = 0; i < nb; ++i) bro[i + 1] += bro[i];
-    }
-    g.sync();
-    for (int i = tid; i < nb; i += nthr) {
-        int e = bro[i];
-        for (int r = 0; r < m; ++r) {
-            if (rbody[2 * r] == i) brow[e++] = 2 * r;
-            if (rbody[2 * r + 1] == i) brow[e++] = 2 * r + 1;
-        }
-    }
-
-    // ---- 8. Proximal-ADMM (Alg. 1).  The linear solve of every iteration is one step of
-    // iterative refinement from the previous x:  x^i = x^{i-1} - A^-1 (b + A x^{i-1}), with A x
-    // evaluated matrix-free from the rows (P J M^-1 J^T P x + (eta + rho) x) and A^-1 the swept
-    // inverse.  At a fixed point A x = -b holds to the accuracy of the matrix-free product, so the
-    // inverse's own rounding (which the nearly singular D~ would amplify) does not move the
-    // solution.  With refine64, once r_p and r_d fall below KAMINO_REFINE64_BELOW the refinement
-    // end game runs in FP64: the right-hand side b (from the FP64 v_f), the per-body velocities
-    // M^-1 J^T P x and the residual b + A x are formed in FP64, and the iterates x, y, z, y^, z^
-    // themselves are kept in FP64 (in shared memory that is dead during the loop), as in iterative
-    // refinement whose solution is accumulated in the higher precision: an FP32 iterate cannot hold
-    // the solution of these mechanisms closer than ~1e-4 in u+ (u+ is a small difference of large
-    // joint impulses through light bodies).  The correction S (b + A x) stays on the FP32 / BF16
-    // inverse.
-    //
-    // Unit u (a joint row, or the three rows of a contact) belongs to thread u mod group size for
-    // the whole solve: only its owner writes its x, b, y, z, y^, z^ (the residual rows read x and b
-    // row by row after a barrier), so an iteration has four barriers (after the per-body gather,
-    // after the residual rows, after the mat-vec, and the residual reduction, which also publishes
-    // x, P x and b).
-    const T eta = a.eta, rho = a.rho, irho = T(1) / a.rho;
-    double *bbd = reinterpret_cast<double *>(X + kWarps * mp);   // FP32 worlds only (make_layout)
-    double *gbd = bbd + mp;
-    __nv_bfloat16 *chi = reinterpret_cast<__nv_bfloat16 *>(X), *clo = chi + mp;   // mixed: split c
-    // the FP64 end game only matters below the FP32 residual floor, i.e. for tolerances under the
-    // switch level
-    const bool use64 = sizeof(T) == 4 && a.refine64 && a.tol < T(KAMINO_REFINE64_BELOW);
-    double *x64 = nullptr;
-    if (use64) x64 = fp64_iterates(smem, L, tm, a.mixed && !tm, mp, nb, X);
-    double *y64 = x64 + mp, *z64 = x64 + 2 * mp, *yh64 = x64 + 3 * mp, *zh64 = x64 + 4 * mp;
-    double *yn64 = x64 + 5 * mp, *zn64 = x64 + 6 * mp;
-    bool hp = false;     // b of the coming iteration is the FP64 one; set once, uniform over the group
-    bool hpv = false;    // the iterates live in the FP64 vectors (from the commit after hp is set)
-    bool x_in64 = false; // the last owner update wrote x to the FP64 vector
-    int LB = 8;          // lanes per body in the gather: a power of two with LB * nb <= group size
-    while (LB > 1 && LB * nb > nthr) LB >>= 1;
-    T acc_a = T(1), c_prev = T(INFINITY);
+    double *yfin = nullptr;   // the final y in FP64 when the iterates ended in FP64 (or the sparse formulation)
+    double *fd = nullptr;     // FP64 scratch of 6 nb words for phase 9
     T rp = T(INFINITY), rd = T(INFINITY), rc = T(INFINITY);
     int it = 0;
     bool converged = false;
-    // b = v_f + Gamma(z^) - eta x - rho y^ - z^ and w = P x for the first iteration
-    for (int u = tid; u < nunits; u += nthr) {
-        if (u < nbil) {
-            bb[u] = T(vfd[u]) - eta * x[u] - rho * yh[u] - zh[u];
-            wv[u] = p[u] * x[u];
-        } else {
-            const int r0 = nbil + 3 * (u - nbil);
-            const T s = mut[u - nbil] * sqrt(zh[r0] * zh[r0] + zh[r0 + 1] * zh[r0 + 1]);
+    if constexpr (CR) {
+        // ---- 5c'-8'. Sparse formulation (Sec. 5.1): no matrix, no factorisation; Alg. 1 with every
+        // x-step k Conjugate Residual iterations on the matrix-free operator (see cr_padmm)
+        g.sync();
+        body_row_lists(g, nb, m, rbody, bro, brow);
+        int LB = 8;               // lanes per body in the gather: a power of two with LB * nb <= group size
+        while (LB > 1 && LB * nb > nthr) LB >>= 1;
+        const CrWorld<T> cw{nunits, nfix, nbil, nb, LB, bro, brow, rbody, rJ, p, rreg, bminv, bIinv, mut, mui,
+                            vfd, T(a.eta + a.rho), a.eta, a.rho};
+        // the assembly scratch X is dead: the final y (FP64), then w and g, both sized for FP64
+        double *y64c = reinterpret_cast<double *>(X);
+        double *wbuf = y64c + a.mp_max;
+        double *gbuf = wbuf + a.mp_max;
+        // ---- 6'. warm start in the owners' registers: x0 = y0 = P^-1 lambda0, z0 = v0 + Gamma(v0),
+        // v0 = A x0 - (eta + rho) x0 + v~_f
+        CrIterates<T, S> I;
+#pragma unroll
+        for (int sl = 0; sl < S; ++sl)
+#pragma unroll
+            for (int t = 0; t < 3; ++t)
+                I.x[sl][t] = I.y[sl][t] = I.z[sl][t] = I.yh[sl][t] = I.zh[sl][t] = I.b[sl][t] = I.Ax[sl][t] = T(0);
+        const bool warm = a.warm_mode != KAMINO_WARM_COLD;
+        const T *src = !warm ? nullptr : a.warm_mode == KAMINO_WARM_EXTERNAL ? a.warm : a.cache;
+#pragma unroll
+        for (int sl = 0; sl < S; ++sl) {
+            const int u = tid + sl * nthr;
+            if (u >= nunits || src == nullptr) continue;
+            int r0, cnt;
+            unit_rows(u, nbil, r0, cnt);
+            for (int t = 0; t < cnt; ++t) {   // cache layout: fixed rows, limit candidates, 3 per contact candidate
+                const int r = r0 + t;
+                T l0;
+                if (r < nfix) l0 = src[k0 + r];
+                else if (r < nbil) l0 = src[k0 + nfix + lcid[r - nfix]];
+                else l0 = src[k0 + nfix + nlc + 3 * cid[u - nbil] + t];
+                I.x[sl][t] = l0 / p[r];
+            }
+        }
+        if (warm) {
+            cr_apply<T, T, S>(cw, g, I.x, I.Ax, reinterpret_cast<T *>(wbuf), reinterpret_cast<T *>(gbuf));
+            const T shift = T(a.eta + a.rho);
+#pragma unroll
+            for (int sl = 0; sl < S; ++sl) {
+                const int u = tid + sl * nthr;
+                if (u >= nunits) continue;
+                int r0, cnt;
+                unit_rows(u, nbil, r0, cnt);
+                T v0[3] = {T(0), T(0), T(0)};
+                for (int t = 0; t < cnt; ++t) v0[t] = I.Ax[sl][t] - shift * I.x[sl][t] + T(vfd[r0 + t]);
+                for (int t = 0; t < cnt; ++t) I.z[sl][t] = v0[t];
+                if (cnt == 3) I.z[sl][2] += mut[u - nbil] * sqrt(v0[0] * v0[0] + v0[1] * v0[1]);
+            }
+        }
+#pragma unroll
+        for (int sl = 0; sl < S; ++sl)
+#pragma unroll
             for (int t = 0; t < 3; ++t) {
-                bb[r0 + t] = T(vfd[r0 + t]) + (t == 2 ? s : T(0)) - eta * x[r0 + t] - rho * yh[r0 + t] - zh[r0 + t];
-                wv[r0 + t] = p[r0 + t] * x[r0 + t];
+                I.y[sl][t] = I.yh[sl][t] = I.x[sl][t];
+                I.zh[sl][t] = I.z[sl][t];
             }
-        }
-    }
-    if (a.mixed && !tm) {
-        for (int r = m + tid; r < mp; r += nthr) {
-            chi[r] = __float2bfloat16(0.0f);
-            clo[r] = __float2bfloat16(0.0f);
-        }
-    }
-    g.sync();
-    for (it = 1; it <= a.iters; ++it) {
-        // [8a] per body: g_b = M_b^-1 sum over the body's rows r of J_rb^T (P x)_r; LB lanes per
-        // body take its rows round-robin, then a shuffle reduction
-        for (int base = 0; base < nb * LB; base += nthr) {
-            if (base + (tid & ~31) >= nb * LB) continue;          // the whole warp is past the bodies
-            const int t = base + tid, body = t / LB, sub = t - body * LB;
-            const bool on = t < nb * LB;
-            if (hp) {
-                double f[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-                if (on) {
-                    for (int e = bro[body] + sub; e < bro[body + 1]; e += LB) {
-                        const int code = brow[e], r = code >> 1;
-                        const double w = (double)p[r] * (x_in64 ? x64[r] : (double)x[r]);
-                        const T *J = rJ + 6 * code;                 // 12 r + 6 side
-#pragma unroll
-                        for (int k = 0; k < 6; ++k) f[k] = fma((double)J[k], w, f[k]);
-                    }
-                }
-                for (int o = LB >> 1; o > 0; o >>= 1) {
-#pragma unroll
-                    for (int k = 0; k < 6; ++k) f[k] += __shfl_xor_sync(0xffffffffu, f[k], o);
-                }
-                if (on && sub == 0) {
-                    const double mi = bminv[body];
-                    for (int k = 0; k < 3; ++k) gbd[6 * body + k] = mi * f[k];
-                    symvec3d(bIinv + 6 * body, f + 3, gbd + 6 * body + 3);
-                }
-            } else {
-                T f[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
-                if (on) {
-                    for (int e = bro[body] + sub; e < bro[body + 1]; e += LB) {
-                        const int code = brow[e];
-                        const T w = wv[code >> 1];
-                        const T *J = rJ + 6 * code;
-#pragma unroll
-                        for (int k = 0; k < 6; ++k) f[k] = fma(J[k], w, f[k]);
-                    }
-                }
-                for (int o = LB >> 1; o > 0; o >>= 1) {
-#pragma unroll
-                    for (int k = 0; k < 6; ++k) f[k] += __shfl_xor_sync(0xffffffffu, f[k], o);
-                }
-                if (on && sub == 0) {
-                    const T mi = bminv[body];
-                    for (int k = 0; k < 3; ++k) fb[6 * body + k] = mi * f[k];
-                    symvec3(bIinv + 6 * body, f + 3, fb + 6 * body + 3);
-                }
-            }
-        }
-        g.sync();
-        // [8b] thread r: c_r = b_r + p_r J_r (g_A, g_B) + (eta + rho) x_r (b_r and x_r were written by
-        // the row's owner before the last barrier), stored as the BF16 hi / lo split (mixed, inverse
-        // in shared memory) or in bb (tensor-memory, FP32 and FP64 mat-vecs)
-        for (int r = tid; r < m; r += nthr) {
-            const int sa = rbody[2 * r], sb = rbody[2 * r + 1];
-            const T *J = rJ + 12 * r;
-            T c;
-            if (hp) {
-                double acc = 0.0;
-                if (sa >= 0) {
-#pragma unroll
-                    for (int k = 0; k < 6; ++k) acc = fma((double)J[k], gbd[6 * sa + k], acc);
-                }
-                if (sb >= 0) {
-#pragma unroll
-                    for (int k = 0; k < 6; ++k) acc = fma((double)J[6 + k], gbd[6 * sb + k], acc);
-                }
-                const double xr = x_in64 ? x64[r] : (double)x[r];
-                c = T(bbd[r] + (double)p[r] * acc + ((double)shift + (double)p[r] * (double)p[r] * (double)rreg[r]) * xr);
-            } else {
-                T acc = T(0);
-                if (sa >= 0) {
-#pragma unroll
-                    for (int k = 0; k < 6; ++k) acc = fma(J[k], fb[6 * sa + k], acc);
-                }
-                if (sb >= 0) {
-#pragma unroll
-                    for (int k = 0; k < 6; ++k) acc = fma(J[6 + k], fb[6 * sb + k], acc);
-                }
-                c = bb[r] + p[r] * acc + (shift + p[r] * p[r] * rreg[r]) * x[r];
-            }
-            if (a.mixed && !tm) {
-                const float v = (float)c;
-                const __nv_bfloat16 h = __float2bfloat16(v);
-                chi[r] = h;
-                clo[r] = __float2bfloat16(v - __bfloat162float(h));
-            } else {
-                bb[r] = c;
-            }
-        }
-        g.sync();
-        // [8c] correction: xn = S c with S = -A^-1, so x^i = x^{i-1} + xn (ends with a barrier)
-        bool done_c = false;
+        cr_rhs<T, T, S>(cw, g, I);
+        // ---- 8'. Alg. 1, then (refine64, tolerances below KAMINO_REFINE64_BELOW) the same iterations
+        // in FP64 from the moment r_p and r_d fall below that level
+        CrMomentum mom{1.0, (double)INFINITY};
+        int ph = 0;
+        double rpd = INFINITY, rdd = INFINITY, rcd = INFINITY;
+        it = 1;
+        const bool use64 = sizeof(T) == 4 && a.refine64 && a.tol < T(KAMINO_REFINE64_BELOW);
+        const bool sw = cr_padmm<T, T, S>(cw, g, I, reinterpret_cast<T *>(wbuf), reinterpret_cast<T *>(gbuf),
+                                          reinterpret_cast<T *>(red), ph, it, a.iters, a.cr_iters, (double)a.tol,
+                                          a.nesterov != 0, mom, rpd, rdd, rcd, converged, use64);
+        bool done = false;
         if constexpr (sizeof(T) == 4) {
-            if (tm) { tmem_matvec(tbase, mp, bb, xn, g); done_c = true; }
-        }
-        if (!done_c) {
-            if (a.mixed) apply_bf16_tiles(A, mp, chi, clo, xn, g);
-            else symv_packed(A, mp, bb, xn, X, g);
-        }
-        // [8d] owners: x^i, y^i = Pi_K(x^i - z^/rho), z^i = z^ - rho (x^i - y^i), residual terms; x and
-        // P x go to shared memory at once (the reduction's barrier publishes them for [8a])
-        T lrp = T(0), lrd = T(0), lrc = T(0), lc = T(0);
-        T xnT[S][3], ynT[S][3], znT[S][3];          // units tid + s * group size
-        if (hpv) {
-            // the new FP64 iterates wait for the commit in shared memory (x^i in x, y^i and z^i in
-            // the two spare vectors), not in registers across the reduction
-            double xnD[S][3], ynD[S][3], znD[S][3];
-            owner_update<double, T, S>(g, nunits, nfix, nbil, x64, xn, yh64, zh64, mut, mui, p, wv, eta, rho, irho, xnD, ynD,
-                                       znD, lrp, lrd, lrc, lc);
-            stash_rows<S>(g, nunits, nbil, ynD, yn64);
-            stash_rows<S>(g, nunits, nbil, znD, zn64);
-        } else {
-            owner_update<T, T, S>(g, nunits, nfix, nbil, x, xn, yh, zh, mut, mui, p, wv, eta, rho, irho, xnT, ynT, znT, lrp,
-                                  lrd, lrc, lc);
-        }
-        x_in64 = hpv;
-        group_reduce4(lrp, lrd, lrc, lc, red, it & 1, g);
-        rp = lrp; rd = lrd; rc = lrc;
-        converged = rp < a.tol && rd < a.tol && rc < a.tol;
-        hp = use64 && (hp || fmax(rp, rd) < T(KAMINO_REFINE64_BELOW));
-        // Nesterov with adaptive restart (uniform decision), then the owners commit y, z, y^, z^ and
-        // form the next iteration's b (in FP64 once hp is set)
-        T beta_n = T(0);
-        bool restart = false;
-        if (a.nesterov) {
-            if (lc < T(0.999) * c_prev) {
-                const T an = T(0.5) * (T(1) + sqrt(T(1) + T(4) * acc_a * acc_a));
-                beta_n = (acc_a - T(1)) / an;
-                acc_a = an;
-                c_prev = lc;
-            } else {
-                restart = true;
-                acc_a = T(1);
-                c_prev = c_prev / T(0.999);
+            if (sw) {
+                CrIterates<double, S> D;
+#pragma unroll
+                for (int sl = 0; sl < S; ++sl)
+#pragma unroll
+                    for (int t = 0; t < 3; ++t) {
+                        D.x[sl][t] = I.x[sl][t]; D.y[sl][t] = I.y[sl][t]; D.z[sl][t] = I.z[sl][t];
+                        D.yh[sl][t] = I.yh[sl][t]; D.zh[sl][t] = I.zh[sl][t]; D.b[sl][t] = 0.0;
+                    }
+                cr_rhs<double, T, S>(cw, g, D);                      // from the FP64 v_f
+                cr_apply<double, T, S>(cw, g, D.x, D.Ax, wbuf, gbuf);
+                cr_padmm<double, T, S>(cw, g, D, wbuf, gbuf, reinterpret_cast<double *>(red), ph, it, a.iters,
+                                       a.cr_iters, (double)a.tol, a.nesterov != 0, mom, rpd, rdd, rcd, converged, false);
+#pragma unroll
+                for (int sl = 0; sl < S; ++sl) {
+                    const int u = tid + sl * nthr;
+                    if (u >= nunits) continue;
+                    int r0, cnt;
+                    unit_rows(u, nbil, r0, cnt);
+                    for (int t = 0; t < cnt; ++t) y64c[r0 + t] = D.y[sl][t];
+                }
+                done = true;
             }
         }
-        if (hpv) {
-            double xnD[S][3], ynD[S][3], znD[S][3];
-            unstash_rows<S>(g, nunits, nbil, x64, xnD);
-            unstash_rows<S>(g, nunits, nbil, yn64, ynD);
-            unstash_rows<S>(g, nunits, nbil, zn64, znD);
-            owner_commit<double, T, S>(g, nunits, nbil, y64, z64, yh64, zh64, vfd, mut, eta, rho, a.nesterov != 0,
-                                       restart, beta_n, xnD, ynD, znD, true, bb, bbd, nullptr, mp);
-        } else {
-            // the iterates move to the FP64 vectors at this commit once the end game has started
-            double *init = hp && x64 != nullptr ? x64 : nullptr;
-            owner_commit<T, T, S>(g, nunits, nbil, y, z, yh, zh, vfd, mut, eta, rho, a.nesterov != 0, restart,
-                                  beta_n, xnT, ynT, znT, hp, bb, bbd, init, mp);
-            hpv = init != nullptr;
+        if (!done) {
+#pragma unroll
+            for (int sl = 0; sl < S; ++sl) {
+                const int u = tid + sl * nthr;
+                if (u >= nunits) continue;
+                int r0, cnt;
+                unit_rows(u, nbil, r0, cnt);
+                for (int t = 0; t < cnt; ++t) y64c[r0 + t] = (double)I.y[sl][t];
+            }
         }
-        if (converged) break;
+        rp = T(rpd); rd = T(rdd); rc = T(rcd);
+        yfin = y64c;
+        fd = gbuf;
+    } else {
+        // ---- 5c. A = P (D + R) P + (eta + rho) I in packed storage (identity on the padding rows)
+        const T shift = a.eta + a.rho;
+        for (int j = warp; j < mp; j += nwarps) {
+            T *col = A + col_start(j, mp) - j;
+            const int ja = j < m ? rbody[2 * j] : -2, jb = j < m ? rbody[2 * j + 1] : -2;
+            for (int i = j + lane; i < mp; i += 32) {
+                T v;
+                if (i >= m || j >= m) {
+                    v = i == j ? T(1) : T(0);
+                } else {
+                    const int ia = rbody[2 * i], ib = rbody[2 * i + 1];
+                    const T *Ji = rJ + 12 * i;
+                    const T *Mj = MJ + 12 * j;
+                    T s = T(0);
+                    if (ia >= 0 && ia == ja) for (int k = 0; k < 6; ++k) s += Ji[k] * Mj[k];
+                    if (ia >= 0 && ia == jb) for (int k = 0; k < 6; ++k) s += Ji[k] * Mj[6 + k];
+                    if (ib == ja) for (int k = 0; k < 6; ++k) s += Ji[6 + k] * Mj[k];
+                    if (ib == jb) for (int k = 0; k < 6; ++k) s += Ji[6 + k] * Mj[6 + k];
+                    v = p[i] * p[j] * s + (i == j ? shift + p[i] * p[i] * rreg[i] : T(0));
+                }
+                col[i] = v;
+            }
+        }
+        g.sync();
+
+        // ---- 6. warm start: x0 = y0 = P^-1 lambda0, z0 = v0 + Gamma(v0), v0 = D~ x0 + v~_f
+        const bool warm = a.warm_mode != KAMINO_WARM_COLD;
+        for (int r = tid; r < mp; r += nthr) {
+            T l0 = T(0);
+            if (warm && r < m) {
+                const T *src = a.warm_mode == KAMINO_WARM_EXTERNAL ? a.warm : a.cache;
+                if (src) {   // cache layout: fixed rows, limit candidates, 3 per contact candidate
+                    if (r < nfix) l0 = src[k0 + r];
+                    else if (r < nbil) l0 = src[k0 + nfix + lcid[r - nfix]];
+                    else {
+                        const int k = (r - nbil) / 3, t = (r - nbil) % 3;
+                        l0 = src[k0 + nfix + nlc + 3 * cid[k] + t];
+                    }
+                }
+            }
+            x[r] = l0 / p[r];
+        }
+        g.sync();
+        if (warm) {
+            symv_packed(A, mp, x, xn, X, g);          // xn = A x0 = D~ x0 + (eta + rho) x0
+            for (int u = tid; u < nunits; u += nthr) {
+                if (u < nbil) {
+                    const T v0 = xn[u] - shift * x[u] + T(vfd[u]);
+                    z[u] = v0;
+                } else {
+                    const int r0 = nbil + 3 * (u - nbil);
+                    T v0[3];
+                    for (int t = 0; t < 3; ++t) v0[t] = xn[r0 + t] - shift * x[r0 + t] + T(vfd[r0 + t]);
+                    z[r0] = v0[0]; z[r0 + 1] = v0[1];
+                    z[r0 + 2] = v0[2] + mut[u - nbil] * sqrt(v0[0] * v0[0] + v0[1] * v0[1]);
+                }
+            }
+            g.sync();   // z of a contact is written by the unit's owner and read below row by row
+        }
+        for (int r = tid; r < mp; r += nthr) {
+            if (!warm || r >= m) z[r] = T(0);
+            y[r] = x[r]; yh[r] = x[r]; zh[r] = z[r];
+        }
+        g.sync();
+
+        // ---- 7. A <- -A^-1 (blocked sweep): in tensor memory (mixed mode, whole CTA, mp <= 256), else
+        // on the packed triangle in shared memory, then stored into tensor memory (FP32 mode, whole
+        // CTA) or re-stored as BF16 tiles (mixed mode otherwise); per-body row lists for the
+        // matrix-free products
+        const bool tm = tm_cta && mp <= 256;
+        bool in_tmem = false;                 // the inverse is already in tensor memory
+        if constexpr (sizeof(T) == 4 && NB == 16) {
+            // the two K-major panels (256 rows x 16) and the pivot block must fit the scratch X
+            if (tm && a.mixed && L.A - L.X >= (size_t)(2 * 256 * 16 + 256) * sizeof(float)) {
+                if (!sweep_inverse_tmem(A, mp, X, tbase, misc, g)) {
+                    // the tensor cores did not complete: report the world, leave its state as it was
+                    if (tid == 0) {
+                        kamino_residual rep{};
+                        rep.iterations = 0;
+                        rep.status = KAMINO_WORLD_NOT_CONVERGED | KAMINO_WORLD_TIMEOUT;
+                        rep.num_rows = m;
+                        rep.num_contacts = nact;
+                        rep.r_primal = rep.r_dual = rep.r_compl = rep.r_ncp = INFINITY;
+                        a.res[w] = rep;
+                    }
+                    g.sync();
+                    return;
+                }
+                in_tmem = true;
+            }
+        }
+        if (!in_tmem) sweep_inverse<T, NB>(A, mp, X, a.mixed != 0, g);
+        if constexpr (sizeof(T) == 4) {
+            if (tm && !in_tmem) tmem_store_inverse(A, mp, tbase, g);
+        }
+        if (a.mixed && !tm) pack_bf16_tiles(A, mp, X, g);
+        body_row_lists(g, nb, m, rbody, bro, brow);
+
+        // ---- 8. Proximal-ADMM (Alg. 1).  The linear solve of every iteration is one step of
+        // iterative refinement from the previous x:  x^i = x^{i-1} - A^-1 (b + A x^{i-1}), with A x
+        // evaluated matrix-free from the rows (P J M^-1 J^T P x + (eta + rho) x) and A^-1 the swept
+        // inverse.  At a fixed point A x = -b holds to the accuracy of the matrix-free product, so the
+        // inverse's own rounding (which the nearly singular D~ would amplify) does not move the
+        // solution.  With refine64, once r_p and r_d fall below KAMINO_REFINE64_BELOW the refinement
+        // end game runs in FP64: the right-hand side b (from the FP64 v_f), the per-body velocities
+        // M^-1 J^T P x and the residual b + A x are formed in FP64, and the iterates x, y, z, y^, z^
+        // themselves are kept in FP64 (in shared memory that is dead during the loop), as in iterative
+        // refinement whose solution is accumulated in the higher precision: an FP32 iterate cannot hold
+        // the solution of these mechanisms closer than ~1e-4 in u+ (u+ is a small difference of large
+        // joint impulses through light bodies).  The correction S (b + A x) stays on the FP32 / BF16
+        // inverse.
+        //
+        // Unit u (a joint row, or the three rows of a contact) belongs to thread u mod group size for
+        // the whole solve: only its owner writes its x, b, y, z, y^, z^ (the residual rows read x and b
+        // row by row after a barrier), so an iteration has four barriers (after the per-body gather,
+        // after the residual rows, after the mat-vec, and the residual reduction, which also publishes
+        // x, P x and b).
+        const T eta = a.eta, rho = a.rho, irho = T(1) / a.rho;
+        double *bbd = reinterpret_cast<double *>(X + kWarps * mp);   // FP32 worlds only (make_layout)
+        double *gbd = bbd + mp;
+        __nv_bfloat16 *chi = reinterpret_cast<__nv_bfloat16 *>(X), *clo = chi + mp;   // mixed: split c
+        // the FP64 end game only matters below the FP32 residual floor, i.e. for tolerances under the
+        // switch level
+        const bool use64 = sizeof(T) == 4 && a.refine64 && a.tol < T(KAMINO_REFINE64_BELOW);
+        double *x64 = nullptr;
+        if (use64) x64 = fp64_iterates(smem, L, tm, a.mixed && !tm, mp, nb, X);
+        double *y64 = x64 + mp, *z64 = x64 + 2 * mp, *yh64 = x64 + 3 * mp, *zh64 = x64 + 4 * mp;
+        double *yn64 = x64 + 5 * mp, *zn64 = x64 + 6 * mp;
+        bool hp = false;     // b of the coming iteration is the FP64 one; set once, uniform over the group
+        bool hpv = false;    // the iterates live in the FP64 vectors (from the commit after hp is set)
+        bool x_in64 = false; // the last owner update wrote x to the FP64 vector
+        int LB = 8;          // lanes per body in the gather: a power of two with LB * nb <= group size
+        while (LB > 1 && LB * nb > nthr) LB >>= 1;
+        T acc_a = T(1), c_prev = T(INFINITY);
+        // b = v_f + Gamma(z^) - eta x - rho y^ - z^ and w = P x for the first iteration
+        for (int u = tid; u < nunits; u += nthr) {
+            if (u < nbil) {
+                bb[u] = T(vfd[u]) - eta * x[u] - rho * yh[u] - zh[u];
+                wv[u] = p[u] * x[u];
+            } else {
+                const int r0 = nbil + 3 * (u - nbil);
+                const T s = mut[u - nbil] * sqrt(zh[r0] * zh[r0] + zh[r0 + 1] * zh[r0 + 1]);
+                for (int t = 0; t < 3; ++t) {
+                    bb[r0 + t] = T(vfd[r0 + t]) + (t == 2 ? s : T(0)) - eta * x[r0 + t] - rho * yh[r0 + t] - zh[r0 + t];
+                    wv[r0 + t] = p[r0 + t] * x[r0 + t];
+                }
+            }
+        }
+        if (a.mixed && !tm) {
+            for (int r = m + tid; r < mp; r += nthr) {
+                chi[r] = __float2bfloat16(0.0f);
+                clo[r] = __float2bfloat16(0.0f);
+            }
+        }
+        g.sync();
+        for (it = 1; it <= a.iters; ++it) {
+            // [8a] per body: g_b = M_b^-1 sum over the body's rows r of J_rb^T (P x)_r; LB lanes per
+            // body take its rows round-robin, then a shuffle reduction
+            for (int base = 0; base < nb * LB; base += nthr) {
+                if (base + (tid & ~31) >= nb * LB) continue;          // the whole warp is past the bodies
+                const int t = base + tid, body = t / LB, sub = t - body * LB;
+                const bool on = t < nb * LB;
+                if (hp) {
+                    double f[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+                    if (on) {
+                        for (int e = bro[body] + sub; e < bro[body + 1]; e += LB) {
+                            const int code = brow[e], r = code >> 1;
+                            const double w = (double)p[r] * (x_in64 ? x64[r] : (double)x[r]);
+                            const T *J = rJ + 6 * code;                 // 12 r + 6 side
+    #pragma unroll
+                            for (int k = 0; k < 6; ++k) f[k] = fma((double)J[k], w, f[k]);
+                        }
+                    }
+                    for (int o = LB >> 1; o > 0; o >>= 1) {
+    #pragma unroll
+                        for (int k = 0; k < 6; ++k) f[k] += __shfl_xor_sync(0xffffffffu, f[k], o);
+                    }
+                    if (on && sub == 0) {
+                        const double mi = bminv[body];
+                        for (int k = 0; k < 3; ++k) gbd[6 * body + k] = mi * f[k];
+                        symvec3d(bIinv + 6 * body, f + 3, gbd + 6 * body + 3);
+                    }
+                } else {
+                    T f[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+                    if (on) {
+                        for (int e = bro[body] + sub; e < bro[body + 1]; e += LB) {
+                            const int code = brow[e];
+                            const T w = wv[code >> 1];
+                            const T *J = rJ + 6 * code;
+    #pragma unroll
+                            for (int k = 0; k < 6; ++k) f[k] = fma(J[k], w, f[k]);
+                        }
+                    }
+                    for (int o = LB >> 1; o > 0; o >>= 1) {
+    #pragma unroll
+                        for (int k = 0; k < 6; ++k) f[k] += __shfl_xor_sync(0xffffffffu, f[k], o);
+                    }
+                    if (on && sub == 0) {
+                        const T mi = bminv[body];
+                        for (int k = 0; k < 3; ++k) fb[6 * body + k] = mi * f[k];
+                        symvec3(bIinv + 6 * body, f + 3, fb + 6 * body + 3);
+                    }
+                }
+            }
+            g.sync();
+            // [8b] thread r: c_r = b_r + p_r J_r (g_A, g_B) + (eta + rho) x_r (b_r and x_r were written by
+            // the row's owner before the last barrier), stored as the BF16 hi / lo split (mixed, inverse
+            // in shared memory) or in bb (tensor-memory, FP32 and FP64 mat-vecs)
+            for (int r = tid; r < m; r += nthr) {
+                const int sa = rbody[2 * r], sb = rbody[2 * r + 1];
+                const T *J = rJ + 12 * r;
+                T c;
+                if (hp) {
+                    double acc = 0.0;
+                    if (sa >= 0) {
+    #pragma unroll
+                        for (int k = 0; k < 6; ++k) acc = fma((double)J[k], gbd[6 * sa + k], acc);
+                    }
+                    if (sb >= 0) {
+    #pragma unroll
+                        for (int k = 0; k < 6; ++k) acc = fma((double)J[6 + k], gbd[6 * sb + k], acc);
+                    }
+                    const double xr = x_in64 ? x64[r] : (double)x[r];
+                    c = T(bbd[r] + (double)p[r] * acc + ((double)shift + (double)p[r] * (double)p[r] * (double)rreg[r]) * xr);
+                } else {
+                    T acc = T(0);
+                    if (sa >= 0) {
+    #pragma unroll
+                        for (int k = 0; k < 6; ++k) acc = fma(J[k], fb[6 * sa + k], acc);
+                    }
+                    if (sb >= 0) {
+    #pragma unroll
+                        for (int k = 0; k < 6; ++k) acc = fma(J[6 + k], fb[6 * sb + k], acc);
+                    }
+                    c = bb[r] + p[r] * acc + (shift + p[r] * p[r] * rreg[r]) * x[r];
+                }
+                if (a.mixed && !tm) {
+                    const float v = (float)c;
+                    const __nv_bfloat16 h = __float2bfloat16(v);
+                    chi[r] = h;
+                    clo[r] = __float2bfloat16(v - __bfloat162float(h));
+                } else {
+                    bb[r] = c;
+                }
+            }
+            g.sync();
+            // [8c] correction: xn = S c with S = -A^-1, so x^i = x^{i-1} + xn (ends with a barrier)
+            bool done_c = false;
+            if constexpr (sizeof(T) == 4) {
+                if (tm) { tmem_matvec(tbase, mp, bb, xn, g); done_c = true; }
+            }
+            if (!done_c) {
+                if (a.mixed) apply_bf16_tiles(A, mp, chi, clo, xn, g);
+                else symv_packed(A, mp, bb, xn, X, g);
+            }
+            // [8d] owners: x^i, y^i = Pi_K(x^i - z^/rho), z^i = z^ - rho (x^i - y^i), residual terms; x and
+            // P x go to shared memory at once (the reduction's barrier publishes them for [8a])
+            T lrp = T(0), lrd = T(0), lrc = T(0), lc = T(0);
+            T xnT[S][3], ynT[S][3], znT[S][3];          // units tid + s * group size
+            if (hpv) {
+                // the new FP64 iterates wait for the commit in shared memory (x^i in x, y^i and z^i in
+                // the two spare vectors), not in registers across the reduction
+                double xnD[S][3], ynD[S][3], znD[S][3];
+                owner_update<double, T, S>(g, nunits, nfix, nbil, x64, xn, yh64, zh64, mut, mui, p, wv, eta, rho, irho, xnD, ynD,
+                                           znD, lrp, lrd, lrc, lc);
+                stash_rows<S>(g, nunits, nbil, ynD, yn64);
+                stash_rows<S>(g, nunits, nbil, znD, zn64);
+            } else {
+                owner_update<T, T, S>(g, nunits, nfix, nbil, x, xn, yh, zh, mut, mui, p, wv, eta, rho, irho, xnT, ynT, znT, lrp,
+                                      lrd, lrc, lc);
+            }
+            x_in64 = hpv;
+            group_reduce4(lrp, lrd, lrc, lc, red, it & 1, g);
+            rp = lrp; rd = lrd; rc = lrc;
+            converged = rp < a.tol && rd < a.tol && rc < a.tol;
+            hp = use64 && (hp || fmax(rp, rd) < T(KAMINO_REFINE64_BELOW));
+            // Nesterov with adaptive restart (uniform decision), then the owners commit y, z, y^, z^ and
+            // form the next iteration's b (in FP64 once hp is set)
+            T beta_n = T(0);
+            bool restart = false;
+            if (a.nesterov) {
+                if (lc < T(0.999) * c_prev) {
+                    const T an = T(0.5) * (T(1) + sqrt(T(1) + T(4) * acc_a * acc_a));
+                    beta_n = (acc_a - T(1)) / an;
+                    acc_a = an;
+                    c_prev = lc;
+                } else {
+                    restart = true;
+                    acc_a = T(1);
+                    c_prev = c_prev / T(0.999);
+                }
+            }
+            if (hpv) {
+                double xnD[S][3], ynD[S][3], znD[S][3];
+                unstash_rows<S>(g, nunits, nbil, x64, xnD);
+                unstash_rows<S>(g, nunits, nbil, yn64, ynD);
+                unstash_rows<S>(g, nunits, nbil, zn64, znD);
+                owner_commit<double, T, S>(g, nunits, nbil, y64, z64, yh64, zh64, vfd, mut, eta, rho, a.nesterov != 0,
+                                           restart, beta_n, xnD, ynD, znD, true, bb, bbd, nullptr, mp);
+            } else {
+                // the iterates move to the FP64 vectors at this commit once the end game has started
+                double *init = hp && x64 != nullptr ? x64 : nullptr;
+                owner_commit<T, T, S>(g, nunits, nbil, y, z, yh, zh, vfd, mut, eta, rho, a.nesterov != 0, restart,
+                                      beta_n, xnT, ynT, znT, hp, bb, bbd, init, mp);
+                hpv = init != nullptr;
+            }
+            if (converged) break;
+        }
+        if (it > a.iters) it = a.iters;
+        yfin = hpv ? y64 : nullptr;
+        fd = sizeof(T) == 8 ? reinterpret_cast<double *>(fb) : gbd;
     }
-    if (it > a.iters) it = a.iters;
     g.sync();
 
     // ---- 9. lambda = P y; u+ = u_free + M^-1 J^T lambda; integrate; cache; report.  Formed in
     // FP64 (once per step): u+ is a small difference of large joint impulses through light bodies,
     // and the pose update adds a small increment to the stored pose.
-    for (int r = tid; r < m; r += nthr) xn[r] = T((double)p[r] * (hpv ? y64[r] : (double)y[r]));
+    for (int r = tid; r < m; r += nthr) xn[r] = T((double)p[r] * (yfin ? yfin[r] : (double)y[r]));
     // J^T lambda per (body, component), one thread each, into FP64 scratch (the per-body FP64
     // velocities of the refinement for FP32 worlds, the per-body force words for FP64 worlds)
-    double *fd = sizeof(T) == 8 ? reinterpret_cast<double *>(fb) : gbd;
     for (int t = tid; t < 6 * nb; t += nthr) {
         const int i = t / 6, k = t - 6 * (t / 6);
         double f = 0.0;
         for (int e = bro[i]; e < bro[i + 1]; ++e) {
             const int code = brow[e], r = code >> 1;
-            const double yr = hpv ? y64[r] : (double)y[r];
+            const double yr = yfin ? yfin[r] : (double)y[r];
             f = fma((double)rJ[6 * code + k], (double)p[r] * yr, f);   // 12 r + 6 side + k
         }
         fd[t] = f;
@@ -1768,7 +2188,7 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
             if (sa >= 0) v = fma((double)rJ[12 * r + q], fd[6 * sa + q], v);
             v = fma((double)rJ[12 * r + 6 + q], fd[6 * sb + q], v);
         }
-        const double vs = (double)p[r] * v, ls = hpv ? y64[r] : (double)y[r];
+        const double vs = (double)p[r] * v, ls = yfin ? yfin[r] : (double)y[r];
         lncp = fmax(lncp, T(fabs(ls - fmax(ls - vs, 0.0))));
     }
     for (int k = tid; k < nact; k += nthr) {
@@ -1782,7 +2202,7 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
                 v = fma((double)rJ[12 * r + 6 + q], fd[6 * sb + q], v);
             }
             vs[t] = (double)p[r] * v;
-            ls[t] = hpv ? y64[r] : (double)y[r];
+            ls[t] = yfin ? yfin[r] : (double)y[r];
         }
         const double mu = (double)mut[k];
         const double s[3] = {ls[0] - vs[0], ls[1] - vs[1], ls[2] - (vs[2] + mu * sqrt(vs[0] * vs[0] + vs[1] * vs[1]))};
@@ -1877,14 +2297,24 @@ __global__ void __launch_bounds__(kThreads, 1) step_kernel(const StepArgs<T> a) 
     const Group g{(int)threadIdx.x, kThreads, 0};
     const bool tm = sizeof(T) == 4 && a.tmem;
     const uint32_t tbase = tm ? cta_tmem_alloc<T, NB>(a, smem) : 0u;
-    world_step<T, NB, S>(a, w, smem, g, tbase, tm);
+    world_step<T, NB, S, false>(a, w, smem, g, tbase, tm);
     if (tm) cta_tmem_free(tbase);
+}
+
+// The sparse formulation, one world per CTA: no tensor memory, and a working set small enough for
+// several CTAs per SM (hence the register bound of two resident CTAs).
+template <typename T, int S>
+__global__ void __launch_bounds__(kThreads, 2) step_kernel_cr(const StepArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int w = a.world_order ? a.world_order[blockIdx.x] : (int)blockIdx.x;
+    const Group g{(int)threadIdx.x, kThreads, 0};
+    world_step<T, 16, S, true>(a, w, smem, g, 0u, false);
 }
 
 // Persistent launch over a list of worlds: the CTA is split into groups of `group` threads, each
 // with its own slice of shared memory; every group pulls the next world from an atomic counter
 // until the list is exhausted (dynamic load balance across worlds whose iteration counts differ).
-template <typename T, int NB>
+template <typename T, int NB, bool CR>
 __global__ void __launch_bounds__(kThreads, 1) step_persistent(const StepArgs<T> a, PersistentArgs p) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int gi = threadIdx.x / p.group;
@@ -1893,7 +2323,7 @@ __global__ void __launch_bounds__(kThreads, 1) step_persistent(const StepArgs<T>
     unsigned char *slice = smem + (size_t)gi * p.slice_bytes;
     int *slot = (int *)(smem + (size_t)ngroups * p.slice_bytes) + gi;
     // tensor memory only when one group fills the CTA (a.tmem is set by the host for such buckets)
-    const bool tm = sizeof(T) == 4 && a.tmem && ngroups == 1;
+    const bool tm = !CR && sizeof(T) == 4 && a.tmem && ngroups == 1;
     const uint32_t tbase = tm ? cta_tmem_alloc<T, NB>(a, smem) : 0u;
     for (int round = 0; round < p.count; ++round) {   // bounded: at most one world per round
         if (g.tid == 0) *slot = atomicAdd(p.counter, 1);
@@ -1901,7 +2331,7 @@ __global__ void __launch_bounds__(kThreads, 1) step_persistent(const StepArgs<T>
         const int idx = *slot;
         g.sync();
         if (idx >= p.count) break;
-        world_step<T, NB, kSlots>(a, p.worlds[idx], slice, g, tbase, tm);
+        world_step<T, NB, kSlots, CR>(a, p.worlds[idx], slice, g, tbase, tm);
         g.sync();
     }
     if (tm) cta_tmem_free(tbase);
@@ -1912,7 +2342,9 @@ __global__ void __launch_bounds__(kThreads, 1) step_persistent(const StepArgs<T>
 template <typename T>
 cudaError_t prepare_step(int nb_panel, size_t smem) {
     const int b = (int)smem;
-    cudaError_t e;
+    cudaError_t e = cudaFuncSetAttribute(step_kernel_cr<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(step_kernel_cr<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (e != cudaSuccess) return e;
     if (nb_panel == 16) {
         e = cudaFuncSetAttribute(step_kernel<T, 16, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(step_kernel<T, 16, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
@@ -1927,7 +2359,10 @@ template <typename T>
 cudaError_t launch_step(const StepArgs<T> &args, int num_worlds, int nb_panel, size_t smem, cudaStream_t stream) {
     if (num_worlds <= 0) return cudaSuccess;
     const bool one = args.mp_max <= kThreads;     // units <= rows <= mp_max
-    if (nb_panel == 16) {
+    if (args.cr_iters > 0) {
+        if (one) step_kernel_cr<T, 1><<<num_worlds, kThreads, smem, stream>>>(args);
+        else step_kernel_cr<T, 2><<<num_worlds, kThreads, smem, stream>>>(args);
+    } else if (nb_panel == 16) {
         if (one) step_kernel<T, 16, 1><<<num_worlds, kThreads, smem, stream>>>(args);
         else step_kernel<T, 16, 2><<<num_worlds, kThreads, smem, stream>>>(args);
     } else {
@@ -1939,26 +2374,32 @@ cudaError_t launch_step(const StepArgs<T> &args, int num_worlds, int nb_panel, s
 
 template <typename T>
 cudaError_t prepare_persistent(int nb_panel, size_t smem) {
+    cudaError_t e = cudaFuncSetAttribute(step_persistent<T, 16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
     if (nb_panel == 16)
-        return cudaFuncSetAttribute(step_persistent<T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    return cudaFuncSetAttribute(step_persistent<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        return cudaFuncSetAttribute(step_persistent<T, 16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return cudaFuncSetAttribute(step_persistent<T, 8, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
 template <typename T>
-cudaError_t occupancy_persistent(int nb_panel, size_t smem, int *blocks_per_sm) {
+cudaError_t occupancy_persistent(int nb_panel, size_t smem, int cr, int *blocks_per_sm) {
+    if (cr) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, step_persistent<T, 16, true>, kThreads, smem);
     if (nb_panel == 16)
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, step_persistent<T, 16>, kThreads, smem);
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, step_persistent<T, 8>, kThreads, smem);
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, step_persistent<T, 16, false>, kThreads, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, step_persistent<T, 8, false>, kThreads, smem);
 }
 
 template <typename T>
 cudaError_t launch_persistent(const StepArgs<T> &args, const PersistentArgs &p, int nb_panel, int grid, size_t smem,
                               cudaStream_t stream) {
     if (p.count <= 0 || grid <= 0) return cudaSuccess;
-    if (nb_panel == 16)
-        step_persistent<T, 16><<<grid, kThreads, smem, stream>>>(args, p);
+    if (args.cr_iters > 0)
+        step_persistent<T, 16, true><<<grid, kThreads, smem, stream>>>(args, p);
+    else if (nb_panel == 16)
+        step_persistent<T, 16, false><<<grid, kThreads, smem, stream>>>(args, p);
     else
-        step_persistent<T, 8><<<grid, kThreads, smem, stream>>>(args, p);
+        step_persistent<T, 8, false><<<grid, kThreads, smem, stream>>>(args, p);
     return cudaGetLastError();
 }
 
@@ -1968,8 +2409,8 @@ template cudaError_t launch_step<float>(const StepArgs<float> &, int, int, size_
 template cudaError_t launch_step<double>(const StepArgs<double> &, int, int, size_t, cudaStream_t);
 template cudaError_t prepare_persistent<float>(int, size_t);
 template cudaError_t prepare_persistent<double>(int, size_t);
-template cudaError_t occupancy_persistent<float>(int, size_t, int *);
-template cudaError_t occupancy_persistent<double>(int, size_t, int *);
+template cudaError_t occupancy_persistent<float>(int, size_t, int, int *);
+template cudaError_t occupancy_persistent<double>(int, size_t, int, int *);
 template cudaError_t launch_persistent<float>(const StepArgs<float> &, const PersistentArgs &, int, int, size_t,
                                               cudaStream_t);
 template cudaError_t launch_persistent<double>(const StepArgs<double> &, const PersistentArgs &, int, int, size_t,

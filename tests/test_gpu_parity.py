@@ -36,10 +36,11 @@ def K():
     return kamino
 
 
-def gpu_step(K, ws, q, u, tau, dt, iters, tol, precision="fp32", rho=0.1, warm=0, cache=None, model=None):
-    """One GPU step from host state (q, u); returns (q+, u+, residual report, cache)."""
+def gpu_step(K, ws, q, u, tau, dt, iters, tol, precision="fp32", rho=0.1, warm=0, cache=None, model=None, **pkw):
+    """One GPU step from host state (q, u); returns (q+, u+, residual report, cache).  ``pkw``: further
+    solver parameters (``cr_iters``, ``integrator``)."""
     if model is None:
-        model = K.Model(ws, precision, K.make_params(rho=rho, warm_mode=warm))
+        model = K.Model(ws, precision, K.make_params(rho=rho, warm_mode=warm, **pkw))
     st = K.State(model)
     dtype = st.dtype
     st.body_q.copy_(torch.tensor(q.reshape(-1, 7), dtype=dtype))
@@ -67,9 +68,9 @@ def errors(q0, q_gpu, u_gpu, q_ref, u_ref, dt, precision="fp32"):
     return eu, eq
 
 
-def oracle_step(ws, q, u, tau, dt, rho=0.1, eps=1e-11, n_max=50000, warm="cold", cache=None):
+def oracle_step(ws, q, u, tau, dt, rho=0.1, eps=1e-11, n_max=50000, warm="cold", cache=None, **okw):
     st = T.WorldState(q=q.copy(), u=u.copy(), cache=cache or [None] * ws.num_worlds)
-    params = T.SolverParams(rho=rho, eps=eps, n_max=n_max, warm=warm)
+    params = T.SolverParams(rho=rho, eps=eps, n_max=n_max, warm=warm, **okw)
     return T.step(ws, st, tau, dt, params)
 
 
@@ -134,9 +135,16 @@ def _cache_offsets(ws, infos):
     return off
 
 
-def _ncp(info, u_plus, lam):
+def _ncp_parts(info, u_plus, lam):
+    """The oracle's audit of (lambda, u+): (contact and joint-limit blocks, bilateral range part),
+    with the world's drive-row regularisation and limit rows."""
     from oracle import audit as AU
-    return max(AU.ncp_residual(info.J, u_plus, info.v_star, lam, info.p, info.n_bilateral, info.mu))
+    return AU.ncp_residual(info.J, u_plus, info.v_star, lam, info.p, info.n_bilateral, info.mu, info.reg,
+                           info.unilateral)
+
+
+def _ncp(info, u_plus, lam):
+    return max(_ncp_parts(info, u_plus, lam))
 
 
 def _gpu_lambda(info, cache_w):
@@ -169,8 +177,10 @@ NCP_FACTOR = 10.0
 
 
 def _biped_parity(K, ws, q, u, tau, dt, precision, warm=0, warm_buf=None, require_oracle_converged=True,
-                  cache_gpu=None, cache_oracle=None):
-    model = K.Model(ws, precision, K.make_params(rho=0.1, warm_mode=warm))
+                  cache_gpu=None, cache_oracle=None, pkw=None, okw=None):
+    """``pkw`` / ``okw``: further solver parameters of the GPU / oracle side (sparse formulation,
+    integrator), the same method on both."""
+    model = K.Model(ws, precision, K.make_params(rho=0.1, warm_mode=warm, **(pkw or {})))
     st = K.State(model)
     st.body_q.copy_(torch.tensor(q.reshape(-1, 7), dtype=st.dtype))
     st.body_u.copy_(torch.tensor(u.reshape(-1, 6), dtype=st.dtype))
@@ -184,7 +194,7 @@ def _biped_parity(K, ws, q, u, tau, dt, precision, warm=0, warm_buf=None, requir
     qg, ug, rep = st.body_q.double().cpu().numpy(), st.body_u.double().cpu().numpy(), st.residuals()
     cache = st.cache.double().cpu().numpy()
     ref, infos = oracle_step(ws, q, u, tau, dt, eps=1e-11, warm="cold" if cache_oracle is None else "cached",
-                             cache=cache_oracle)
+                             cache=cache_oracle, **(okw or {}))
     check_report(rep, infos)
     if require_oracle_converged:
         assert all(i.converged for i in infos), [i.iterations for i in infos]
@@ -194,7 +204,8 @@ def _biped_parity(K, ws, q, u, tau, dt, precision, warm=0, warm_buf=None, requir
         bs = ws.bodies(w)
         eu, eq = errors(q[bs], qg[bs], ug[bs], ref.q[bs], ref.u[bs], dt, precision)
         lam_g = _gpu_lambda(info, cache[off[w]:off[w + 1]])
-        r_gpu = _ncp(info, ug[bs].reshape(-1), lam_g)
+        r_gpu_c, r_gpu_b = _ncp_parts(info, ug[bs].reshape(-1), lam_g)
+        r_gpu = max(r_gpu_c, r_gpu_b)
         r_orc = _ncp(info, info.u_plus, info.lam)
         r32 = _ncp32(info)
         rec = dict(world=w, err_u=float(eu), err_q=float(eq), gpu_iters=int(rep["iterations"][w]),
@@ -204,8 +215,9 @@ def _biped_parity(K, ws, q, u, tau, dt, precision, warm=0, warm_buf=None, requir
         # where the oracle converged (to 1e-11) the GPU must converge (to 1e-8); where the contact
         # set is inconsistent (reading 17) the oracle stops at its cap and the GPU may too
         assert rep["status"][w] == 0 if info.converged else rep["status"][w] & K.WORLD_NONFINITE == 0, rec
-        # the device's own residual is the same quantity (its scaling is the FP32 one)
-        assert abs(rec["ncp_gpu_device"] - r_gpu) <= 1e-6 + 0.1 * r_gpu, rec
+        rec["ncp_gpu_contact"], rec["ncp_gpu_bilateral"] = r_gpu_c, r_gpu_b
+        # the device's own residual is the audit's contact and limit part (its scaling is the FP32 one)
+        assert abs(rec["ncp_gpu_device"] - r_gpu_c) <= 1e-6 + 0.1 * r_gpu_c, rec
         if eu <= 1e-4 and eq <= 1e-4:
             matched += 1
             rec["class"] = "a"
@@ -430,9 +442,10 @@ def test_full_size_bipeds_sampled_parity(K):
         bs = ws.bodies(w)
         assert rep["num_rows"][w] == a.m
         lam_g = _gpu_lambda(a, cache[off[w]:off[w + 1]])
-        rg = _ncp(a, ug[bs].reshape(-1), lam_g)
+        rg_c, rg_b = _ncp_parts(a, ug[bs].reshape(-1), lam_g)
+        rg = max(rg_c, rg_b)
         rs = _ncp(a, a.u_plus, a.lam)
-        assert abs(float(rep["r_ncp"][w]) - rg) <= 1e-6 + 0.1 * rg, (w, float(rep["r_ncp"][w]), rg)
+        assert abs(float(rep["r_ncp"][w]) - rg_c) <= 1e-6 + 0.1 * rg_c, (w, float(rep["r_ncp"][w]), rg_c)
         scale = max(np.abs(b.u_plus).max(), G * dt)
         e_conv = float(np.abs(ug[bs].reshape(-1) - b.u_plus).max() / scale)
         lines.append((w, bool(conv[w]), int(rep["iterations"][w]), a.iterations, b.converged, rg, rs, e_conv))

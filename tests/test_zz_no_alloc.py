@@ -56,3 +56,28 @@ def test_static_scratch_refuses_oversized_batch(K):
     with pytest.raises(K.KaminoError) as err:
         net.predict_static(X)
     assert err.value.status == 7 and "static scratch" in str(err.value)
+
+
+def test_static_scratch_at_its_limit(K):
+    """The largest batch the refusal message names for a hidden-256 network fits the array (its
+    activations packed up to the array's end) and matches the allocating path; one row more is
+    refused."""
+    import re
+    ws = wg.make_biped(num_worlds=4, seed=6)
+    model = K.Model(ws, "mixed", K.make_params())
+    net = K.Mlp(model, np.arange(4), hidden=256, max_batch=8192, seed=2)
+    din = net.info.d_in
+    with pytest.raises(K.KaminoError) as err:
+        net.predict_static(torch.zeros((20000, din), dtype=torch.float32, device="cuda"))
+    rows = int(re.search(r"at most (\d+) rows", str(err.value)).group(1))
+    assert 1000 < rows < 8192
+    rng = np.random.default_rng(3)
+    X = torch.tensor(rng.standard_normal((rows + 1, din)), dtype=torch.float32, device="cuda")
+    for _ in range(2):                                         # two calls in a row at the limit
+        got = net.predict_static(X[:rows])
+        ref = net.predict(X[:rows])
+        torch.cuda.synchronize()
+        torch.testing.assert_close(got, ref, rtol=1e-6, atol=1e-6)
+    with pytest.raises(K.KaminoError) as err:
+        net.predict_static(X)
+    assert err.value.status == 7
