@@ -4,10 +4,11 @@
 Workload (one "step" = one kamino_step over the whole batch, the full hot path in one launch):
 4096 synthetic bipeds (31 bodies, 36 revolute joints, 6 loops, 16 foot-corner contact candidates
 on the plane), dt = 2 ms, Gaussian actuation sigma = 5 N m from the counter-based generator,
-Proximal-ADMM to tol 1e-5 with N_max = 1000 and rho = 0.1.  Four variants are timed: plain FP32
-from a cold start, and the mixed mode (TF32 tensor-core sweep, FP32 iteration; the FP64
-refinement stays off at tol 1e-5) from a cold start, from the impulse cache and from the learned
-warm start; the headline is the last.  The simulation really advances: K timed steps follow W warm-up steps from the standing pose.
+Proximal-ADMM to tol 1e-5 with N_max = 1000 and rho = 0.1.  Five variants are timed: plain FP32
+from a cold start, the mixed mode (TF32 tensor-core sweep, FP32 iteration; the FP64 refinement
+stays off at tol 1e-5) from a cold start, from the impulse cache and from the learned warm start,
+and the sparse formulation of Sec. 5.1 (matrix-free Delassus operator, --cr warm-started Conjugate
+Residual iterations per x-step, FP32, cold start); the headline is the learned warm start.  The simulation really advances: K timed steps follow W warm-up steps from the standing pose.
 
 Reported: ``value`` = world-steps/s with the state resident in HBM (CUDA events on the launching
 stream, L2 flushed between timed steps); ``e2e`` = the same through the C ABI with the actuation
@@ -32,7 +33,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "world-steps/s @4096 closed-loop bipeds, NCP residual<=1e-5; warm vs plain"
 UNIT = "world-steps/s"
-SM_COUNT, FP32_LANES = 152, 128
+FP32_LANES = 128                      # FP32 FMA lanes per SM (sm_100 / sm_103)
 
 
 def parse():
@@ -55,6 +56,10 @@ def parse():
     p.add_argument("--gen-steps", type=int, default=40, help="solver steps generating training pairs")
     p.add_argument("--train-steps", type=int, default=600, help="Adam steps of the warm-start network")
     p.add_argument("--graph", type=int, default=0, help="replay a captured CUDA graph per step")
+    p.add_argument("--ncp-stop", type=int, default=1, help="a world converges only once its natural-map NCP "
+                                                           "residual is below tol too (the metric's condition)")
+    p.add_argument("--cr", type=int, default=9, help="CR iterations per x-step of the timed sparse-formulation "
+                                                     "variant (Sec. 5.1); 0: not timed")
     return p.parse_args()
 
 
@@ -338,6 +343,7 @@ def run_gpu(args, rank, world):
     sptr = C.c_void_p(stream.cuda_stream)
     model_plain = K.Model(ws, "fp32", K.make_params(rho=args.rho))
     model = K.Model(ws, "mixed", K.make_params(rho=args.rho))
+    model_sparse = K.Model(ws, "fp32", K.make_params(rho=args.rho, cr_iters=args.cr)) if args.cr > 0 else None
     tune_report = None
     if args.workload == "hetero":
         # per-bucket (group size, panel) chosen by the autotuner on a scratch state (not timed)
@@ -394,9 +400,10 @@ def run_gpu(args, rank, world):
                         "loss_last": lasts if len(nets) > 1 else lasts[0], "seconds": time.perf_counter() - t0}
         del bufs, st_gen
 
-    def run_variant(name, warm_mode, learned=False, mdl=None, refine64=True):
+    def run_variant(name, warm_mode, learned=False, mdl=None, refine64=True, cr=0):
         mdl = mdl or model
-        mdl.set_params(K.make_params(rho=args.rho, warm_mode=warm_mode, refine64=refine64))
+        mdl.set_params(K.make_params(rho=args.rho, warm_mode=warm_mode, refine64=refine64, cr_iters=cr,
+                                     ncp_stop=args.ncp_stop))
         st = K.State(mdl, dev)
         graph = None
         if args.graph:
@@ -459,6 +466,9 @@ def run_gpu(args, rank, world):
     results["mixed_cached_warm"] = run_variant("mixed_cached_warm", K.WARM_CACHED)
     if nets:
         results["mixed_learned_warm"] = run_variant("mixed_learned_warm", K.WARM_EXTERNAL, learned=True)
+    if model_sparse is not None:
+        results[f"sparse_cr{args.cr}_fp32_cold"] = run_variant(f"sparse_cr{args.cr}_fp32_cold", K.WARM_COLD,
+                                                               mdl=model_sparse, refine64=False, cr=args.cr)
     clocks = sampler.stop()
     units = job_units(W, args.steps, world)
     variants = {}
@@ -474,7 +484,8 @@ def run_gpu(args, rank, world):
 
     # ---- end to end through the C ABI: pinned host actuation in, body state out, every step
     learned = head == "mixed_learned_warm"
-    model.set_params(K.make_params(rho=args.rho, warm_mode=K.WARM_EXTERNAL if learned else K.WARM_CACHED))
+    model.set_params(K.make_params(rho=args.rho, warm_mode=K.WARM_EXTERNAL if learned else K.WARM_CACHED,
+                                   ncp_stop=args.ncp_stop))
     B = int(ws.world_body_offset[-1])
     tau_pin = torch.tensor(tau_host).pin_memory()
     q_out = torch.empty((B, 7), dtype=torch.float32).pin_memory()
@@ -518,7 +529,8 @@ def run_gpu(args, rank, world):
     # launching stream, so the warm-start network's launches are not counted).
     peaks = measured_peaks()
     smax = clocks.get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
-    alu_peak = SM_COUNT * FP32_LANES * 2 * smax * 1e6 / 1e12       # FP32 FMA lanes x clock, TFLOP/s
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    alu_peak = sm_count * FP32_LANES * 2 * smax * 1e6 / 1e12       # FP32 FMA lanes x clock, TFLOP/s
     flops = float(algorithmic_flops(rows_h, its_h).sum()) / 1e12
     achieved = flops / (sum(ms_step_h) / 1e3)
     traffic = step_kernel_traffic(args.workload, W)
@@ -530,7 +542,9 @@ def run_gpu(args, rank, world):
         "warmup": args.warmup, "ms_per_step": 1e3 * t_head / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+tf32+bf16", "data": "synthetic",
         "config": {"workload": f"{desc} per GPU, dt={args.dt}, Gaussian actuation sigma=5, PADMM tol={args.tol}, "
-                               f"N_max={args.iters}, rho={args.rho}; headline: {head}",
+                               f"N_max={args.iters}, rho={args.rho}"
+                               f"{', converged = ADMM residuals and NCP residual below tol' if args.ncp_stop else ''}"
+                               f"; headline: {head}",
                    "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}"},
         "variants": variants,
         "warm_over_plain": v_head / variants["plain_fp32_cold"]["value"],
@@ -542,7 +556,7 @@ def run_gpu(args, rank, world):
                      "frac": achieved / alu_peak, "traffic": traffic,
                      "kernel": "kamino step kernel (one launch per step)",
                      "launch_ms": sum(ms_step_h) / len(ms_step_h),
-                     "peak_note": f"derived FP32 FMA peak: {SM_COUNT} SMs x {FP32_LANES} lanes x 2 x {smax:.0f} MHz",
+                     "peak_note": f"derived FP32 FMA peak: {sm_count} SMs x {FP32_LANES} lanes x 2 x {smax:.0f} MHz",
                      "hbm": hbm_roofline(traffic, sum(ms_step_h) / len(ms_step_h), peaks)},
         "clocks": clocks,
     }

@@ -97,6 +97,11 @@ typedef struct {
                         * per step, Sec. 5.1).  k >= 1: sparse formulation (Sec. 5.1): D applied
                         * matrix-free from the rows, each PADMM x-step k Conjugate Residual
                         * iterations warm-started at the previous x (the paper uses 9)         */
+    int32_t ncp_stop;  /* 0: a world has converged when Sec. 4.1's residuals r_p, r_d, r_c are below
+                        * tol (the paper's test).  1: in addition, the natural-map NCP residual of
+                        * the iterate's (lambda, u+) on the contact and joint-limit blocks
+                        * (kamino_residual.r_ncp) must be below tol; it is evaluated only in the
+                        * iterations whose residuals pass, and the world iterates on otherwise. */
 } kamino_solver_params;
 
 /* Time stepping (Sec. 3).  EULER: semi-implicit Euler, everything evaluated at the start-of-step
@@ -348,6 +353,29 @@ kamino_status kamino_mlp_get_params(kamino_mlp_t mlp, float *host, int64_t count
 kamino_status kamino_mlp_set_params(kamino_mlp_t mlp, const float *host, int64_t count);
 kamino_status kamino_mlp_get_normalization(kamino_mlp_t mlp, float *host);
 kamino_status kamino_mlp_set_normalization(kamino_mlp_t mlp, const float *host);
+
+/* ---- Forward kinematics for resets (Sec. 6.3: the Gauss-Newton solver that resets mechanisms with
+ * kinematic loops to poses consistent with given joint coordinates).  For every world, from the poses
+ * in KAMINO_BUF_BODY_Q, Gauss-Newton on F(q) = [f(q); d_j(q) - target_j over the selected joints]:
+ * f are the errors of the joint rows (the rows the step uses, whose J is the rate of f) and d_j the
+ * joint coordinate of the drives (hinge angle, slide; revolute differences wrapped into (-pi, pi]).
+ * Each iteration takes the minimum-norm least-squares step over the twists of the bodies that are
+ * not held, delta = -J^T P (P J J^T P + 1e-10 I)^-1 P F with P scaling the rows to unit norm
+ * (factorised in FP64 on chip), and moves the poses along it (r += delta_v, q = exp(delta_w) q).
+ * It stops when max|F| < tol or after max_iters iterations.
+ *   joint_target_dev  [J] double, device: target coordinate of every joint (read where selected)
+ *   joint_select_dev  [J] int32, device: nonzero = the joint's coordinate is prescribed (revolute and
+ *                     prismatic joints; others are ignored).  NULL = the actuated joints
+ *   body_fixed_dev    [B] int32, device: nonzero = the body keeps its pose.  NULL = none
+ * Writes the poses (in the state's precision; twists are not changed) and, per world, into
+ * KAMINO_BUF_RESIDUAL: iterations, status (KAMINO_WORLD_NOT_CONVERGED when max|F| >= tol, e.g. a
+ * target the mechanism cannot reach), num_rows = rows of F, r_primal = max|F| (m, rad) at the
+ * returned poses; the other fields 0.  Asynchronous on `stream`; the arrays must stay valid until
+ * the work completes.  KAMINO_E_INVALID_ARG: NULL state or targets, max_iters < 1, tol < 0 or not
+ * finite.  KAMINO_E_UNSUPPORTED: a world's FP64 system does not fit in one SM's shared memory
+ * (about 216 rows of F). */
+kamino_status kamino_fk(kamino_state_t state, const double *joint_target_dev, const int32_t *joint_select_dev,
+                        const int32_t *body_fixed_dev, int32_t max_iters, double tol, void *stream);
 
 /* ---- Allocation-free inference of the warm-start network (the paper has no counterpart).
  * kamino_mlp_predict with its activations in a file-scope device array of

@@ -80,6 +80,7 @@ struct kamino_model_s {
     int precision = KAMINO_FP32;
     int W = 0, B = 0, J = 0, C = 0;
     int nb_max = 0, nj_max = 0, nc_max = 0, mp_max = 0, max_rows = 0, n_act_max = 0, cache_len = 0;
+    int fk_rows_max = 0;                   // joint rows + revolute / prismatic joints of a world (FK)
     int nb_panel = 16;
     size_t smem = 0;
     bool prepared = false;
@@ -324,6 +325,7 @@ StepArgs<T> make_args(kamino_state_s *st, double dt, int iters, double tol, cons
     a.midpoint = m->params.integrator == KAMINO_INTEGRATOR_MIDPOINT ? 1 : 0;
     a.refine64 = m->params.refine64 ? 1 : 0;
     a.cr_iters = m->params.cr_iters;
+    a.ncp_stop = m->params.ncp_stop ? 1 : 0;
     // the inverse may live in tensor memory when a world's shared memory keeps a second CTA off the SM
     // (the 512-column allocation then never waits for another CTA); the sparse formulation has none
     a.tmem = (sizeof(T) == 4 && a.cr_iters == 0 && m->mp_max <= 256 && m->smem > kMaxSmem / 2) ? 1 : 0;
@@ -397,6 +399,31 @@ kamino_status do_step(kamino_state_s *st, double dt, int iters, double tol, cons
         if ((e = cudaEventRecord(m->join[b], m->side[b])) != cudaSuccess) return cuda_fail(e, "join");
         if ((e = cudaStreamWaitEvent(stream, m->join[b], 0)) != cudaSuccess) return cuda_fail(e, "join wait");
     }
+    return KAMINO_OK;
+}
+
+// Forward kinematics for resets over every world of the state (kamino_fk).
+template <typename T>
+kamino_status do_fk(kamino_state_s *st, const double *target, const int32_t *select, const int32_t *fixed,
+                           int iters, double tol, cudaStream_t stream) {
+    kamino_model_s *m = st->model;
+    const FkLayout L = make_fk_layout(m->nb_max, m->fk_rows_max);
+    if (L.total > kMaxSmem)
+        return fail(KAMINO_E_UNSUPPORTED, "forward kinematics of a world with %d rows needs %zu bytes of shared memory "
+                    "(at most %zu)", m->fk_rows_max, L.total, kMaxSmem);
+    FkArgs<T> a{};
+    a.m = view<T>(m);
+    a.body_q = (T *)st->ptr(st->off_q);
+    a.res = (kamino_residual *)st->ptr(st->off_res);
+    a.target = target;
+    a.select = select;
+    a.fixed = fixed;
+    a.iters = iters;
+    a.tol = tol;
+    a.nb_max = m->nb_max;
+    a.m_max = m->fk_rows_max;
+    cudaError_t e = launch_fk<T>(a, m->W, L.total, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "forward kinematics launch");
     return KAMINO_OK;
 }
 
@@ -597,7 +624,7 @@ kamino_status kamino_model_create(const kamino_model_desc *d, kamino_model_t *ou
         const int j0 = d->world_joint_offset[w], nj = d->world_joint_offset[w + 1] - j0;
         const int c0 = d->world_contact_offset[w], nc = d->world_contact_offset[w + 1] - c0;
         const int nact = d->world_num_actuators[w];
-        int row = 0;
+        int row = 0, ncoord = 0;
         for (int j = j0; j < j0 + nj; ++j) {
             const int t = d->joint_type[j], par = d->joint_parent[j], ch = d->joint_child[j], act = d->joint_actuator[j];
             if (rows_of(t) < 0) { delete m; return fail(KAMINO_E_TOPOLOGY, "joint %d: unknown type %d", j, t); }
@@ -632,7 +659,9 @@ kamino_status kamino_model_create(const kamino_model_desc *d, kamino_model_t *ou
             jm[j] = make_int4(t, par, ch, act);
             jrow[j] = row;
             row += rows_of(t);
+            ncoord += (t == KAMINO_JOINT_REVOLUTE || t == KAMINO_JOINT_PRISMATIC) ? 1 : 0;
         }
+        m->fk_rows_max = std::max(m->fk_rows_max, row + ncoord);
         // joint-space dynamics: a drive row per driven joint after the joint rows, then one limit
         // candidate per finite bound
         int nlc = 0;
@@ -904,6 +933,16 @@ kamino_status kamino_step(kamino_state_t s, double dt, int32_t iters, double tol
     if (!(tol >= 0.0)) return fail(KAMINO_E_INVALID_ARG, "tol must be >= 0");
     return s->model->precision == KAMINO_FP64 ? do_step<double>(s, dt, iters, tol, tau_dev, (cudaStream_t)stream)
                                               : do_step<float>(s, dt, iters, tol, tau_dev, (cudaStream_t)stream);
+}
+
+kamino_status kamino_fk(kamino_state_t s, const double *joint_target_dev, const int32_t *joint_select_dev,
+                        const int32_t *body_fixed_dev, int32_t max_iters, double tol, void *stream) {
+    if (!s || !joint_target_dev) return fail(KAMINO_E_INVALID_ARG, "state and joint_target_dev must not be NULL");
+    if (max_iters < 1) return fail(KAMINO_E_INVALID_ARG, "max_iters must be >= 1 (got %d)", max_iters);
+    if (!(tol >= 0.0) || !std::isfinite(tol)) return fail(KAMINO_E_INVALID_ARG, "tol must be finite and >= 0");
+    return s->model->precision == KAMINO_FP64
+               ? do_fk<double>(s, joint_target_dev, joint_select_dev, body_fixed_dev, max_iters, tol, (cudaStream_t)stream)
+               : do_fk<float>(s, joint_target_dev, joint_select_dev, body_fixed_dev, max_iters, tol, (cudaStream_t)stream);
 }
 
 kamino_status kamino_residuals(kamino_state_t s, kamino_residual *out_dev, void *stream) {

@@ -61,6 +61,7 @@ struct StepArgs {
     int midpoint;              // 1: Moreau-Jean midpoint scheme (KAMINO_INTEGRATOR_MIDPOINT)
     int refine64;              // 1: FP64 right-hand side and refinement residual near convergence
     int cr_iters;              // 0: dense formulation; k >= 1: sparse formulation, k CR iterations per x-step
+    int ncp_stop;              // 1: converged also requires the natural-map NCP residual below tol
     int tmem;                  // 1: keep the swept inverse in tensor memory (FP32, whole-CTA groups, mp <= 256)
     // shared-memory layout bounds (maxima over the launched worlds)
     int nb_max, nj_max, nc_max, mp_max, nl_max;
@@ -165,6 +166,49 @@ __host__ __device__ inline Layout make_layout(int nb, int nj, int nc, int mp, in
     return L;
 }
 
+// Forward kinematics for resets (fk_kernel): one world per CTA, everything in FP64 on chip.
+template <typename T>
+struct FkArgs {
+    ModelView<T> m;
+    T *body_q;                 // [B*7] poses, read and written
+    kamino_residual *res;      // [W]
+    const double *target;      // [J] joint-coordinate targets
+    const int *select;         // [J] nonzero: prescribed coordinate; nullptr: the actuated joints
+    const int *fixed;          // [B] nonzero: the body keeps its pose; nullptr: none
+    int iters;
+    double tol;
+    int nb_max, m_max;         // bodies and rows of F (joint rows + coordinate rows) of the largest world
+};
+
+struct FkLayout {
+    size_t bq, bq0, bRd, rbody, rJ, F, y, p, dinv, bro, brow, dl, A, red, misc, total;
+};
+
+// Shared memory of the FK kernel: the packed lower FP64 matrix of m_max rows dominates.
+__host__ __device__ inline FkLayout make_fk_layout(int nb, int m) {
+    FkLayout L{};
+    size_t o = 0;
+    auto take = [&](size_t &field, size_t bytes) { field = o; o = align_up(o + bytes, 16); };
+    const int mm = m > 0 ? m : 1;
+    take(L.bq, nb * 7 * sizeof(double));
+    take(L.bq0, nb * 7 * sizeof(double));    // the poses before the last step
+    take(L.bRd, nb * 9 * sizeof(double));
+    take(L.rbody, mm * 2 * sizeof(int));
+    take(L.rJ, mm * 12 * sizeof(double));
+    take(L.F, mm * sizeof(double));
+    take(L.y, mm * sizeof(double));
+    take(L.p, mm * sizeof(double));
+    take(L.dinv, mm * sizeof(double));
+    take(L.bro, (nb + 1) * sizeof(int));
+    take(L.brow, 2 * mm * sizeof(int));
+    take(L.dl, nb * 6 * sizeof(double));
+    take(L.A, (size_t)mm * (mm + 1) / 2 * sizeof(double));
+    take(L.red, 2 * 4 * kWarps * sizeof(double));
+    take(L.misc, 16 * sizeof(int));
+    L.total = o;
+    return L;
+}
+
 // Launchers (kamino_step.cu).  Return the launch error (cudaSuccess on success).
 template <typename T>
 cudaError_t launch_step(const StepArgs<T> &args, int num_worlds, int nb_panel, size_t smem,
@@ -178,5 +222,7 @@ template <typename T>
 cudaError_t prepare_persistent(int nb_panel, size_t smem);
 template <typename T>
 cudaError_t occupancy_persistent(int nb_panel, size_t smem, int cr, int *blocks_per_sm);
+template <typename T>
+cudaError_t launch_fk(const FkArgs<T> &args, int num_worlds, size_t smem, cudaStream_t stream);
 
 }  // namespace kamino

@@ -1125,6 +1125,101 @@ __device__ __forceinline__ void owner_commit(const Group &g, int nunits, int nbi
     }
 }
 
+// ----------------------------------------------------------------------------- NCP residual
+// What the natural-map residual of a world needs (shared memory, built by phases 1-5).
+template <typename T>
+struct NcpWorld {
+    int nb, nfix, nbil, nact;
+    const int *bro, *brow, *rbody;
+    const T *rJ, *p, *mut, *bminv, *bIinv, *bufree;
+    const double *rvs;
+};
+
+// u+ = u_free + M^-1 J^T P y in FP64 into fd (6 per body); y from `yfin` (FP64) when set, else `y`.
+// Thread per (body, component) for J^T lambda, then thread per body; ends without a barrier.
+// Returns true when a velocity this thread formed is not finite.
+template <typename T>
+__device__ bool ncp_velocities(const NcpWorld<T> &c, const Group &g, const double *yfin, const T *y, double *fd) {
+    const int tid = g.tid, nthr = g.size;
+    for (int t = tid; t < 6 * c.nb; t += nthr) {
+        const int i = t / 6, k = t - 6 * (t / 6);
+        double f = 0.0;
+        for (int e = c.bro[i]; e < c.bro[i + 1]; ++e) {
+            const int code = c.brow[e], r = code >> 1;
+            const double yr = yfin ? yfin[r] : (double)y[r];
+            f = fma((double)c.rJ[6 * code + k], (double)c.p[r] * yr, f);   // 12 r + 6 side + k
+        }
+        fd[t] = f;
+    }
+    g.sync();
+    // each thread reads and writes only its body's words
+    bool bad = false;
+    for (int i = tid; i < c.nb; i += nthr) {
+        double f[6];
+        for (int k = 0; k < 6; ++k) f[k] = fd[6 * i + k];
+        double dw[3];
+        symvec3d(c.bIinv + 6 * i, f + 3, dw);
+        for (int k = 0; k < 3; ++k) {
+            fd[6 * i + k] = (double)c.bufree[6 * i + k] + (double)c.bminv[i] * f[k];
+            fd[6 * i + 3 + k] = (double)c.bufree[6 * i + 3 + k] + dw[k];
+        }
+        for (int k = 0; k < 6; ++k) bad |= !isfinite(fd[6 * i + k]);
+    }
+    return bad;
+}
+
+// Natural-map NCP residual of (lambda, u+) on the complementarity blocks (Eq. 3), scaled units, with
+// u+ in fd (after a barrier that follows ncp_velocities): with v~ = P (J u+ + v*) and
+// lambda~ = P^-1 lambda = y, max_k || lambda~_k - Pi_K(lambda~_k - (v~_k + Gamma(v~_k))) ||_inf over the
+// contacts; a joint-limit row (0 <= lambda ⟂ g >= 0) adds |lambda~ - max(lambda~ - v~, 0)|.  Every
+// thread gets the group's value (one reduction, buffer `phase`).
+template <typename T>
+__device__ T ncp_natural_map(const NcpWorld<T> &c, const Group &g, const double *yfin, const T *y, const double *fd,
+                             T *red, int phase) {
+    const int tid = g.tid, nthr = g.size;
+    T lncp = T(0);
+    for (int r = c.nfix + tid; r < c.nbil; r += nthr) {
+        const int sa = c.rbody[2 * r], sb = c.rbody[2 * r + 1];
+        double v = c.rvs[r];
+        for (int q = 0; q < 6; ++q) {
+            if (sa >= 0) v = fma((double)c.rJ[12 * r + q], fd[6 * sa + q], v);
+            v = fma((double)c.rJ[12 * r + 6 + q], fd[6 * sb + q], v);
+        }
+        const double vs = (double)c.p[r] * v, ls = yfin ? yfin[r] : (double)y[r];
+        lncp = fmax(lncp, T(fabs(ls - fmax(ls - vs, 0.0))));
+    }
+    for (int k = tid; k < c.nact; k += nthr) {
+        const int r0 = c.nbil + 3 * k;
+        double vs[3], ls[3];
+        for (int t = 0; t < 3; ++t) {
+            const int r = r0 + t, sa = c.rbody[2 * r], sb = c.rbody[2 * r + 1];
+            double v = c.rvs[r];
+            for (int q = 0; q < 6; ++q) {
+                if (sa >= 0) v = fma((double)c.rJ[12 * r + q], fd[6 * sa + q], v);
+                v = fma((double)c.rJ[12 * r + 6 + q], fd[6 * sb + q], v);
+            }
+            vs[t] = (double)c.p[r] * v;
+            ls[t] = yfin ? yfin[r] : (double)y[r];
+        }
+        const double mu = (double)c.mut[k];
+        const double s[3] = {ls[0] - vs[0], ls[1] - vs[1], ls[2] - (vs[2] + mu * sqrt(vs[0] * vs[0] + vs[1] * vs[1]))};
+        const double tn = sqrt(s[0] * s[0] + s[1] * s[1]);
+        double pr[3];
+        if (tn <= mu * s[2]) {
+            pr[0] = s[0]; pr[1] = s[1]; pr[2] = s[2];
+        } else if (mu * tn <= -s[2]) {
+            pr[0] = pr[1] = pr[2] = 0.0;
+        } else {
+            const double nn = (mu * tn + s[2]) / (1.0 + mu * mu);
+            pr[0] = mu * nn * s[0] / tn; pr[1] = mu * nn * s[1] / tn; pr[2] = nn;
+        }
+        for (int t = 0; t < 3; ++t) lncp = fmax(lncp, T(fabs(ls[t] - pr[t])));
+    }
+    T d0 = T(0), d1 = T(0), d2 = T(0);
+    group_reduce4(lncp, d0, d1, d2, red, phase, g);
+    return lncp;
+}
+
 // Per-body row lists for the matrix-free products: bro[i] .. bro[i+1] index brow, whose entries are
 // 2 r + side for every row r that has body i on that side (side 0: A, side 1: B).
 __device__ void body_row_lists(const Group &g, int nb, int m, const int *rbody, int *bro, int *brow) {
@@ -1180,6 +1275,9 @@ struct CrWorld {
     const T *rJ, *p, *rreg, *bminv, *bIinv, *mut, *mui;
     const double *vfd;
     T shift, eta, rho;
+    int ncp_stop;              // converged also requires the natural-map residual below tol
+    NcpWorld<T> ncw;
+    double *yout, *fd;         // FP64 y for the NCP check and phase 9; FP64 scratch (6 nb)
 };
 
 // The PADMM iterates of this thread's units, in registers: slot [s][t] is row t of unit
@@ -1444,6 +1542,112 @@ __device__ bool cr_padmm(const CrWorld<T> &c, const Group &g, CrIterates<V, S> &
     }
     it = iters;
     return false;
+}
+
+// ncp_stop in the sparse formulation: the natural-map residual of the iterates' (lambda, u+) on the
+// complementarity blocks, with y published to c.yout (FP64); true when it is below tol.
+template <typename V, typename T, int S>
+__device__ bool cr_ncp_ok(const CrWorld<T> &c, const Group &g, const CrIterates<V, S> &I, V *red, int &ph,
+                          double tol) {
+#pragma unroll
+    for (int sl = 0; sl < S; ++sl) {
+        const int u = g.tid + sl * g.size;
+        if (u >= c.nunits) continue;
+        int r0, cnt;
+        unit_rows(u, c.nbil, r0, cnt);
+        for (int t = 0; t < cnt; ++t) c.yout[r0 + t] = (double)I.y[sl][t];
+    }
+    g.sync();
+    ncp_velocities(c.ncw, g, c.yout, static_cast<const T *>(nullptr), c.fd);
+    g.sync();
+    return (double)ncp_natural_map(c.ncw, g, c.yout, static_cast<const T *>(nullptr), c.fd,
+                                   reinterpret_cast<T *>(red), ph++ & 1) < tol;
+}
+
+// ncp_stop at tolerances of 1e-6 and above: the natural-map residual of ncp_natural_map evaluated in
+// the iteration's own precision with the loop's machinery instead of FP64 (whose rate on this part
+// makes the FP64 check cost more than an iteration): the owners publish w = P y, LB lanes per body
+// gather M^-1 J^T w into fb, and the owners of the limit rows and contacts form
+// v~ = v~_f + P J (M^-1 J^T P y) on their rows and the natural map.  Two barriers and one reduction;
+// y from y64 when set.  The caller compares with a margin below tol for the FP32 rounding of v~.
+template <typename T, int S>
+__device__ T ncp_check_fast(const Group &g, int nunits, int nfix, int nbil, int nb, int LB, const int *bro,
+                            const int *brow, const int *rbody, const T *rJ, const T *p, const T *mut,
+                            const T *bminv, const T *bIinv, const double *vfd, const T *y, const double *y64,
+                            T *w, T *fb, T *red, int phase) {
+    const int tid = g.tid, nthr = g.size;
+#pragma unroll
+    for (int sl = 0; sl < S; ++sl) {
+        const int u = tid + sl * nthr;
+        if (u >= nunits) continue;
+        int r0, cnt;
+        unit_rows(u, nbil, r0, cnt);
+        for (int t = 0; t < cnt; ++t) w[r0 + t] = p[r0 + t] * (y64 ? T(y64[r0 + t]) : y[r0 + t]);
+    }
+    g.sync();
+    for (int base = 0; base < nb * LB; base += nthr) {
+        if (base + (tid & ~31) >= nb * LB) continue;
+        const int t = base + tid, body = t / LB, sub = t - body * LB;
+        const bool on = t < nb * LB;
+        T f[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+        if (on) {
+            for (int e = bro[body] + sub; e < bro[body + 1]; e += LB) {
+                const int code = brow[e];
+                const T wr = w[code >> 1];
+                const T *J = rJ + 6 * code;
+#pragma unroll
+                for (int k = 0; k < 6; ++k) f[k] = fma(J[k], wr, f[k]);
+            }
+        }
+        for (int o = LB >> 1; o > 0; o >>= 1) {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) f[k] += __shfl_xor_sync(0xffffffffu, f[k], o);
+        }
+        if (on && sub == 0) {
+            const T mi = bminv[body];
+            for (int k = 0; k < 3; ++k) fb[6 * body + k] = mi * f[k];
+            symvec3(bIinv + 6 * body, f + 3, fb + 6 * body + 3);
+        }
+    }
+    g.sync();
+    T lncp = T(0);
+#pragma unroll
+    for (int sl = 0; sl < S; ++sl) {
+        const int u = tid + sl * nthr;
+        if (u >= nunits || u < nfix) continue;
+        int r0, cnt;
+        unit_rows(u, nbil, r0, cnt);
+        T vs[3], ls[3];
+        for (int t = 0; t < cnt; ++t) {
+            const int r = r0 + t, sa = rbody[2 * r], sb = rbody[2 * r + 1];
+            const T *J = rJ + 12 * r;
+            T acc = T(0);
+            if (sa >= 0) for (int k = 0; k < 6; ++k) acc = fma(J[k], fb[6 * sa + k], acc);
+            if (sb >= 0) for (int k = 0; k < 6; ++k) acc = fma(J[6 + k], fb[6 * sb + k], acc);
+            vs[t] = T(vfd[r]) + p[r] * acc;
+            ls[t] = y64 ? T(y64[r]) : y[r];
+        }
+        if (cnt == 1) {                       // joint-limit row: 0 <= lambda ⟂ v >= 0
+            lncp = fmax(lncp, fabs(ls[0] - fmax(ls[0] - vs[0], T(0))));
+            continue;
+        }
+        const T mu = mut[u - nbil];
+        const T sv[3] = {ls[0] - vs[0], ls[1] - vs[1], ls[2] - (vs[2] + mu * sqrt(vs[0] * vs[0] + vs[1] * vs[1]))};
+        const T tn = sqrt(sv[0] * sv[0] + sv[1] * sv[1]);
+        T pr[3];
+        if (tn <= mu * sv[2]) {
+            pr[0] = sv[0]; pr[1] = sv[1]; pr[2] = sv[2];
+        } else if (mu * tn <= -sv[2]) {
+            pr[0] = pr[1] = pr[2] = T(0);
+        } else {
+            const T nn = (mu * tn + sv[2]) / (T(1) + mu * mu);
+            pr[0] = mu * nn * sv[0] / tn; pr[1] = mu * nn * sv[1] / tn; pr[2] = nn;
+        }
+        for (int t = 0; t < 3; ++t) lncp = fmax(lncp, fabs(ls[t] - pr[t]));
+    }
+    T d0 = T(0), d1 = T(0), d2 = T(0);
+    group_reduce4(lncp, d0, d1, d2, red, phase, g);
+    return lncp;
 }
 
 // ----------------------------------------------------------------------------- the step kernel
@@ -1714,6 +1918,7 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
         mut[k] = M.world_mu[w] * p[rt + 2] / p[rt];
         mui[k] = T(1) / (T(1) + mut[k] * mut[k]);
     }
+    const NcpWorld<T> ncw{nb, nfix, nbil, nact, bro, brow, rbody, rJ, p, mut, bminv, bIinv, bufree, rvs};
     double *yfin = nullptr;   // the final y in FP64 when the iterates ended in FP64 (or the sparse formulation)
     double *fd = nullptr;     // FP64 scratch of 6 nb words for phase 9
     T rp = T(INFINITY), rd = T(INFINITY), rc = T(INFINITY);
@@ -1726,12 +1931,12 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
         body_row_lists(g, nb, m, rbody, bro, brow);
         int LB = 8;               // lanes per body in the gather: a power of two with LB * nb <= group size
         while (LB > 1 && LB * nb > nthr) LB >>= 1;
-        const CrWorld<T> cw{nunits, nfix, nbil, nb, LB, bro, brow, rbody, rJ, p, rreg, bminv, bIinv, mut, mui,
-                            vfd, T(a.eta + a.rho), a.eta, a.rho};
         // the assembly scratch X is dead: the final y (FP64), then w and g, both sized for FP64
         double *y64c = reinterpret_cast<double *>(X);
         double *wbuf = y64c + a.mp_max;
         double *gbuf = wbuf + a.mp_max;
+        const CrWorld<T> cw{nunits, nfix, nbil, nb, LB, bro, brow, rbody, rJ, p, rreg, bminv, bIinv, mut, mui,
+                            vfd, T(a.eta + a.rho), a.eta, a.rho, a.ncp_stop, ncw, y64c, gbuf};
         // ---- 6'. warm start in the owners' registers: x0 = y0 = P^-1 lambda0, z0 = v0 + Gamma(v0),
         // v0 = A x0 - (eta + rho) x0 + v~_f
         CrIterates<T, S> I;
@@ -1787,9 +1992,16 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
         double rpd = INFINITY, rdd = INFINITY, rcd = INFINITY;
         it = 1;
         const bool use64 = sizeof(T) == 4 && a.refine64 && a.tol < T(KAMINO_REFINE64_BELOW);
-        const bool sw = cr_padmm<T, T, S>(cw, g, I, reinterpret_cast<T *>(wbuf), reinterpret_cast<T *>(gbuf),
-                                          reinterpret_cast<T *>(red), ph, it, a.iters, a.cr_iters, (double)a.tol,
-                                          a.nesterov != 0, mom, rpd, rdd, rcd, converged, use64);
+        bool sw = false;
+        for (;;) {   // the iterations, then (ncp_stop) the natural-map check, resumed if it fails
+            sw = cr_padmm<T, T, S>(cw, g, I, reinterpret_cast<T *>(wbuf), reinterpret_cast<T *>(gbuf),
+                                   reinterpret_cast<T *>(red), ph, it, a.iters, a.cr_iters, (double)a.tol,
+                                   a.nesterov != 0, mom, rpd, rdd, rcd, converged, use64);
+            if (sw || !(converged && a.ncp_stop)) break;
+            converged = cr_ncp_ok<T, T, S>(cw, g, I, reinterpret_cast<T *>(red), ph, (double)a.tol);
+            if (converged || it >= a.iters) break;
+            ++it;
+        }
         bool done = false;
         if constexpr (sizeof(T) == 4) {
             if (sw) {
@@ -1803,8 +2015,15 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
                     }
                 cr_rhs<double, T, S>(cw, g, D);                      // from the FP64 v_f
                 cr_apply<double, T, S>(cw, g, D.x, D.Ax, wbuf, gbuf);
-                cr_padmm<double, T, S>(cw, g, D, wbuf, gbuf, reinterpret_cast<double *>(red), ph, it, a.iters,
-                                       a.cr_iters, (double)a.tol, a.nesterov != 0, mom, rpd, rdd, rcd, converged, false);
+                for (;;) {
+                    cr_padmm<double, T, S>(cw, g, D, wbuf, gbuf, reinterpret_cast<double *>(red), ph, it, a.iters,
+                                           a.cr_iters, (double)a.tol, a.nesterov != 0, mom, rpd, rdd, rcd, converged,
+                                           false);
+                    if (!(converged && a.ncp_stop)) break;
+                    converged = cr_ncp_ok<double, T, S>(cw, g, D, reinterpret_cast<double *>(red), ph, (double)a.tol);
+                    if (converged || it >= a.iters) break;
+                    ++it;
+                }
 #pragma unroll
                 for (int sl = 0; sl < S; ++sl) {
                     const int u = tid + sl * nthr;
@@ -1985,7 +2204,12 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
             }
         }
         g.sync();
-        for (it = 1; it <= a.iters; ++it) {
+        // The iterations run until Sec. 4.1's test passes; with ncp_stop the natural-map check follows
+        // outside the loop (kept out of the loop body, which it would otherwise make slower) and the
+        // iterations resume if it fails.
+        it = 1;
+        for (;;) {
+        for (; it <= a.iters; ++it) {
             // [8a] per body: g_b = M_b^-1 sum over the body's rows r of J_rb^T (P x)_r; LB lanes per
             // body take its rows round-robin, then a shuffle reduction
             for (int base = 0; base < nb * LB; base += nthr) {
@@ -2138,6 +2362,26 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
             }
             if (converged) break;
         }
+        if (!(converged && a.ncp_stop)) break;
+        if (a.tol >= T(1e-6)) {
+            // ncp_stop: the natural-map residual of the committed (lambda, u+) on the complementarity
+            // blocks must be below tol too; in the iteration's precision, with a margin of 20 % for
+            // its rounding of v~ (~1e-6 here), so that phase 9's FP64 report stays below tol
+            g.sync();
+            converged = ncp_check_fast<T, S>(g, nunits, nfix, nbil, nb, LB, bro, brow, rbody, rJ, p, mut, bminv,
+                                             bIinv, vfd, y, hpv ? y64 : nullptr, xn, fb, red, (it + 1) & 1) <
+                        T(0.8) * a.tol;
+        } else {
+            // tighter tolerances: in FP64 (the scratch of the refinement end game is free here)
+            double *fdl = sizeof(T) == 8 ? reinterpret_cast<double *>(fb) : gbd;
+            g.sync();
+            ncp_velocities(ncw, g, hpv ? y64 : nullptr, y, fdl);
+            g.sync();
+            converged = ncp_natural_map(ncw, g, hpv ? y64 : nullptr, y, fdl, red, (it + 1) & 1) < a.tol;
+        }
+        if (converged) break;
+        ++it;
+        }
         if (it > a.iters) it = a.iters;
         yfin = hpv ? y64 : nullptr;
         fd = sizeof(T) == 8 ? reinterpret_cast<double *>(fb) : gbd;
@@ -2148,80 +2392,12 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
     // FP64 (once per step): u+ is a small difference of large joint impulses through light bodies,
     // and the pose update adds a small increment to the stored pose.
     for (int r = tid; r < m; r += nthr) xn[r] = T((double)p[r] * (yfin ? yfin[r] : (double)y[r]));
-    // J^T lambda per (body, component), one thread each, into FP64 scratch (the per-body FP64
-    // velocities of the refinement for FP32 worlds, the per-body force words for FP64 worlds)
-    for (int t = tid; t < 6 * nb; t += nthr) {
-        const int i = t / 6, k = t - 6 * (t / 6);
-        double f = 0.0;
-        for (int e = bro[i]; e < bro[i + 1]; ++e) {
-            const int code = brow[e], r = code >> 1;
-            const double yr = yfin ? yfin[r] : (double)y[r];
-            f = fma((double)rJ[6 * code + k], (double)p[r] * yr, f);   // 12 r + 6 side + k
-        }
-        fd[t] = f;
-    }
-    g.sync();
-    // u+ per body (over J^T lambda in fd: each thread reads and writes only its body's words)
-    bool bad = false;
-    for (int i = tid; i < nb; i += nthr) {
-        double f[6];
-        for (int k = 0; k < 6; ++k) f[k] = fd[6 * i + k];
-        double dw[3];
-        symvec3d(bIinv + 6 * i, f + 3, dw);
-        for (int k = 0; k < 3; ++k) {
-            fd[6 * i + k] = (double)bufree[6 * i + k] + (double)bminv[i] * f[k];
-            fd[6 * i + 3 + k] = (double)bufree[6 * i + 3 + k] + dw[k];
-        }
-        for (int k = 0; k < 6; ++k) bad |= !isfinite(fd[6 * i + k]);
-    }
-    if (bad) atomicOr(misc + 1, 1);
+    // u+ into FP64 scratch (the per-body FP64 velocities of the refinement for FP32 worlds, the
+    // per-body force words for FP64 worlds), then the natural-map NCP residual of (lambda, u+)
+    if (ncp_velocities(ncw, g, yfin, y, fd)) atomicOr(misc + 1, 1);
     g.sync();
     const bool world_bad = (misc[1] & 1) != 0;
-    // natural-map NCP residual of (lambda, u+) on the contact blocks (Eq. 3), scaled units: with
-    // v~ = P (J u+ + v*) and lambda~ = P^-1 lambda, max_k || lambda~_k - Pi_K(lambda~_k - (v~_k + Gamma(v~_k))) ||_inf;
-    // a joint-limit row (0 <= lambda ⟂ g >= 0) adds |lambda~ - max(lambda~ - v~, 0)|
-    T lncp = T(0);
-    for (int r = nfix + tid; r < nbil; r += nthr) {
-        const int sa = rbody[2 * r], sb = rbody[2 * r + 1];
-        double v = rvs[r];
-        for (int q = 0; q < 6; ++q) {
-            if (sa >= 0) v = fma((double)rJ[12 * r + q], fd[6 * sa + q], v);
-            v = fma((double)rJ[12 * r + 6 + q], fd[6 * sb + q], v);
-        }
-        const double vs = (double)p[r] * v, ls = yfin ? yfin[r] : (double)y[r];
-        lncp = fmax(lncp, T(fabs(ls - fmax(ls - vs, 0.0))));
-    }
-    for (int k = tid; k < nact; k += nthr) {
-        const int r0 = nbil + 3 * k;
-        double vs[3], ls[3];
-        for (int t = 0; t < 3; ++t) {
-            const int r = r0 + t, sa = rbody[2 * r], sb = rbody[2 * r + 1];
-            double v = rvs[r];
-            for (int q = 0; q < 6; ++q) {
-                if (sa >= 0) v = fma((double)rJ[12 * r + q], fd[6 * sa + q], v);
-                v = fma((double)rJ[12 * r + 6 + q], fd[6 * sb + q], v);
-            }
-            vs[t] = (double)p[r] * v;
-            ls[t] = yfin ? yfin[r] : (double)y[r];
-        }
-        const double mu = (double)mut[k];
-        const double s[3] = {ls[0] - vs[0], ls[1] - vs[1], ls[2] - (vs[2] + mu * sqrt(vs[0] * vs[0] + vs[1] * vs[1]))};
-        const double tn = sqrt(s[0] * s[0] + s[1] * s[1]);
-        double pr[3];
-        if (tn <= mu * s[2]) {
-            pr[0] = s[0]; pr[1] = s[1]; pr[2] = s[2];
-        } else if (mu * tn <= -s[2]) {
-            pr[0] = pr[1] = pr[2] = 0.0;
-        } else {
-            const double nn = (mu * tn + s[2]) / (1.0 + mu * mu);
-            pr[0] = mu * nn * s[0] / tn; pr[1] = mu * nn * s[1] / tn; pr[2] = nn;
-        }
-        for (int t = 0; t < 3; ++t) lncp = fmax(lncp, T(fabs(ls[t] - pr[t])));
-    }
-    {
-        T d0 = T(0), d1 = T(0), d2 = T(0);
-        group_reduce4(lncp, d0, d1, d2, red, (it + 1) & 1, g);
-    }
+    const T lncp = ncp_natural_map(ncw, g, yfin, y, fd, red, (it + 1) & 1);
     // poses and twists (a non-finite world keeps its state and cache; its report says so)
     for (int i = tid; i < nb && !world_bad; i += nthr) {
         // semi-implicit Euler: q+ = q (+) dt u+; Moreau-Jean: q+ = q_m (+) (dt/2) u+ (Sec. 3)
@@ -2337,6 +2513,213 @@ __global__ void __launch_bounds__(kThreads, 1) step_persistent(const StepArgs<T>
     if (tm) cta_tmem_free(tbase);
 }
 
+// ----------------------------------------------------------------------------- forward kinematics
+// Gauss-Newton forward kinematics for resets (Sec. 6.3): poses consistent with the joint constraints
+// and prescribed joint coordinates.  F(q) = [f(q); d_j(q) - target_j], f the errors of the joint
+// rows (the dynamics' own rows, whose J is the rate of f), d_j the joint coordinate (hinge angle,
+// wrapped into (-pi, pi], or slide).  Each iteration takes the minimum-norm least-squares step over
+// the twists of the bodies that are not held, delta = -J^T P (P J J^T P + mu I)^-1 P F (P the row
+// scaling to unit norm, mu = 1e-10: the loops make rows redundant and a partial selection leaves
+// directions free), factorised as L D L^T in FP64, and moves the poses along it as the integrator
+// does (r += delta_v, q = exp(delta_w) q).  One CTA per world; every quantity FP64 on chip.
+
+__device__ __forceinline__ int joint_row_count(int type) {
+    switch (type) {
+        case KAMINO_JOINT_REVOLUTE: return 5;
+        case KAMINO_JOINT_PRISMATIC: return 5;
+        case KAMINO_JOINT_UNIVERSAL: return 4;
+        case KAMINO_JOINT_SPHERICAL: return 3;
+        case KAMINO_JOINT_FIXED: return 6;
+        default: return 0;
+    }
+}
+
+template <typename T>
+__device__ void fk_world(const FkArgs<T> &a, int w, unsigned char *smem, const Group &g) {
+    constexpr double kMu = 1e-10;
+    const int tid = g.tid, lane = g.lane(), warp = g.warp(), nthr = g.size, nwarps = g.warps();
+    const ModelView<T> &M = a.m;
+    const int4 wa = M.world_a[w], wb = M.world_b[w];
+    const int b0 = wa.x, j0 = wa.y, nb = wb.x, nj = wb.y;
+    const FkLayout L = make_fk_layout(a.nb_max, a.m_max);
+    double *bq = (double *)(smem + L.bq), *bq0 = (double *)(smem + L.bq0), *bRd = (double *)(smem + L.bRd);
+    double *rJ = (double *)(smem + L.rJ);
+    double *F = (double *)(smem + L.F), *y = (double *)(smem + L.y), *p = (double *)(smem + L.p);
+    double *dinv = (double *)(smem + L.dinv), *dl = (double *)(smem + L.dl), *A = (double *)(smem + L.A);
+    double *red = (double *)(smem + L.red);
+    int *rbody = (int *)(smem + L.rbody), *bro = (int *)(smem + L.bro), *brow = (int *)(smem + L.brow);
+    int *misc = (int *)(smem + L.misc);
+    const int njr = nj > 0 ? M.joint_row[j0 + nj - 1] + joint_row_count(M.joint_meta[j0 + nj - 1].x) : 0;
+    for (int i = tid; i < nb; i += nthr) {
+        const T *gq = a.body_q + 7 * (size_t)(b0 + i);
+        double q[7];
+        for (int k = 0; k < 7; ++k) q[k] = (double)gq[k];
+        const double qn = 1.0 / sqrt(q[3] * q[3] + q[4] * q[4] + q[5] * q[5] + q[6] * q[6]);
+        for (int k = 0; k < 7; ++k) bq[7 * i + k] = k < 3 ? q[k] : q[k] * qn;
+    }
+    g.sync();
+    int it = 0, m = njr;
+    double res = INFINITY;
+    for (it = 0;; ++it) {
+        for (int i = tid; i < nb; i += nthr) quat_rot(bq + 7 * i + 3, bRd + 9 * i);
+        g.sync();
+        // joint rows (kbias 1: the row's value is f itself), then the selected coordinate rows
+        for (int j = tid; j < nj; j += nthr) {
+            const int4 meta = M.joint_meta[j0 + j];
+            double wr[12];
+            joint_rows<double>(meta.x, meta.y, meta.z, M.joint_frames + 14 * (size_t)(j0 + j), bq, bRd,
+                               M.joint_row[j0 + j], 1.0, rbody, rJ, F, false, 0.0, wr);
+        }
+        if (warp == nwarps - 1) {
+            int count = 0;
+            for (int jb = 0; jb < nj; jb += 32) {
+                const int j = jb + lane;
+                bool sel = false;
+                int4 meta = make_int4(0, 0, 0, -1);
+                if (j < nj) {
+                    meta = M.joint_meta[j0 + j];
+                    const bool coord = meta.x == KAMINO_JOINT_REVOLUTE || meta.x == KAMINO_JOINT_PRISMATIC;
+                    sel = coord && (a.select ? a.select[j0 + j] != 0 : meta.w >= 0);
+                }
+                const unsigned mask = __ballot_sync(0xffffffffu, sel);
+                const int rank = count + __popc(mask & ((1u << lane) - 1u));
+                if (sel) {
+                    double d, Ja[6], Jb[6];
+                    joint_coordinate(meta.x, meta.y, meta.z, M.joint_frames + 14 * (size_t)(j0 + j), bq, bRd, &d, Ja, Jb);
+                    double diff = d - a.target[j0 + j];
+                    if (meta.x == KAMINO_JOINT_REVOLUTE)
+                        diff -= 2.0 * 3.141592653589793 * floor((diff + 3.141592653589793) / (2.0 * 3.141592653589793));
+                    put_row(rbody, rJ, F, njr + rank, meta.y, meta.z, Ja, Jb, diff);
+                }
+                count += __popc(mask);
+            }
+            if (lane == 0) misc[0] = count;
+        }
+        g.sync();
+        m = njr + misc[0];
+        // held bodies are not unknowns: their blocks leave the rows
+        for (int r = tid; r < m; r += nthr)
+            for (int s = 0; s < 2; ++s) {
+                const int b = rbody[2 * r + s];
+                if (b >= 0 && a.fixed != nullptr && a.fixed[b0 + b] != 0) rbody[2 * r + s] = -1;
+            }
+        double lres = 0.0;
+        for (int r = tid; r < m; r += nthr) lres = fmax(lres, fabs(F[r]));
+        {
+            double d0 = 0.0, d1 = 0.0, d2 = 0.0;
+            group_reduce4(lres, d0, d1, d2, red, it & 1, g);
+        }
+        if (!isfinite(lres)) {
+            // the last step diverged (a target out of reach near a singular configuration): keep
+            // the poses it started from, whose residual is `res`
+            for (int e = tid; e < 7 * nb; e += nthr) bq[e] = bq0[e];
+            g.sync();
+            break;
+        }
+        res = lres;
+        if (res < a.tol || it >= a.iters) break;
+        // row scaling to unit norm over the unknown blocks
+        for (int r = tid; r < m; r += nthr) {
+            double s = 0.0;
+            for (int side = 0; side < 2; ++side)
+                if (rbody[2 * r + side] >= 0)
+                    for (int k = 0; k < 6; ++k) s += rJ[12 * r + 6 * side + k] * rJ[12 * r + 6 * side + k];
+            p[r] = s > 0.0 ? 1.0 / sqrt(s) : 1.0;
+        }
+        g.sync();
+        body_row_lists(g, nb, m, rbody, bro, brow);
+        // P J J^T P + mu I, packed lower (warp per column, block-sparse over shared bodies)
+        for (int j = warp; j < m; j += nwarps) {
+            double *col = A + col_start(j, m) - j;
+            const int ja = rbody[2 * j], jb = rbody[2 * j + 1];
+            const double *Jj = rJ + 12 * j;
+            for (int i = j + lane; i < m; i += 32) {
+                const int ia = rbody[2 * i], ib = rbody[2 * i + 1];
+                const double *Ji = rJ + 12 * i;
+                double s = 0.0;
+                if (ia >= 0 && ia == ja) for (int k = 0; k < 6; ++k) s += Ji[k] * Jj[k];
+                if (ia >= 0 && ia == jb) for (int k = 0; k < 6; ++k) s += Ji[k] * Jj[6 + k];
+                if (ib >= 0 && ib == ja) for (int k = 0; k < 6; ++k) s += Ji[6 + k] * Jj[k];
+                if (ib >= 0 && ib == jb) for (int k = 0; k < 6; ++k) s += Ji[6 + k] * Jj[6 + k];
+                col[i] = p[i] * p[j] * s + (i == j ? kMu : 0.0);
+            }
+        }
+        g.sync();
+        // L D L^T in place, right-looking (A(i, k) holds l_ik d_k): one barrier per column
+        for (int k = 0; k < m; ++k) {
+            const double dk = A[pidx(k, k, m)];
+            const double idk = 1.0 / dk;
+            for (int j = k + 1 + warp; j < m; j += nwarps) {
+                const double ljk = A[pidx(j, k, m)] * idk;
+                double *col = A + col_start(j, m) - j;
+                const double *ck = A + col_start(k, m) - k;
+                for (int i = j + lane; i < m; i += 32) col[i] -= ck[i] * ljk;
+            }
+            if (tid == 0) dinv[k] = idk;
+            g.sync();
+        }
+        // y = -(L D L^T)^-1 P F: forward and backward substitution in one warp
+        if (warp == 0) {
+            for (int r = lane; r < m; r += 32) y[r] = -p[r] * F[r];
+            __syncwarp();
+            for (int k = 0; k < m; ++k) {
+                const double zk = y[k], idk = dinv[k];
+                const double *ck = A + col_start(k, m) - k;
+                for (int i = k + 1 + lane; i < m; i += 32) y[i] -= ck[i] * idk * zk;
+                __syncwarp();
+            }
+            for (int r = lane; r < m; r += 32) y[r] *= dinv[r];
+            __syncwarp();
+            for (int k = m - 1; k > 0; --k) {
+                const double yk = y[k];
+                for (int i = lane; i < k; i += 32) y[i] -= A[pidx(k, i, m)] * dinv[i] * yk;
+                __syncwarp();
+            }
+        }
+        g.sync();
+        // delta = J^T P y per (body, component), then the poses move along it
+        for (int t = tid; t < 6 * nb; t += nthr) {
+            const int i = t / 6, k = t - 6 * (t / 6);
+            double f = 0.0;
+            for (int e = bro[i]; e < bro[i + 1]; ++e) {
+                const int code = brow[e], r = code >> 1;
+                f = fma(rJ[6 * code + k], p[r] * y[r], f);
+            }
+            dl[t] = f;
+        }
+        g.sync();
+        for (int i = tid; i < nb; i += nthr) {
+            double qn[7];
+            pose_advance(bq + 7 * i, dl + 6 * i, dl + 6 * i + 3, 1.0, qn);
+            for (int k = 0; k < 7; ++k) {
+                bq0[7 * i + k] = bq[7 * i + k];
+                bq[7 * i + k] = qn[k];
+            }
+        }
+        g.sync();
+    }
+    const bool ok = res < a.tol;
+    for (int i = tid; i < nb; i += nthr) {
+        T *gq = a.body_q + 7 * (size_t)(b0 + i);
+        for (int k = 0; k < 7; ++k) gq[k] = T(bq[7 * i + k]);
+    }
+    if (tid == 0) {
+        kamino_residual rep{};
+        rep.iterations = it;
+        rep.status = ok ? 0 : KAMINO_WORLD_NOT_CONVERGED;
+        rep.num_rows = m;
+        rep.r_primal = (float)res;
+        a.res[w] = rep;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads, 1) fk_kernel(const FkArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const Group g{(int)threadIdx.x, kThreads, 0};
+    fk_world<T>(a, (int)blockIdx.x, smem, g);
+}
+
 }  // namespace
 
 template <typename T>
@@ -2403,6 +2786,17 @@ cudaError_t launch_persistent(const StepArgs<T> &args, const PersistentArgs &p, 
     return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_fk(const FkArgs<T> &args, int num_worlds, size_t smem, cudaStream_t stream) {
+    if (num_worlds <= 0) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(fk_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    fk_kernel<T><<<num_worlds, kThreads, smem, stream>>>(args);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_fk<float>(const FkArgs<float> &, int, size_t, cudaStream_t);
+template cudaError_t launch_fk<double>(const FkArgs<double> &, int, size_t, cudaStream_t);
 template cudaError_t prepare_step<float>(int, size_t);
 template cudaError_t prepare_step<double>(int, size_t);
 template cudaError_t launch_step<float>(const StepArgs<float> &, int, int, size_t, cudaStream_t);

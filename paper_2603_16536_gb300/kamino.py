@@ -33,16 +33,16 @@ class KaminoError(RuntimeError):
 class SolverParams(C.Structure):
     _fields_ = [("eta", C.c_double), ("rho", C.c_double), ("beta", C.c_double), ("margin", C.c_double),
                 ("nesterov", C.c_int32), ("precond", C.c_int32), ("warm_mode", C.c_int32), ("refine64", C.c_int32),
-                ("integrator", C.c_int32), ("cr_iters", C.c_int32)]
+                ("integrator", C.c_int32), ("cr_iters", C.c_int32), ("ncp_stop", C.c_int32)]
 
 
 INTEGRATOR_EULER, INTEGRATOR_MIDPOINT = 0, 1
 
 
 def make_params(eta=1e-6, rho=0.1, beta=0.2, margin=0.005, nesterov=True, precond=True, warm_mode=WARM_COLD,
-                refine64=True, integrator=INTEGRATOR_EULER, cr_iters=0):
+                refine64=True, integrator=INTEGRATOR_EULER, cr_iters=0, ncp_stop=False):
     return SolverParams(eta, rho, beta, margin, int(nesterov), int(precond), int(warm_mode), int(refine64),
-                        int(integrator), int(cr_iters))
+                        int(integrator), int(cr_iters), int(ncp_stop))
 
 
 _P = C.c_void_p
@@ -117,6 +117,7 @@ def load_library(path: str | None = None):
         "kamino_state_download": ([vp, i32, vp, i64, vp], i32),
         "kamino_step": ([vp, dbl, i32, dbl, vp, vp], i32),
         "kamino_residuals": ([vp, vp, vp], i32),
+        "kamino_fk": ([vp, vp, vp, vp, i32, dbl, vp], i32),
         "kamino_last_error": ([], C.c_char_p),
         "kamino_plan_get": ([vp, C.POINTER(BucketInfo), i32, C.POINTER(i32), C.POINTER(i32)], i32),
         "kamino_plan_set_mode": ([vp, i32], i32),
@@ -311,6 +312,20 @@ class State:
         tptr = _tau_ptr(tau, self.dtype, self._tau_len)
         _check(load_library().kamino_step(self.handle, float(dt), int(iters), float(tol), tptr,
                                           C.c_void_p(stream.cuda_stream)))
+
+    def fk(self, targets, select=None, fixed=None, max_iters: int = 50, tol: float = 1e-12, stream=None):
+        """Gauss-Newton forward kinematics for resets (kamino_fk): ``targets`` device float64 [J] joint
+        coordinates, ``select`` device int32 [J] (None: the actuated joints), ``fixed`` device int32
+        [B] bodies that keep their poses (None: none).  Poses are updated in place; the per-world
+        report (iterations, status, max |F| in r_primal) is in residuals()."""
+        import torch
+        stream = stream or torch.cuda.current_stream()
+        nj, nb = len(self.model.ws.joint_type), int(self.model.ws.world_body_offset[-1])
+        tp = _dev(targets, torch.float64, "targets", min_numel=nj)
+        sp = None if select is None else _dev(select, torch.int32, "select", min_numel=nj)
+        fp = None if fixed is None else _dev(fixed, torch.int32, "fixed", min_numel=nb)
+        _check(load_library().kamino_fk(self.handle, tp, sp, fp, int(max_iters), float(tol),
+                                        C.c_void_p(stream.cuda_stream)))
 
     def autotune(self, dt: float, iters: int, tol: float, tau=None, stream=None):
         """Time every feasible per-bucket configuration on this state's worlds (state unchanged)."""

@@ -1,6 +1,7 @@
 """CPU-side checks of the C-ABI library: it loads, exports every function include/kamino.h declares,
 and rejects bad world descriptions on the host before touching the GPU."""
 import ctypes as C
+import os
 
 import numpy as np
 import pytest
@@ -25,13 +26,34 @@ def test_library_exports_every_declared_function(lib):
     assert not missing, missing
 
 
-def test_struct_layout_matches_header():
-    """The ctypes mirror has the size the C compiler gives (checked through a layout probe on the
-    field offsets that the header implies: 8-byte aligned pointers after two int32s)."""
-    assert C.sizeof(K.SolverParams) == 56
+def test_struct_layout_matches_header(tmp_path):
+    """The ctypes mirror has the sizes and offsets the C compiler gives the header's structs (a probe
+    compiled from include/kamino.h as plain C99)."""
+    import shutil
+    import subprocess
     assert K.ModelDesc.world_body_offset.offset == 8
     assert K.ModelDesc.gravity.offset == 8 + 15 * 8
-    assert C.sizeof(K.ModelInfo) == 40
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    probe = tmp_path / "probe.c"
+    probe.write_text("""#include <stdio.h>
+#include <stddef.h>
+#include "kamino.h"
+int main(void) {
+    printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(kamino_solver_params), sizeof(kamino_model_desc),
+           offsetof(kamino_model_desc, params), offsetof(kamino_model_desc, joint_drive),
+           offsetof(kamino_model_desc, joint_limit), sizeof(kamino_model_info), sizeof(kamino_residual));
+    return 0;
+}
+""")
+    exe = tmp_path / "probe"
+    include = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run([cc, "-std=c99", "-I" + include, str(probe), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    assert got == [C.sizeof(K.SolverParams), C.sizeof(K.ModelDesc), K.ModelDesc.params.offset,
+                   K.ModelDesc.joint_drive.offset, K.ModelDesc.joint_limit.offset, C.sizeof(K.ModelInfo),
+                   K.RESIDUAL_DTYPE.itemsize]
 
 
 def _create(ws, **override):
