@@ -58,6 +58,8 @@ def parse():
     p.add_argument("--graph", type=int, default=0, help="replay a captured CUDA graph per step")
     p.add_argument("--ncp-stop", type=int, default=1, help="a world converges only once its natural-map NCP "
                                                            "residual is below tol too (the metric's condition)")
+    p.add_argument("--stall-window", type=int, default=64,
+                   help="with --ncp-stop: the stall exit of worlds whose dual residual sits on its floor (0: off)")
     p.add_argument("--cr", type=int, default=9, help="CR iterations per x-step of the timed sparse-formulation "
                                                      "variant (Sec. 5.1); 0: not timed")
     return p.parse_args()
@@ -236,7 +238,7 @@ def ncp_report(ncp, status, its, tol, n_max, rate):
     capped = (status & 1) != 0
     out = {"ncp_le_tol_fraction": float(ok.mean()), "ncp_qualified_value": float(rate * ok.mean()),
            "ncp_median": float(np.median(ncp)), "ncp_p99": float(np.quantile(ncp, 0.99)),
-           "capped_fraction": float(capped.mean()),
+           "capped_fraction": float(capped.mean()), "stalled_fraction": float(np.mean((status & 8) != 0)),
            "capped_iteration_share": float(its[capped].sum() / max(its.sum(), 1))}
     if capped.any():
         c = ncp[capped]
@@ -400,10 +402,47 @@ def run_gpu(args, rank, world):
                         "loss_last": lasts if len(nets) > 1 else lasts[0], "seconds": time.perf_counter() - t0}
         del bufs, st_gen
 
+    def learned_vs_cold():
+        """The learned warm start against the cold start on identical states (not timed): the bipeds
+        after the warm-up steps, one step each way to the benchmark's tolerance; iterations to tol and
+        the relative velocity difference |u_learned - u_cold|inf / max(|u_cold|inf, g dt) per world."""
+        model.set_params(K.make_params(rho=args.rho, ncp_stop=args.ncp_stop, stall_window=args.stall_window))
+        st0 = K.State(model, dev)
+        for k in range(args.warmup):
+            st0.step(args.dt, args.iters, args.tol, tau_dev[k], stream)
+        q0, u0, c0 = st0.body_q.clone(), st0.body_u.clone(), st0.cache.clone()
+        out = {}
+        for name, mode in (("cold", K.WARM_COLD), ("learned", K.WARM_EXTERNAL)):
+            model.set_params(K.make_params(rho=args.rho, warm_mode=mode, ncp_stop=args.ncp_stop,
+                                           stall_window=args.stall_window))
+            st1 = K.State(model, dev)
+            st1.body_q.copy_(q0); st1.body_u.copy_(u0); st1.cache.copy_(c0)
+            if mode == K.WARM_EXTERNAL:
+                for net in nets:
+                    net.warm_start(st1, tau_dev[args.warmup], stream)
+            st1.step(args.dt, args.iters, args.tol, tau_dev[args.warmup], stream)
+            torch.cuda.synchronize()
+            rep = st1.residuals()
+            out[name] = (st1.body_u.double().cpu().numpy(), rep)
+        uc, ul = out["cold"][0], out["learned"][0]
+        err = []
+        for w in range(W):
+            b = slice(int(ws.world_body_offset[w]), int(ws.world_body_offset[w + 1]))
+            err.append(np.abs(ul[b] - uc[b]).max() / max(np.abs(uc[b]).max(), 9.81 * args.dt))
+        err = np.array(err)
+        both = (out["cold"][1]["status"] == 0) & (out["learned"][1]["status"] == 0)
+        return {"state": f"the {W} worlds after {args.warmup} warm-up steps, one step each way, tol {args.tol}",
+                "mean_iterations": {k: float(v[1]["iterations"].mean()) for k, v in out.items()},
+                "converged_fraction": {k: float(np.mean(v[1]["status"] == 0)) for k, v in out.items()},
+                "err_u_learned_vs_cold": {"median": float(np.median(err)), "p99": float(np.quantile(err, 0.99)),
+                                          "max_where_both_converged": float(err[both].max()) if both.any() else None}}
+
+    learned_report = learned_vs_cold() if nets and args.workload == "biped" else None
+
     def run_variant(name, warm_mode, learned=False, mdl=None, refine64=True, cr=0):
         mdl = mdl or model
         mdl.set_params(K.make_params(rho=args.rho, warm_mode=warm_mode, refine64=refine64, cr_iters=cr,
-                                     ncp_stop=args.ncp_stop))
+                                     ncp_stop=args.ncp_stop, stall_window=args.stall_window))
         st = K.State(mdl, dev)
         graph = None
         if args.graph:
@@ -446,7 +485,7 @@ def run_gpu(args, rank, world):
             rep = st.residuals()
             rows.append(rep["num_rows"].copy())
             its.append(rep["iterations"].copy())
-            conv.append(float(np.mean(rep["status"] == 0)))
+            conv.append(float(np.mean((rep["status"] & ~8) == 0)))    # converged, or stopped by the stall exit
             ncp.append(rep["r_ncp"].copy())
             status.append(rep["status"].copy())
         torch.cuda.nvtx.range_pop()
@@ -485,7 +524,7 @@ def run_gpu(args, rank, world):
     # ---- end to end through the C ABI: pinned host actuation in, body state out, every step
     learned = head == "mixed_learned_warm"
     model.set_params(K.make_params(rho=args.rho, warm_mode=K.WARM_EXTERNAL if learned else K.WARM_CACHED,
-                                   ncp_stop=args.ncp_stop))
+                                   ncp_stop=args.ncp_stop, stall_window=args.stall_window))
     B = int(ws.world_body_offset[-1])
     tau_pin = torch.tensor(tau_host).pin_memory()
     q_out = torch.empty((B, 7), dtype=torch.float32).pin_memory()
@@ -544,6 +583,7 @@ def run_gpu(args, rank, world):
         "config": {"workload": f"{desc} per GPU, dt={args.dt}, Gaussian actuation sigma=5, PADMM tol={args.tol}, "
                                f"N_max={args.iters}, rho={args.rho}"
                                f"{', converged = ADMM residuals and NCP residual below tol' if args.ncp_stop else ''}"
+                               f"{f', stall exit every {args.stall_window} iterations' if args.ncp_stop and args.stall_window else ''}"
                                f"; headline: {head}",
                    "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}"},
         "variants": variants,
@@ -562,6 +602,8 @@ def run_gpu(args, rank, world):
     }
     if train_report:
         line["learned_warm_start_training"] = train_report
+    if learned_report:
+        line["learned_vs_cold_start"] = learned_report
     if tune_report:
         line["autotuned_plan"] = tune_report
     if args.graph:

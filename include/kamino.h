@@ -76,7 +76,8 @@ enum { KAMINO_WARM_COLD = 0, KAMINO_WARM_CACHED = 1, KAMINO_WARM_EXTERNAL = 2 };
  * velocity; the world's state and impulse cache are left as they were before the step.  TIMEOUT: a
  * bounded device wait (the tensor cores' completion signal in the mixed-precision factorisation)
  * expired twice; the world is abandoned for this step, its state left as it was. */
-enum { KAMINO_WORLD_NOT_CONVERGED = 1, KAMINO_WORLD_NONFINITE = 2, KAMINO_WORLD_TIMEOUT = 4 };
+enum { KAMINO_WORLD_NOT_CONVERGED = 1, KAMINO_WORLD_NONFINITE = 2, KAMINO_WORLD_TIMEOUT = 4,
+       KAMINO_WORLD_STALLED = 8 };
 
 typedef struct {
     double eta;        /* proximal regularisation, Alg. 1 (scaled units), >= 0              */
@@ -102,6 +103,12 @@ typedef struct {
                         * the iterate's (lambda, u+) on the contact and joint-limit blocks
                         * (kamino_residual.r_ncp) must be below tol; it is evaluated only in the
                         * iterations whose residuals pass, and the world iterates on otherwise. */
+    int32_t stall_window; /* 0: off.  W > 0 (dense formulation, with ncp_stop): every W iterations, a
+                        * world whose r_p and r_c are below tol but whose r_d is not also stops when
+                        * the natural-map residual is below tol and u+ moved by less than tol
+                        * (relative to max(|u+|inf, |g| dt)) over the last W iterations: the dual
+                        * residual's floor of redundant rows, which no iteration removes and which
+                        * leaves u+ (nearly) fixed.  Reported as KAMINO_WORLD_STALLED. */
 } kamino_solver_params;
 
 /* Time stepping (Sec. 3).  EULER: semi-implicit Euler, everything evaluated at the start-of-step

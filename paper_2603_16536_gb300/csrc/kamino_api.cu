@@ -58,6 +58,7 @@ kamino_status check_params(const kamino_solver_params &p) {
         return fail(KAMINO_E_INVALID_ARG, "params.warm_mode %d is not a KAMINO_WARM_* value", p.warm_mode);
     if (p.integrator != KAMINO_INTEGRATOR_EULER && p.integrator != KAMINO_INTEGRATOR_MIDPOINT)
         return fail(KAMINO_E_INVALID_ARG, "params.integrator %d is not a KAMINO_INTEGRATOR_* value", p.integrator);
+    if (p.stall_window < 0) return fail(KAMINO_E_INVALID_ARG, "params.stall_window must be >= 0");
     if (p.cr_iters < 0 || p.cr_iters > KAMINO_MAX_CR_ITERS)
         return fail(KAMINO_E_INVALID_ARG, "params.cr_iters must be in [0, %d] (got %d)", KAMINO_MAX_CR_ITERS, p.cr_iters);
     return KAMINO_OK;
@@ -326,6 +327,7 @@ StepArgs<T> make_args(kamino_state_s *st, double dt, int iters, double tol, cons
     a.refine64 = m->params.refine64 ? 1 : 0;
     a.cr_iters = m->params.cr_iters;
     a.ncp_stop = m->params.ncp_stop ? 1 : 0;
+    a.stall_window = m->params.ncp_stop ? m->params.stall_window : 0;
     // the inverse may live in tensor memory when a world's shared memory keeps a second CTA off the SM
     // (the 512-column allocation then never waits for another CTA); the sparse formulation has none
     a.tmem = (sizeof(T) == 4 && a.cr_iters == 0 && m->mp_max <= 256 && m->smem > kMaxSmem / 2) ? 1 : 0;

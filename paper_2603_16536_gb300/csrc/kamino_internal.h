@@ -62,6 +62,7 @@ struct StepArgs {
     int refine64;              // 1: FP64 right-hand side and refinement residual near convergence
     int cr_iters;              // 0: dense formulation; k >= 1: sparse formulation, k CR iterations per x-step
     int ncp_stop;              // 1: converged also requires the natural-map NCP residual below tol
+    int stall_window;          // > 0: the stall exit every stall_window iterations (dense formulation)
     int tmem;                  // 1: keep the swept inverse in tensor memory (FP32, whole-CTA groups, mp <= 256)
     // shared-memory layout bounds (maxima over the launched worlds)
     int nb_max, nj_max, nc_max, mp_max, nl_max;
@@ -80,7 +81,7 @@ struct PersistentArgs {
 struct Layout {
     size_t bq, bu, bRd, bI, bIinv, bminv, bufree, jwr, cid, cslot, rbody, rJ, rvs, rreg;
     size_t lgap, lJ, lrank, lcid;
-    size_t vfd, p, x, xn, y, z, yh, zh, b, mut, mui, wv, fb, bro, brow, X, A, red, misc, total;
+    size_t vfd, p, x, xn, y, z, yh, zh, b, mut, mui, wv, fb, ust, bro, brow, X, A, red, misc, total;
 };
 
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -137,6 +138,7 @@ __host__ __device__ inline Layout make_layout(int nb, int nj, int nc, int mp, in
     take(L.mui, (nc > 0 ? nc : 1) * s);
     take(L.wv, dv * s);
     take(L.fb, (dense ? nb * 6 : 0) * s);
+    take(L.ust, (dense ? nb * 6 : 0) * s);   // u+ at the last stall check
     take(L.bro, (nb + 1) * sizeof(int));
     take(L.brow, 2 * mp * sizeof(int));
     if (!dense) {

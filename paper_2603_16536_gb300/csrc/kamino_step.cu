@@ -1570,11 +1570,15 @@ __device__ bool cr_ncp_ok(const CrWorld<T> &c, const Group &g, const CrIterates<
 // gather M^-1 J^T w into fb, and the owners of the limit rows and contacts form
 // v~ = v~_f + P J (M^-1 J^T P y) on their rows and the natural map.  Two barriers and one reduction;
 // y from y64 when set.  The caller compares with a margin below tol for the FP32 rounding of v~.
+// With `ust` set (the stall exit), also u+ = u_free + M^-1 J^T P y per body: `du` gets the largest
+// change against the u+ stored in `ust` by the previous check, `umax` the largest |u+|, and `ust`
+// the new u+.
 template <typename T, int S>
 __device__ T ncp_check_fast(const Group &g, int nunits, int nfix, int nbil, int nb, int LB, const int *bro,
                             const int *brow, const int *rbody, const T *rJ, const T *p, const T *mut,
                             const T *bminv, const T *bIinv, const double *vfd, const T *y, const double *y64,
-                            T *w, T *fb, T *red, int phase) {
+                            T *w, T *fb, T *red, int phase, const T *bufree = nullptr, T *ust = nullptr,
+                            T *du = nullptr, T *umax = nullptr) {
     const int tid = g.tid, nthr = g.size;
 #pragma unroll
     for (int sl = 0; sl < S; ++sl) {
@@ -1610,7 +1614,16 @@ __device__ T ncp_check_fast(const Group &g, int nunits, int nfix, int nbil, int 
         }
     }
     g.sync();
-    T lncp = T(0);
+    T lncp = T(0), ldu = T(0), lum = T(0);
+    if (ust != nullptr) {
+        for (int i = tid; i < nb; i += nthr)
+            for (int k = 0; k < 6; ++k) {
+                const T uk = bufree[6 * i + k] + fb[6 * i + k];
+                ldu = fmax(ldu, fabs(uk - ust[6 * i + k]));
+                lum = fmax(lum, fabs(uk));
+                ust[6 * i + k] = uk;
+            }
+    }
 #pragma unroll
     for (int sl = 0; sl < S; ++sl) {
         const int u = tid + sl * nthr;
@@ -1645,8 +1658,10 @@ __device__ T ncp_check_fast(const Group &g, int nunits, int nfix, int nbil, int 
         }
         for (int t = 0; t < 3; ++t) lncp = fmax(lncp, fabs(ls[t] - pr[t]));
     }
-    T d0 = T(0), d1 = T(0), d2 = T(0);
-    group_reduce4(lncp, d0, d1, d2, red, phase, g);
+    T d2 = T(0);
+    group_reduce4(lncp, ldu, lum, d2, red, phase, g);
+    if (du) *du = ldu;
+    if (umax) *umax = lum;
     return lncp;
 }
 
@@ -1923,7 +1938,7 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
     double *fd = nullptr;     // FP64 scratch of 6 nb words for phase 9
     T rp = T(INFINITY), rd = T(INFINITY), rc = T(INFINITY);
     int it = 0;
-    bool converged = false;
+    bool converged = false, stalled = false;
     if constexpr (CR) {
         // ---- 5c'-8'. Sparse formulation (Sec. 5.1): no matrix, no factorisation; Alg. 1 with every
         // x-step k Conjugate Residual iterations on the matrix-free operator (see cr_padmm)
@@ -2208,6 +2223,8 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
         // outside the loop (kept out of the loop body, which it would otherwise make slower) and the
         // iterations resume if it fails.
         it = 1;
+        bool stall_due = false, stall_prev = false;
+        T *ust = (T *)(smem + L.ust);
         for (;;) {
         for (; it <= a.iters; ++it) {
             // [8a] per body: g_b = M_b^-1 sum over the body's rows r of J_rb^T (P x)_r; LB lanes per
@@ -2361,6 +2378,31 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
                 hpv = init != nullptr;
             }
             if (converged) break;
+            if (a.stall_window > 0 && it % a.stall_window == 0) {
+                if (rp < a.tol && rc < a.tol) { stall_due = true; break; }
+                stall_prev = false;
+            }
+        }
+        if (stall_due) {
+            // the stall exit: r_p and r_c are below tol, r_d is not.  Stop when the natural map is
+            // below tol and u+ moved by less than tol (relative) since the check stall_window
+            // iterations ago: r_d then sits on the floor of the redundant rows (readings 15, 17)
+            stall_due = false;
+            g.sync();
+            T du = T(0), umax = T(0);
+            const T r = ncp_check_fast<T, S>(g, nunits, nfix, nbil, nb, LB, bro, brow, rbody, rJ, p, mut, bminv,
+                                             bIinv, vfd, y, hpv ? y64 : nullptr, xn, fb, red, (it + 1) & 1, bufree,
+                                             ust, &du, &umax);
+            const T gdt = dt * sqrt(M.gx * M.gx + M.gy * M.gy + M.gz * M.gz);
+            if (stall_prev && r < T(0.8) * a.tol && du < a.tol * fmax(umax, gdt)) {
+                converged = true;
+                stalled = true;
+                break;
+            }
+            stall_prev = true;
+            if (it >= a.iters) break;
+            ++it;
+            continue;
         }
         if (!(converged && a.ncp_stop)) break;
         if (a.tol >= T(1e-6)) {
@@ -2423,7 +2465,8 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
     if (tid == 0) {
         kamino_residual rep;
         rep.iterations = it;
-        rep.status = (converged ? 0 : KAMINO_WORLD_NOT_CONVERGED) | (world_bad ? KAMINO_WORLD_NONFINITE : 0);
+        rep.status = (converged ? 0 : KAMINO_WORLD_NOT_CONVERGED) | (world_bad ? KAMINO_WORLD_NONFINITE : 0) |
+                     (stalled ? KAMINO_WORLD_STALLED : 0);
         rep.num_rows = m;
         rep.num_contacts = nact;
         rep.r_primal = (float)rp;

@@ -19,7 +19,7 @@ from . import build as _build
 FP32, FP64, MIXED = 0, 1, 2
 WARM_COLD, WARM_CACHED, WARM_EXTERNAL = 0, 1, 2
 BUF_BODY_Q, BUF_BODY_U, BUF_CACHE, BUF_WARM, BUF_RESIDUAL, BUF_TAU = 0, 1, 2, 3, 4, 5
-WORLD_NOT_CONVERGED, WORLD_NONFINITE, WORLD_TIMEOUT = 1, 2, 4
+WORLD_NOT_CONVERGED, WORLD_NONFINITE, WORLD_TIMEOUT, WORLD_STALLED = 1, 2, 4, 8
 STATUS = {0: "KAMINO_OK", 1: "KAMINO_E_INVALID_ARG", 2: "KAMINO_E_TOPOLOGY", 3: "KAMINO_E_NOMEM",
           4: "KAMINO_E_CUDA", 5: "KAMINO_E_NONFINITE", 6: "KAMINO_E_TIMEOUT", 7: "KAMINO_E_UNSUPPORTED"}
 
@@ -33,16 +33,17 @@ class KaminoError(RuntimeError):
 class SolverParams(C.Structure):
     _fields_ = [("eta", C.c_double), ("rho", C.c_double), ("beta", C.c_double), ("margin", C.c_double),
                 ("nesterov", C.c_int32), ("precond", C.c_int32), ("warm_mode", C.c_int32), ("refine64", C.c_int32),
-                ("integrator", C.c_int32), ("cr_iters", C.c_int32), ("ncp_stop", C.c_int32)]
+                ("integrator", C.c_int32), ("cr_iters", C.c_int32), ("ncp_stop", C.c_int32),
+                ("stall_window", C.c_int32)]
 
 
 INTEGRATOR_EULER, INTEGRATOR_MIDPOINT = 0, 1
 
 
 def make_params(eta=1e-6, rho=0.1, beta=0.2, margin=0.005, nesterov=True, precond=True, warm_mode=WARM_COLD,
-                refine64=True, integrator=INTEGRATOR_EULER, cr_iters=0, ncp_stop=False):
+                refine64=True, integrator=INTEGRATOR_EULER, cr_iters=0, ncp_stop=False, stall_window=0):
     return SolverParams(eta, rho, beta, margin, int(nesterov), int(precond), int(warm_mode), int(refine64),
-                        int(integrator), int(cr_iters), int(ncp_stop))
+                        int(integrator), int(cr_iters), int(ncp_stop), int(stall_window))
 
 
 _P = C.c_void_p

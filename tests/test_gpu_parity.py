@@ -631,3 +631,55 @@ def test_ncp_stop_qualifies_every_converged_world(K, cr):
         assert rep["num_rows"][w] == info.m
         rc, _ = _ncp_parts(info, ug[ws.bodies(w)].reshape(-1), _gpu_lambda(info, cache[off[w]:off[w + 1]]))
         assert abs(float(rep["r_ncp"][w]) - rc) <= 1e-6 + 0.1 * rc, (w, float(rep["r_ncp"][w]), rc)
+
+
+def test_stall_exit_matches_the_long_run_oracle(K):
+    """The stall exit (ncp_stop with stall_window 64) on 4096 actuated bipeds after 12 steps, where
+    some contact + joint sets are inconsistent (reading 17): the worlds it stops (KAMINO_WORLD_STALLED,
+    reported converged) have r_p, r_c and the natural map below tol and u+ at rest over 64 iterations.
+    On up to 8 of them, from the same state, against the oracle run far past the benchmark's cap
+    (eps 1e-10, 4000 iterations): each is within 1e-4 in u+ or, where the oracle's own answer still
+    moves, an NCP solution under the contact-world criterion.  The exit also cuts the iterations."""
+    ws = wg.make_biped(num_worlds=4096, seed=0)
+    dt, nmax, tol = 2e-3, 1000, 1e-5
+    model = K.Model(ws, "mixed", K.make_params(rho=0.1, ncp_stop=True, stall_window=64))
+    st = K.State(model)
+    tau = lambda k: torch.tensor(wg.actuation(ws, 0, 10000 + k), dtype=torch.float32, device="cuda").contiguous()
+    for k in range(12):
+        st.step(dt, nmax, tol, tau(k))
+    torch.cuda.synchronize()
+    q, u = st.body_q.double().cpu().numpy(), st.body_u.double().cpu().numpy()
+    c0 = st.cache.clone()
+    st.step(dt, nmax, tol, tau(12))
+    torch.cuda.synchronize()
+    rep, ug, cache = st.residuals(), st.body_u.double().cpu().numpy(), st.cache.double().cpu().numpy()
+    stalled = np.nonzero(rep["status"] & K.WORLD_STALLED)[0]
+    assert np.all(rep["status"][stalled] & K.WORLD_NOT_CONVERGED == 0)
+    assert np.all(rep["r_ncp"][stalled] < tol) and np.all(rep["r_primal"][stalled] < tol)
+    # the same step without the exit, from the same state
+    model2 = K.Model(ws, "mixed", K.make_params(rho=0.1, ncp_stop=True))
+    st2 = K.State(model2)
+    st2.body_q.copy_(torch.tensor(q, dtype=torch.float32)); st2.body_u.copy_(torch.tensor(u, dtype=torch.float32))
+    st2.cache.copy_(c0)
+    st2.step(dt, nmax, tol, tau(12))
+    torch.cuda.synchronize()
+    rep2 = st2.residuals()
+    print(f"stalled worlds {len(stalled)} of 4096; mean iterations {rep['iterations'].mean():.1f} with the exit, "
+          f"{rep2['iterations'].mean():.1f} without; capped {np.mean(rep['status'] & 1):.4f} vs "
+          f"{np.mean(rep2['status'] & 1):.4f}")
+    assert len(stalled) > 0
+    assert rep["iterations"].sum() < rep2["iterations"].sum()
+    sample = [int(w) for w in stalled[:8]]
+    st0 = T.WorldState(q=q.copy(), u=u.copy(), cache=[None] * ws.num_worlds)
+    _, long = T.step(ws, st0, wg.actuation(ws, 0, 10012), dt, T.SolverParams(rho=0.1, eps=1e-10, n_max=4000),
+                     worlds=sample)
+    off = _cache_offsets(ws, _all_infos_like(ws))
+    for w, info in zip(sample, long):
+        bs = ws.bodies(w)
+        eu = np.abs(ug[bs].reshape(-1) - info.u_plus).max() / max(np.abs(info.u_plus).max(), G * dt)
+        lam = _gpu_lambda(info, cache[off[w]:off[w + 1]])
+        r_gpu = _ncp(info, ug[bs].reshape(-1), lam)
+        r_orc, r32 = _ncp(info, info.u_plus, info.lam), _ncp32(info)
+        print(f"world {w}: iterations {int(rep['iterations'][w])}, err_u vs long oracle {eu:.2e}, ncp gpu {r_gpu:.2e}, "
+              f"oracle {r_orc:.2e} (converged {info.converged}), fp32 floor {r32:.2e}")
+        assert eu <= 1e-4 or r_gpu <= NCP_FACTOR * max(r_orc, r32), (w, eu, r_gpu, r_orc, r32)
