@@ -574,7 +574,8 @@ def run_gpu(args, rank, world):
     achieved = flops / (sum(ms_step_h) / 1e3)
     traffic = step_kernel_traffic(args.workload, W)
     plan_mode, plan_buckets = model.plan()
-    step_launches = len(plan_buckets) if plan_mode == K.LAUNCH_PERSISTENT else 1
+    # one launch per bucket (persistent plan), else the step kernel and the longest-first order kernel
+    step_launches = len(plan_buckets) if plan_mode == K.LAUNCH_PERSISTENT else 2
     launches_per_step = step_launches + (7 * len(nets) if learned else 0)
     line = {
         "metric": METRIC, "value": v_head, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -109,7 +109,15 @@ typedef struct {
                         * (relative to max(|u+|inf, |g| dt)) over the last W iterations: the dual
                         * residual's floor of redundant rows, which no iteration removes and which
                         * leaves u+ (nearly) fixed.  Reported as KAMINO_WORLD_STALLED. */
+    int32_t schedule;  /* KAMINO_SCHEDULE_*: order in which the one-CTA-per-world launch takes the
+                        * worlds (results do not depend on it; every world is independent) */
 } kamino_solver_params;
+
+/* IN_ORDER: world w in CTA w.  LONGEST_FIRST: before each step a one-CTA kernel orders the worlds by
+ * the PADMM iterations of their previous step (counting sort, most first), so that the worlds that
+ * will run longest start first and do not extend the end of the launch (the SMs take CTAs in launch
+ * order).  On a state's first step (no previous report) the order is arbitrary. */
+enum { KAMINO_SCHEDULE_IN_ORDER = 0, KAMINO_SCHEDULE_LONGEST_FIRST = 1 };
 
 /* Time stepping (Sec. 3).  EULER: semi-implicit Euler, everything evaluated at the start-of-step
  * pose q-, then q+ = q- (+) dt u+.  MIDPOINT: Moreau-Jean, kinematics, rows, contacts and biases

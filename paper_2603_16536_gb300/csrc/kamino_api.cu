@@ -59,6 +59,8 @@ kamino_status check_params(const kamino_solver_params &p) {
     if (p.integrator != KAMINO_INTEGRATOR_EULER && p.integrator != KAMINO_INTEGRATOR_MIDPOINT)
         return fail(KAMINO_E_INVALID_ARG, "params.integrator %d is not a KAMINO_INTEGRATOR_* value", p.integrator);
     if (p.stall_window < 0) return fail(KAMINO_E_INVALID_ARG, "params.stall_window must be >= 0");
+    if (p.schedule != KAMINO_SCHEDULE_IN_ORDER && p.schedule != KAMINO_SCHEDULE_LONGEST_FIRST)
+        return fail(KAMINO_E_INVALID_ARG, "params.schedule %d is not a KAMINO_SCHEDULE_* value", p.schedule);
     if (p.cr_iters < 0 || p.cr_iters > KAMINO_MAX_CR_ITERS)
         return fail(KAMINO_E_INVALID_ARG, "params.cr_iters must be in [0, %d] (got %d)", KAMINO_MAX_CR_ITERS, p.cr_iters);
     return KAMINO_OK;
@@ -123,7 +125,8 @@ struct kamino_state_s {
     kamino_model_t model = nullptr;
     char *base = nullptr;
     bool owned = false;
-    size_t off_q = 0, off_u = 0, off_cache = 0, off_warm = 0, off_res = 0, off_tau = 0, off_cnt = 0, bytes = 0;
+    size_t off_q = 0, off_u = 0, off_cache = 0, off_warm = 0, off_res = 0, off_tau = 0, off_cnt = 0, off_order = 0;
+    size_t bytes = 0;
     void *ptr(size_t off) const { return base + off; }
 };
 
@@ -379,7 +382,14 @@ kamino_status do_step(kamino_state_s *st, double dt, int iters, double tol, cons
             if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute (step kernel shared memory)");
             m->prepared = true;
         }
-        cudaError_t e = launch_step<T>(a, m->W, m->nb_panel, m->smem, stream);
+        StepArgs<T> b = a;
+        if (m->params.schedule == KAMINO_SCHEDULE_LONGEST_FIRST && m->W > 1) {
+            int *order = (int *)st->ptr(st->off_order);
+            cudaError_t e = launch_order((const kamino_residual *)st->ptr(st->off_res), m->W, order, stream);
+            if (e != cudaSuccess) return cuda_fail(e, "world order launch");
+            b.world_order = order;
+        }
+        cudaError_t e = launch_step<T>(b, m->W, m->nb_panel, m->smem, stream);
         if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
         return KAMINO_OK;
     }
@@ -832,6 +842,7 @@ static void state_layout(kamino_model_t m, kamino_state_s *s) {
     take(s->off_res, (size_t)m->W * sizeof(kamino_residual));
     take(s->off_tau, (size_t)m->W * std::max(m->n_act_max, 1) * esz);
     take(s->off_cnt, std::max<size_t>(m->buckets.size(), 1) * sizeof(int));
+    take(s->off_order, (size_t)m->W * sizeof(int));
     s->bytes = o;
 }
 

@@ -226,5 +226,7 @@ template <typename T>
 cudaError_t occupancy_persistent(int nb_panel, size_t smem, int cr, int *blocks_per_sm);
 template <typename T>
 cudaError_t launch_fk(const FkArgs<T> &args, int num_worlds, size_t smem, cudaStream_t stream);
+// Longest-first order of the worlds from the iterations of their previous step (one CTA).
+cudaError_t launch_order(const kamino_residual *res, int num_worlds, int *order, cudaStream_t stream);
 
 }  // namespace kamino

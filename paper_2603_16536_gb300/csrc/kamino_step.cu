@@ -224,6 +224,20 @@ __device__ __forceinline__ void group_reduce4(T &a, T &b, T &c, T &d, T *red, in
     }
 }
 
+// Six consecutive words at an 8-byte aligned shared-memory address (a row block of J, 12 r + 6 side,
+// or a per-body 6-vector): three 8-byte loads in FP32.
+template <typename T>
+__device__ __forceinline__ void load6(const T *p, T (&v)[6]) {
+    if constexpr (sizeof(T) == 4) {
+        const float2 *q = reinterpret_cast<const float2 *>(p);
+        const float2 a = q[0], b = q[1], c = q[2];
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y; v[4] = c.x; v[5] = c.y;
+    } else {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) v[k] = p[k];
+    }
+}
+
 // 16 consecutive values from a 16-byte aligned shared-memory address (vector loads).
 __device__ __forceinline__ void load16(const float *p, float (&v)[16]) {
     const float4 *q = reinterpret_cast<const float4 *>(p);
@@ -2259,9 +2273,10 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
                         for (int e = bro[body] + sub; e < bro[body + 1]; e += LB) {
                             const int code = brow[e];
                             const T w = wv[code >> 1];
-                            const T *J = rJ + 6 * code;
+                            T Jv[6];
+                            load6(rJ + 6 * code, Jv);
     #pragma unroll
-                            for (int k = 0; k < 6; ++k) f[k] = fma(J[k], w, f[k]);
+                            for (int k = 0; k < 6; ++k) f[k] = fma(Jv[k], w, f[k]);
                         }
                     }
                     for (int o = LB >> 1; o > 0; o >>= 1) {
@@ -2296,14 +2311,18 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
                     const double xr = x_in64 ? x64[r] : (double)x[r];
                     c = T(bbd[r] + (double)p[r] * acc + ((double)shift + (double)p[r] * (double)p[r] * (double)rreg[r]) * xr);
                 } else {
-                    T acc = T(0);
+                    T acc = T(0), Jv[6], gv[6];
                     if (sa >= 0) {
+                        load6(J, Jv);
+                        load6(fb + 6 * sa, gv);
     #pragma unroll
-                        for (int k = 0; k < 6; ++k) acc = fma(J[k], fb[6 * sa + k], acc);
+                        for (int k = 0; k < 6; ++k) acc = fma(Jv[k], gv[k], acc);
                     }
                     if (sb >= 0) {
+                        load6(J + 6, Jv);
+                        load6(fb + 6 * sb, gv);
     #pragma unroll
-                        for (int k = 0; k < 6; ++k) acc = fma(J[6 + k], fb[6 * sb + k], acc);
+                        for (int k = 0; k < 6; ++k) acc = fma(Jv[k], gv[k], acc);
                     }
                     c = bb[r] + p[r] * acc + (shift + p[r] * p[r] * rreg[r]) * x[r];
                 }
@@ -2835,6 +2854,40 @@ cudaError_t launch_fk(const FkArgs<T> &args, int num_worlds, size_t smem, cudaSt
     cudaError_t e = cudaFuncSetAttribute(fk_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     fk_kernel<T><<<num_worlds, kThreads, smem, stream>>>(args);
+    return cudaGetLastError();
+}
+
+namespace {
+// Counting sort of the worlds by the PADMM iterations of their previous step, most first (keys
+// clamped to kKeys - 1): a histogram in shared memory, the start of every key (thread 0), then every
+// world takes the next slot of its key.  The order within a key is arbitrary; it is a permutation.
+constexpr int kOrderKeys = 1024;
+__global__ void __launch_bounds__(1024, 1) order_kernel(const kamino_residual *res, int W, int *order) {
+    __shared__ int start[kOrderKeys];
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    for (int k = tid; k < kOrderKeys; k += nthr) start[k] = 0;
+    __syncthreads();
+    for (int w = tid; w < W; w += nthr) atomicAdd(&start[min(max(res[w].iterations, 0), kOrderKeys - 1)], 1);
+    __syncthreads();
+    if (tid == 0) {
+        int acc = 0;
+        for (int k = kOrderKeys - 1; k >= 0; --k) {
+            const int c = start[k];
+            start[k] = acc;
+            acc += c;
+        }
+    }
+    __syncthreads();
+    for (int w = tid; w < W; w += nthr) {
+        const int pos = atomicAdd(&start[min(max(res[w].iterations, 0), kOrderKeys - 1)], 1);
+        order[pos] = w;
+    }
+}
+}  // namespace
+
+cudaError_t launch_order(const kamino_residual *res, int num_worlds, int *order, cudaStream_t stream) {
+    if (num_worlds <= 0) return cudaSuccess;
+    order_kernel<<<1, 1024, 0, stream>>>(res, num_worlds, order);
     return cudaGetLastError();
 }
 

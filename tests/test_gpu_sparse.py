@@ -159,3 +159,41 @@ def test_sparse_full_size_bipeds(K):
         assert abs(float(rep["r_ncp"][w]) - r) <= 1e-6 + 0.1 * r, (w, float(rep["r_ncp"][w]), r)
     print(f"sparse 4096 bipeds: mean iterations {rep['iterations'].mean():.1f}, converged "
           f"{np.mean(rep['status'] == 0):.3f}, median r_ncp {np.median(rep['r_ncp']):.2e}")
+
+
+def test_fp64_bipeds_in_the_air_match_to_1e9(K):
+    """FP64 on the biped (the dense FP64 working set does not fit in shared memory; the sparse one
+    does): 180 bilateral rows with six redundant loops, unique u+, one actuated step to 1e-12 against
+    the oracle's sparse formulation to 1e-12, within the FP64 bar 1e-9."""
+    ws = wg.make_biped(num_worlds=4, seed=3, z_lift=0.2)
+    q, u = np.asarray(ws.body_q0, np.float64), np.asarray(ws.body_u0, np.float64)
+    tau = wg.actuation(ws, 3, 0)
+    qg, ug, rep, _ = gpu_step(K, ws, q, u, tau, 2e-3, 50000, 1e-12, "fp64", cr_iters=CR)
+    ref, infos = oracle_step(ws, q, u, tau, 2e-3, eps=1e-12, cr_iters=CR)
+    check_report(rep, infos)
+    eu, eq = errors(q, qg, ug, ref.q, ref.u, 2e-3, "fp64")
+    print(f"FP64 sparse bipeds in the air: err_u {eu:.2e}, err_q {eq:.2e}, iterations {rep['iterations'].tolist()}, "
+          f"oracle converged {[i.converged for i in infos]}")
+    assert eu <= 1e-9 and eq <= 1e-9
+
+
+def test_fp64_standing_bipeds(K):
+    """FP64 standing bipeds (8 active contacts each), one actuated step to 1e-12: every world matches
+    the oracle within the FP64 bar 1e-9 or, where the frictional solution is not unique (reading 19),
+    is an NCP solution within 10x the oracle's own residual."""
+    from tests.test_gpu_parity import _all_infos_like, _cache_offsets, _gpu_lambda, _ncp
+    ws = wg.make_biped(num_worlds=4, seed=2)
+    q, u = np.asarray(ws.body_q0, np.float64), np.asarray(ws.body_u0, np.float64)
+    tau = wg.actuation(ws, 2, 0)
+    qg, ug, rep, cache = gpu_step(K, ws, q, u, tau, 2e-3, 50000, 1e-12, "fp64", cr_iters=CR)
+    ref, infos = oracle_step(ws, q, u, tau, 2e-3, eps=1e-12, cr_iters=CR)
+    check_report(rep, infos)
+    off = _cache_offsets(ws, _all_infos_like(ws))
+    for w, info in enumerate(infos):
+        bs = ws.bodies(w)
+        eu, eq = errors(q[bs], qg[bs], ug[bs], ref.q[bs], ref.u[bs], 2e-3, "fp64")
+        r_gpu = _ncp(info, ug[bs].reshape(-1), _gpu_lambda(info, cache[off[w]:off[w + 1]]))
+        r_orc = _ncp(info, info.u_plus, info.lam)
+        print(f"world {w}: err_u {eu:.2e}, err_q {eq:.2e}, iterations {int(rep['iterations'][w])}, "
+              f"ncp gpu {r_gpu:.2e} oracle {r_orc:.2e}")
+        assert (eu <= 1e-9 and eq <= 1e-9) or r_gpu <= 10.0 * max(r_orc, 1e-13), (w, eu, r_gpu, r_orc)
