@@ -51,7 +51,8 @@ def parse():
     p.add_argument("--cpu-sample", type=int, default=4096, help="worlds in the CPU-oracle sample (one step each)")
     p.add_argument("--ref-sample", type=int, default=64, help="worlds per timed step of --impl reference")
     p.add_argument("--no-cpu", action="store_true")
-    p.add_argument("--workload", default="biped", choices=["biped", "heightfield", "hetero", "fourbar"])
+    p.add_argument("--workload", default="biped", choices=["biped", "heightfield", "hetero", "fourbar", "team"])
+    p.add_argument("--team", type=int, default=2, help="bipeds per world of the 'team' workload (sparse formulation)")
     p.add_argument("--learned", type=int, default=1, help="train and time the learned warm start")
     p.add_argument("--gen-steps", type=int, default=40, help="solver steps generating training pairs")
     p.add_argument("--train-steps", type=int, default=600, help="Adam steps of the warm-start network")
@@ -227,6 +228,16 @@ def algorithmic_flops(rows, iters):
     return m ** 3 / 3.0 + it * (2.0 * m * m + 20.0 * m) + 2.0 * 12.0 * m * 8.0
 
 
+def algorithmic_flops_sparse(rows, iters, k):
+    """Flops of the sparse formulation per world-step: per PADMM iteration k + 1 applications of the
+    matrix-free operator (per row: the two 6-blocks of J against the gathered body vectors, and the
+    gather of J^T P v, ~96 flops), k CR iterations of vector updates and dot products (~10 m) and
+    ~20 m elementwise; no factorisation."""
+    m = rows.astype("float64")
+    it = iters.astype("float64")
+    return it * ((k + 1) * 96.0 * m + k * 10.0 * m + 20.0 * m)
+
+
 def ncp_report(ncp, status, its, tol, n_max, rate):
     """The metric's qualifying condition over every world-step of a variant: the device's
     natural-map NCP residual of the returned (lambda, u+) (kamino_residual.r_ncp) against the
@@ -297,6 +308,10 @@ def build_workload(args, seed):
         return wg.concat([wg.make_fourbar(q, seed=seed), wg.make_stewart(q, seed=seed), wg.make_excavator(q, seed=seed),
                           wg.make_biped(q, seed=seed)]), \
             f"{4 * q} heterogeneous worlds ({q} each: four-bar 20 rows, 6-UPS Stewart 72, excavator 60, biped <=228)"
+    if args.workload == "team":
+        return wg.make_biped_team(num_worlds=args.worlds, seed=seed, per_world=args.team), \
+            f"{args.worlds} worlds of {args.team} closed-loop bipeds each ({31 * args.team} bodies, " \
+            f"{180 * args.team} joint rows + up to {48 * args.team} contact rows; beyond the dense formulation)"
     if args.workload == "fourbar":
         return wg.make_fourbar(num_worlds=args.worlds, seed=seed), f"{args.worlds} planar four-bars (20 rows)"
     raise ValueError(args.workload)
@@ -343,8 +358,19 @@ def run_gpu(args, rank, world):
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)   # > L2 (129 MB)
     lib = K.load_library()
     sptr = C.c_void_p(stream.cuda_stream)
-    model_plain = K.Model(ws, "fp32", K.make_params(rho=args.rho))
-    model = K.Model(ws, "mixed", K.make_params(rho=args.rho))
+    def dense_model(precision):
+        """The dense formulation's model, or None where its matrix does not fit (larger worlds)."""
+        try:
+            return K.Model(ws, precision, K.make_params(rho=args.rho))
+        except K.KaminoError as e:
+            if e.status != 7:
+                raise
+            return None
+
+    model_plain = dense_model("fp32")
+    model = dense_model("mixed")
+    if model is None:
+        args.learned = 0              # the learned warm start is timed with the dense formulation
     model_sparse = K.Model(ws, "fp32", K.make_params(rho=args.rho, cr_iters=args.cr)) if args.cr > 0 else None
     tune_report = None
     if args.workload == "hetero":
@@ -500,9 +526,11 @@ def run_gpu(args, rank, world):
     sampler = ClockSampler(local)
     sampler.start()
     results = {}
-    results["plain_fp32_cold"] = run_variant("plain_fp32_cold", K.WARM_COLD, mdl=model_plain, refine64=False)
-    results["mixed_cold"] = run_variant("mixed_cold", K.WARM_COLD)
-    results["mixed_cached_warm"] = run_variant("mixed_cached_warm", K.WARM_CACHED)
+    if model_plain is not None:
+        results["plain_fp32_cold"] = run_variant("plain_fp32_cold", K.WARM_COLD, mdl=model_plain, refine64=False)
+    if model is not None:
+        results["mixed_cold"] = run_variant("mixed_cold", K.WARM_COLD)
+        results["mixed_cached_warm"] = run_variant("mixed_cached_warm", K.WARM_CACHED)
     if nets:
         results["mixed_learned_warm"] = run_variant("mixed_learned_warm", K.WARM_EXTERNAL, learned=True)
     if model_sparse is not None:
@@ -516,14 +544,19 @@ def run_gpu(args, rank, world):
         variants[name] = {"value": units / t, "ms_per_step": 1e3 * t / args.steps,
                           "mean_iterations": float(its.mean()), "converged_fraction": float(np.mean(conv)),
                           **ncp_report(ncp, status, its, args.tol, args.iters, units / t)}
-    head = "mixed_learned_warm" if nets else "mixed_cached_warm"
+    sparse_name = f"sparse_cr{args.cr}_fp32_cold"
+    head = "mixed_learned_warm" if nets else "mixed_cached_warm" if model is not None else sparse_name
+    head_sparse = head == sparse_name
     st_h, ms_h, rows_h, its_h, _, ms_step_h, _, _ = results[head]
     v_head = variants[head]["value"]
     t_head = units / v_head
 
     # ---- end to end through the C ABI: pinned host actuation in, body state out, every step
     learned = head == "mixed_learned_warm"
-    model.set_params(K.make_params(rho=args.rho, warm_mode=K.WARM_EXTERNAL if learned else K.WARM_CACHED,
+    if head_sparse:
+        model = model_sparse
+    model.set_params(K.make_params(rho=args.rho, warm_mode=K.WARM_EXTERNAL if learned else K.WARM_COLD if head_sparse
+                                   else K.WARM_CACHED, cr_iters=args.cr if head_sparse else 0,
                                    ncp_stop=args.ncp_stop, stall_window=args.stall_window))
     B = int(ws.world_body_offset[-1])
     tau_pin = torch.tensor(tau_host).pin_memory()
@@ -570,7 +603,8 @@ def run_gpu(args, rank, world):
     smax = clocks.get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     alu_peak = sm_count * FP32_LANES * 2 * smax * 1e6 / 1e12       # FP32 FMA lanes x clock, TFLOP/s
-    flops = float(algorithmic_flops(rows_h, its_h).sum()) / 1e12
+    flops = float((algorithmic_flops_sparse(rows_h, its_h, args.cr) if head_sparse
+                   else algorithmic_flops(rows_h, its_h)).sum()) / 1e12
     achieved = flops / (sum(ms_step_h) / 1e3)
     traffic = step_kernel_traffic(args.workload, W)
     plan_mode, plan_buckets = model.plan()
@@ -580,7 +614,7 @@ def run_gpu(args, rank, world):
     line = {
         "metric": METRIC, "value": v_head, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_head / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32+tf32+bf16", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if head_sparse else "f32+tf32+bf16", "data": "synthetic",
         "config": {"workload": f"{desc} per GPU, dt={args.dt}, Gaussian actuation sigma=5, PADMM tol={args.tol}, "
                                f"N_max={args.iters}, rho={args.rho}"
                                f"{', converged = ADMM residuals and NCP residual below tol' if args.ncp_stop else ''}"
@@ -588,14 +622,15 @@ def run_gpu(args, rank, world):
                                f"; headline: {head}",
                    "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}"},
         "variants": variants,
-        "warm_over_plain": v_head / variants["plain_fp32_cold"]["value"],
+        "warm_over_plain": v_head / variants["plain_fp32_cold"]["value"] if "plain_fp32_cold" in variants else None,
         "mean_rows": float(rows_h.mean()),
         "gpu_launches": args.steps * launches_per_step,
         "e2e": {"value": v_e2e, "unit": UNIT, "h2d_bytes_per_step": W * ws.n_act_max * 4,
                 "d2h_bytes_per_step": B * 13 * 4},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                      "frac": achieved / alu_peak, "traffic": traffic,
-                     "kernel": "kamino step kernel (one launch per step)",
+                     "kernel": "kamino step kernel, sparse formulation" if head_sparse
+                     else "kamino step kernel (one launch per step)",
                      "launch_ms": sum(ms_step_h) / len(ms_step_h),
                      "peak_note": f"derived FP32 FMA peak: {sm_count} SMs x {FP32_LANES} lanes x 2 x {smax:.0f} MHz",
                      "hbm": hbm_roofline(traffic, sum(ms_step_h) / len(ms_step_h), peaks)},

@@ -237,8 +237,8 @@ size_t esize(const kamino_model_s *m) { return m->precision == KAMINO_FP64 ? siz
 size_t persistent_smem(const kamino_model_s *m, const Bucket &b, int group, int nbp, size_t *slice) {
     if (b.units > kSlots * group) return 0;
     const int mp = std::max(((b.rows + 15) / 16) * 16, 16);
-    if (mp > kMaxRowsPad) return 0;
     const bool dense = m->params.cr_iters == 0;
+    if (mp > (dense ? kMaxRowsPad : kMaxRowsPadSparse)) return 0;
     const Layout L = esize(m) == sizeof(double) ? make_layout<double>(b.nb, b.nj, b.nc, mp, nbp, m->nl_max, dense)
                                                 : make_layout<float>(b.nb, b.nj, b.nc, mp, nbp, m->nl_max, dense);
     const size_t sl = align_up(L.total, 16);
@@ -525,7 +525,7 @@ static kamino_status configure(kamino_model_s *m) {
     m->prepared = false;
     for (int nbp : {16, 8}) {
         const int mp = std::max(((m->max_rows + 15) / 16) * 16, 16);
-        if (mp > kMaxRowsPad) continue;
+        if (mp > (dense ? kMaxRowsPad : kMaxRowsPadSparse)) continue;
         const Layout L = m->precision == KAMINO_FP64
                              ? make_layout<double>(m->nb_max, m->nj_max, m->nc_max, mp, nbp, m->nl_max, dense)
                              : make_layout<float>(m->nb_max, m->nj_max, m->nc_max, mp, nbp, m->nl_max, dense);
@@ -538,8 +538,9 @@ static kamino_status configure(kamino_model_s *m) {
     }
     if (m->smem == 0)
         return fail(KAMINO_E_UNSUPPORTED,
-                    "a world needs %d constraint rows; the shared-memory working set exceeds %zu bytes "
-                    "(max %d padded rows)", m->max_rows, kMaxSmem, kMaxRowsPad);
+                    "a world needs %d constraint rows; the %s formulation's shared-memory working set exceeds %zu "
+                    "bytes (max %d padded rows)", m->max_rows, dense ? "dense" : "sparse", kMaxSmem,
+                    dense ? kMaxRowsPad : kMaxRowsPadSparse);
     for (auto &b : m->buckets) {
         b.grid = 0;
         if (!choose_default(m, b))

@@ -12,7 +12,8 @@ namespace kamino {
 
 constexpr int kThreads = 256;        // CTA size of the per-world step kernel (8 warps)
 constexpr int kWarps = kThreads / 32;
-constexpr int kMaxRowsPad = 288;     // largest padded row count the step kernel supports
+constexpr int kMaxRowsPad = 288;     // largest padded row count of the dense formulation (its matrix)
+constexpr int kMaxRowsPadSparse = 1024;   // of the sparse formulation (units <= 4 per thread)
 constexpr int kMaxChunks = kMaxRowsPad / 32;
 constexpr int kMaxCandidates = 64;   // contact candidates per world
 constexpr int kSlots = 4;            // PADMM units (joint rows / contacts) per thread: units <= kSlots * group

@@ -2540,9 +2540,10 @@ __global__ void __launch_bounds__(kThreads, 1) step_kernel(const StepArgs<T> a) 
 }
 
 // The sparse formulation, one world per CTA: no tensor memory, and a working set small enough for
-// several CTAs per SM (hence the register bound of two resident CTAs).
+// several CTAs per SM (hence the register bound of two resident CTAs, up to 2 units a thread; the
+// largest worlds, up to 4 units a thread, keep their registers with one CTA per SM).
 template <typename T, int S>
-__global__ void __launch_bounds__(kThreads, 2) step_kernel_cr(const StepArgs<T> a) {
+__global__ void __launch_bounds__(kThreads, S <= 2 ? 2 : 1) step_kernel_cr(const StepArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int w = a.world_order ? a.world_order[blockIdx.x] : (int)blockIdx.x;
     const Group g{(int)threadIdx.x, kThreads, 0};
@@ -2789,6 +2790,7 @@ cudaError_t prepare_step(int nb_panel, size_t smem) {
     const int b = (int)smem;
     cudaError_t e = cudaFuncSetAttribute(step_kernel_cr<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(step_kernel_cr<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(step_kernel_cr<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
     if (e != cudaSuccess) return e;
     if (nb_panel == 16) {
         e = cudaFuncSetAttribute(step_kernel<T, 16, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
@@ -2804,9 +2806,10 @@ template <typename T>
 cudaError_t launch_step(const StepArgs<T> &args, int num_worlds, int nb_panel, size_t smem, cudaStream_t stream) {
     if (num_worlds <= 0) return cudaSuccess;
     const bool one = args.mp_max <= kThreads;     // units <= rows <= mp_max
-    if (args.cr_iters > 0) {
+    if (args.cr_iters > 0) {     // units <= rows <= mp_max
         if (one) step_kernel_cr<T, 1><<<num_worlds, kThreads, smem, stream>>>(args);
-        else step_kernel_cr<T, 2><<<num_worlds, kThreads, smem, stream>>>(args);
+        else if (args.mp_max <= 2 * kThreads) step_kernel_cr<T, 2><<<num_worlds, kThreads, smem, stream>>>(args);
+        else step_kernel_cr<T, 4><<<num_worlds, kThreads, smem, stream>>>(args);
     } else if (nb_panel == 16) {
         if (one) step_kernel<T, 16, 1><<<num_worlds, kThreads, smem, stream>>>(args);
         else step_kernel<T, 16, 2><<<num_worlds, kThreads, smem, stream>>>(args);

@@ -197,3 +197,19 @@ def test_fp64_standing_bipeds(K):
         print(f"world {w}: err_u {eu:.2e}, err_q {eq:.2e}, iterations {int(rep['iterations'][w])}, "
               f"ncp gpu {r_gpu:.2e} oracle {r_orc:.2e}")
         assert (eu <= 1e-9 and eq <= 1e-9) or r_gpu <= 10.0 * max(r_orc, 1e-13), (w, eu, r_gpu, r_orc)
+
+
+@pytest.mark.parametrize("per_world", [2, 4])
+def test_sparse_beyond_the_dense_limit(K, per_world):
+    """Worlds of 2 and 4 standing bipeds (408 and 816 rows: beyond the 288 padded rows the dense
+    formulation's matrix can hold, which refuses them): one actuated FP32 sparse step to 1e-8 against
+    the oracle's sparse formulation under the contact-world criterion (2 and 4 units per thread)."""
+    ws = wg.make_biped_team(num_worlds=2, seed=3, per_world=per_world)
+    with pytest.raises(K.KaminoError) as err:
+        K.Model(ws, "fp32", K.make_params(rho=0.1))
+    assert err.value.status == 7
+    q, u = rnd(ws.body_q0), rnd(ws.body_u0)
+    assert _margin_clear(None, ws, q)
+    lines = _biped_parity(K, ws, q, u, wg.actuation(ws, 3, 0), 2e-3, "fp32", pkw=dict(cr_iters=CR),
+                          okw=dict(cr_iters=CR))
+    assert len(lines) == 2

@@ -23,6 +23,6 @@ Conventions (shared by every consumer of a ``WorldSet``):
 from .worlds import (  # noqa: F401
     JOINT_REVOLUTE, JOINT_PRISMATIC, JOINT_UNIVERSAL, JOINT_SPHERICAL, JOINT_FIXED,
     JOINT_ROWS, TERRAIN_NONE, TERRAIN_PLANE, TERRAIN_HEIGHTFIELD, DRIVE_TORQUE, DRIVE_PD,
-    WorldSet, concat, with_joint_drives, with_joint_limits, make_pendulum, make_free_body, make_box, make_fourbar, make_biped, make_biped_heightfield,
+    WorldSet, concat, with_joint_drives, with_joint_limits, make_pendulum, make_free_body, make_box, make_fourbar, make_biped, make_biped_heightfield, make_biped_team,
     make_stewart, make_excavator, make_heightfield, actuation, count_loops,
 )

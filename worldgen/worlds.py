@@ -25,6 +25,7 @@ DRIVE_TORQUE, DRIVE_PD = 0, 1
 
 # world-type tags (used for the stream key and for per-type bookkeeping)
 KIND_PIN, KIND_FOURBAR, KIND_BIPED, KIND_STEWART, KIND_EXCAVATOR = 0, 1, 2, 3, 4
+KIND_BIPED_TEAM = 5
 
 
 @dataclass
@@ -483,6 +484,36 @@ def make_biped(num_worlds=4096, seed=0, terrain=None, foot_points="corners", z_l
     worlds = [_biped_world(_rng(seed, KIND_BIPED, w), foot_points=foot_points, z_lift=z_lift)
               for w in range(num_worlds)]
     return _assemble(worlds, terrain=terrain or {"kind": TERRAIN_PLANE})
+
+
+def _biped_team_world(seed, w, per_world, spacing=1.0):
+    """``per_world`` bipeds side by side (x offsets of ``spacing`` m) in one world: one large system
+    of independent mechanisms (31 k bodies, 180 k joint rows, 16 k foot-corner candidates).  Each
+    biped is drawn from its own stream; the world keeps the first one's friction."""
+    team = _World(KIND_BIPED_TEAM)
+    for i in range(per_world):
+        wd = _biped_world(_rng(seed, KIND_BIPED_TEAM, per_world * w + i))
+        if i == 0:
+            team.mu = wd.mu
+        nb0, act0 = len(team.bodies), team.n_act
+        for (m, inertia, pos, quat, v, om) in wd.bodies:
+            team.bodies.append((m, inertia, pos + np.array([spacing * i, 0.0, 0.0]), quat, v, om))
+        for (jt, par, ch, fp, fc, act) in wd.joints:
+            # every biped joint joins two of its own bodies (the pelvis floats), so the body-local
+            # frames move with the bodies
+            assert par >= 0
+            team.joints.append((jt, par + nb0, ch + nb0, fp, fc, act + act0 if act >= 0 else -1))
+        for (b, pt) in wd.contacts:
+            team.contacts.append((b + nb0, pt))
+        team.n_act += wd.n_act
+    return team
+
+
+def make_biped_team(num_worlds=1024, seed=0, per_world=2):
+    """Large worlds for the sparse formulation: ``per_world`` closed-loop bipeds standing side by side
+    in every world (2: 62 bodies, 360 joint rows, up to 456 rows; 4: up to 912 rows), on the plane."""
+    worlds = [_biped_team_world(seed, w, per_world) for w in range(num_worlds)]
+    return _assemble(worlds, terrain={"kind": TERRAIN_PLANE})
 
 
 def make_biped_heightfield(num_worlds=16384, seed=0, hmax=0.05):
