@@ -701,3 +701,29 @@ def test_longest_first_schedule_changes_no_result(K):
         runs.append((st.body_q.cpu(), st.body_u.cpu(), st.cache.cpu(), st.residual_raw.cpu()))
     for a, b in zip(*runs):
         assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("cr", [0, 9])
+def test_reported_residuals_and_iterations_match_the_oracle(K, cr):
+    """The per-world report against the oracle's own, FP64, 64 four-bars from one state, both run to
+    1e-10: the iteration counts agree within 2 (the same Alg. 1 in the same order; the GPU's explicit
+    inverse with refinement reaches the same iterates up to rounding), and the reported r_p, r_d, r_c
+    are below tol and, in the worlds that stop at the same iteration, within a factor 10 of the
+    oracle's (or both below 1e-14)."""
+    ws = wg.make_fourbar(num_worlds=64, seed=5)
+    dt, tol = 1e-3, 1e-10
+    q, u = rnd(ws.body_q0, "fp64"), rnd(ws.body_u0, "fp64")
+    _, _, rep, _ = gpu_step(K, ws, q, u, None, dt, 20000, tol, "fp64", cr_iters=cr)
+    _, infos = oracle_step(ws, q, u, None, dt, eps=tol, cr_iters=cr or None)
+    it_o = np.array([i.iterations for i in infos])
+    print("iterations gpu - oracle:", np.unique(rep["iterations"] - it_o, return_counts=True))
+    assert np.all(rep["status"] == 0) and all(i.converged for i in infos)
+    assert np.all(np.abs(rep["iterations"] - it_o) <= 2)
+    same = rep["iterations"] == it_o
+    assert same.sum() >= 1
+    for key, attr in (("r_primal", "r_p"), ("r_dual", "r_d"), ("r_compl", "r_c")):
+        g = rep[key].astype(np.float64)
+        o = np.array([getattr(i, attr) for i in infos])
+        assert np.all(g < tol)
+        ok = (g <= 10.0 * o + 1e-14) & (o <= 10.0 * g + 1e-14)
+        assert np.all(ok[same]), (key, g[same & ~ok], o[same & ~ok])
