@@ -1071,7 +1071,7 @@ __device__ __forceinline__ void unstash_rows(const Group &g, int nunits, int nbi
 // set, is the FP64 iterate block (x, y, z, y^, z^ of mp each) that takes over from this commit on.
 template <typename V, typename T, int S>
 __device__ __forceinline__ void owner_commit(const Group &g, int nunits, int nbil, V *y, V *z, V *yh, V *zh,
-                                             const double *vfd, const T *mut, T eta_, T rho_,
+                                             const double *vfd, const T (&vfo)[S][3], const T *mut, T eta_, T rho_,
                                              bool nesterov, bool restart, T beta_, const V (&xnew)[S][3],
                                              const V (&ynew)[S][3], const V (&znew)[S][3], bool hp, T *bb, double *bbd,
                                              double *init64, int mp) {
@@ -1133,7 +1133,7 @@ __device__ __forceinline__ void owner_commit(const Group &g, int nunits, int nbi
 #pragma unroll
             for (int t = 0; t < 3; ++t) {
                 if (t >= cnt) break;
-                bb[r0 + t] = T(V(vfd[r0 + t]) + (t == 2 ? sv : V(0)) - eta * xnew[sl][t] - rho * yhv[t] - zhv[t]);
+                bb[r0 + t] = T(V(vfo[sl][t]) + (t == 2 ? sv : V(0)) - eta * xnew[sl][t] - rho * yhv[t] - zhv[t]);
             }
         }
     }
@@ -2211,7 +2211,41 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
         bool x_in64 = false; // the last owner update wrote x to the FP64 vector
         int LB = 8;          // lanes per body in the gather: a power of two with LB * nb <= group size
         while (LB > 1 && LB * nb > nthr) LB >>= 1;
+        // Loop invariants in registers, so that an iteration's loads depend on nothing but the
+        // iterates: the row codes of this gather lane (when one pass covers the bodies and the lane
+        // has at most kGatherRows rows; gcnt < 0 otherwise) and, for the residual row r = tid, its
+        // bodies, its scaling and its diagonal shift + p^2 R.
+        constexpr int kGatherRows = 6;
+        int gcode[kGatherRows];
+        int gcnt = -1;
+        g.sync();            // the row lists are complete (each body's list is written by one thread)
+        if (nb * LB <= nthr) {
+            const int body = tid / LB, sub = tid - body * LB;
+            const int e0 = tid < nb * LB ? bro[body] + sub : 0, e1 = tid < nb * LB ? bro[body + 1] : 0;
+            const int n = e1 > e0 ? (e1 - e0 + LB - 1) / LB : 0;
+#pragma unroll
+            for (int k = 0; k < kGatherRows; ++k) gcode[k] = k < n ? brow[e0 + k * LB] : 0;
+            gcnt = n <= kGatherRows ? n : -1;
+        }
+        int rsa = -1, rsb = -1;
+        T rpr = T(0), rdiag = T(0);
+        if (tid < m) {
+            rsa = rbody[2 * tid];
+            rsb = rbody[2 * tid + 1];
+            rpr = p[tid];
+            rdiag = shift + p[tid] * p[tid] * rreg[tid];
+        }
         T acc_a = T(1), c_prev = T(INFINITY);
+        // v_f of the owner's rows in the iteration's precision, in registers for the whole loop (the
+        // conversion from the FP64 v_f would otherwise run on the slow FP64 pipe every iteration)
+        T vfo[S][3];
+#pragma unroll
+        for (int sl = 0; sl < S; ++sl) {
+            const int u = tid + sl * nthr;
+            const int r0 = u < nbil ? u : nbil + 3 * (u - nbil), cnt = u >= nunits ? 0 : u < nbil ? 1 : 3;
+#pragma unroll
+            for (int t = 0; t < 3; ++t) vfo[sl][t] = t < cnt ? T(vfd[r0 + t]) : T(0);
+        }
         // b = v_f + Gamma(z^) - eta x - rho y^ - z^ and w = P x for the first iteration
         for (int u = tid; u < nunits; u += nthr) {
             if (u < nbil) {
@@ -2269,7 +2303,18 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
                     }
                 } else {
                     T f[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
-                    if (on) {
+                    if (gcnt >= 0) {
+    #pragma unroll
+                        for (int q = 0; q < kGatherRows; ++q) {
+                            if (q >= gcnt) break;
+                            const int code = gcode[q];
+                            const T w = wv[code >> 1];
+                            T Jv[6];
+                            load6(rJ + 6 * code, Jv);
+    #pragma unroll
+                            for (int k = 0; k < 6; ++k) f[k] = fma(Jv[k], w, f[k]);
+                        }
+                    } else if (on) {
                         for (int e = bro[body] + sub; e < bro[body + 1]; e += LB) {
                             const int code = brow[e];
                             const T w = wv[code >> 1];
@@ -2295,7 +2340,8 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
             // the row's owner before the last barrier), stored as the BF16 hi / lo split (mixed, inverse
             // in shared memory) or in bb (tensor-memory, FP32 and FP64 mat-vecs)
             for (int r = tid; r < m; r += nthr) {
-                const int sa = rbody[2 * r], sb = rbody[2 * r + 1];
+                const bool own = r == tid;
+                const int sa = own ? rsa : rbody[2 * r], sb = own ? rsb : rbody[2 * r + 1];
                 const T *J = rJ + 12 * r;
                 T c;
                 if (hp) {
@@ -2324,7 +2370,7 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
     #pragma unroll
                         for (int k = 0; k < 6; ++k) acc = fma(Jv[k], gv[k], acc);
                     }
-                    c = bb[r] + p[r] * acc + (shift + p[r] * p[r] * rreg[r]) * x[r];
+                    c = own ? bb[r] + rpr * acc + rdiag * x[r] : bb[r] + p[r] * acc + (shift + p[r] * p[r] * rreg[r]) * x[r];
                 }
                 if (a.mixed && !tm) {
                     const float v = (float)c;
@@ -2387,12 +2433,12 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
                 unstash_rows<S>(g, nunits, nbil, x64, xnD);
                 unstash_rows<S>(g, nunits, nbil, yn64, ynD);
                 unstash_rows<S>(g, nunits, nbil, zn64, znD);
-                owner_commit<double, T, S>(g, nunits, nbil, y64, z64, yh64, zh64, vfd, mut, eta, rho, a.nesterov != 0,
+                owner_commit<double, T, S>(g, nunits, nbil, y64, z64, yh64, zh64, vfd, vfo, mut, eta, rho, a.nesterov != 0,
                                            restart, beta_n, xnD, ynD, znD, true, bb, bbd, nullptr, mp);
             } else {
                 // the iterates move to the FP64 vectors at this commit once the end game has started
                 double *init = hp && x64 != nullptr ? x64 : nullptr;
-                owner_commit<T, T, S>(g, nunits, nbil, y, z, yh, zh, vfd, mut, eta, rho, a.nesterov != 0, restart,
+                owner_commit<T, T, S>(g, nunits, nbil, y, z, yh, zh, vfd, vfo, mut, eta, rho, a.nesterov != 0, restart,
                                       beta_n, xnT, ynT, znT, hp, bb, bbd, init, mp);
                 hpv = init != nullptr;
             }
