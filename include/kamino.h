@@ -111,6 +111,16 @@ typedef struct {
                         * leaves u+ (nearly) fixed.  Reported as KAMINO_WORLD_STALLED. */
     int32_t schedule;  /* KAMINO_SCHEDULE_*: order in which the one-CTA-per-world launch takes the
                         * worlds (results do not depend on it; every world is independent) */
+    int32_t residual_every; /* dense formulation: every PADMM x-step is one refinement step
+                        * x^i = x^{i-1} - A^-1 c with the swept (reduced-precision) inverse.
+                        * 0 or 1: c = b^i + A x^{i-1}, the residual evaluated matrix-free from the
+                        * rows in every iteration.  K >= 2: evaluated in iterations 1, K+1, 2K+1, ...
+                        * and in every iteration of the FP64 end game; the others take
+                        * c = b^i - b^{i-1}, which equals the residual when the previous x-step was
+                        * solved exactly.  What the reduced-precision inverse leaves is corrected
+                        * at the next evaluated iteration, so the fixed point is the same; the
+                        * skipped iterations save the per-body gather, the residual rows and one
+                        * barrier.  Ignored by the sparse formulation. */
 } kamino_solver_params;
 
 /* IN_ORDER: world w in CTA w.  LONGEST_FIRST: before each step a one-CTA kernel orders the worlds by

@@ -59,6 +59,8 @@ kamino_status check_params(const kamino_solver_params &p) {
     if (p.integrator != KAMINO_INTEGRATOR_EULER && p.integrator != KAMINO_INTEGRATOR_MIDPOINT)
         return fail(KAMINO_E_INVALID_ARG, "params.integrator %d is not a KAMINO_INTEGRATOR_* value", p.integrator);
     if (p.stall_window < 0) return fail(KAMINO_E_INVALID_ARG, "params.stall_window must be >= 0");
+    if (p.residual_every < 0 || p.residual_every > 1024)
+        return fail(KAMINO_E_INVALID_ARG, "params.residual_every must be in [0, 1024]");
     if (p.schedule != KAMINO_SCHEDULE_IN_ORDER && p.schedule != KAMINO_SCHEDULE_LONGEST_FIRST)
         return fail(KAMINO_E_INVALID_ARG, "params.schedule %d is not a KAMINO_SCHEDULE_* value", p.schedule);
     if (p.cr_iters < 0 || p.cr_iters > KAMINO_MAX_CR_ITERS)
@@ -331,6 +333,7 @@ StepArgs<T> make_args(kamino_state_s *st, double dt, int iters, double tol, cons
     a.cr_iters = m->params.cr_iters;
     a.ncp_stop = m->params.ncp_stop ? 1 : 0;
     a.stall_window = m->params.ncp_stop ? m->params.stall_window : 0;
+    a.residual_every = m->params.residual_every > 1 ? m->params.residual_every : 1;
     // the inverse may live in tensor memory when a world's shared memory keeps a second CTA off the SM
     // (the 512-column allocation then never waits for another CTA); the sparse formulation has none
     a.tmem = (sizeof(T) == 4 && a.cr_iters == 0 && m->mp_max <= 256 && m->smem > kMaxSmem / 2) ? 1 : 0;

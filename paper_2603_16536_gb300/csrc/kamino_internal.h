@@ -64,6 +64,7 @@ struct StepArgs {
     int cr_iters;              // 0: dense formulation; k >= 1: sparse formulation, k CR iterations per x-step
     int ncp_stop;              // 1: converged also requires the natural-map NCP residual below tol
     int stall_window;          // > 0: the stall exit every stall_window iterations (dense formulation)
+    int residual_every;        // >= 1: the refinement residual evaluated every residual_every iterations
     int tmem;                  // 1: keep the swept inverse in tensor memory (FP32, whole-CTA groups, mp <= 256)
     // shared-memory layout bounds (maxima over the launched worlds)
     int nb_max, nj_max, nc_max, mp_max, nl_max;

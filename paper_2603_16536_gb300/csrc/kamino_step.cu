@@ -514,30 +514,64 @@ __device__ __forceinline__ void tmem_ld32(uint32_t t, uint32_t (&v)[32]) {
                  : "r"(t) : "memory");
 }
 
+// Waits for this thread's outstanding tensor-memory loads; the registers of the block about to be
+// used are tied to the wait, so no use of them can be scheduled before it.
+__device__ __forceinline__ void tmem_wait_ld32(uint32_t (&v)[32]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]), "+r"(v[7]),
+                   "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]), "+r"(v[12]), "+r"(v[13]), "+r"(v[14]), "+r"(v[15]),
+                   "+r"(v[16]), "+r"(v[17]), "+r"(v[18]), "+r"(v[19]), "+r"(v[20]), "+r"(v[21]), "+r"(v[22]), "+r"(v[23]),
+                   "+r"(v[24]), "+r"(v[25]), "+r"(v[26]), "+r"(v[27]), "+r"(v[28]), "+r"(v[29]), "+r"(v[30]), "+r"(v[31])
+                 :: "memory");
+}
+
+// 32 columns of a row against c (broadcast float4 loads from shared memory), as packed FP32 FMAs on
+// two pairs of partial sums: (a0.x, a0.y, a1.x, a1.y) collect the columns 0, 1, 2, 3 mod 4.
+__device__ __forceinline__ void ffma32(const uint32_t (&v)[32], const float *c, float2 &a0, float2 &a1) {
+    const float4 *cp = reinterpret_cast<const float4 *>(c);
+#pragma unroll
+    for (int q = 0; q < 32; q += 4) {
+        const float4 cc = cp[q / 4];
+        a0 = __ffma2_rn(make_float2(__uint_as_float(v[q]), __uint_as_float(v[q + 1])), make_float2(cc.x, cc.y), a0);
+        a1 = __ffma2_rn(make_float2(__uint_as_float(v[q + 2]), __uint_as_float(v[q + 3])), make_float2(cc.z, cc.w), a1);
+    }
+}
+
+// y = S c with S in tensor memory: lane = row, blocks of 32 columns, the load of the next block in
+// flight while the current one is multiplied (two register blocks), c broadcast from shared memory.
 __device__ void tmem_matvec(uint32_t tbase, int mp, const float *c, float *y, const Group &g) {
     const int warp = g.warp(), lane = g.lane();
     const int ch = warp >> 2;
     const int row = 128 * ch + 32 * (warp & 3) + lane;
     if (128 * ch < mp) {
         const uint32_t t = tbase + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(256 * ch);
-        float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
-        int b = 0;
-        for (; b + 32 <= mp; b += 32) {                       // 32 columns per load
-            uint32_t v[32];
-            tmem_ld32(t + (uint32_t)b, v);
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            const uint32_t (&v0)[16] = *reinterpret_cast<const uint32_t (*)[16]>(&v[0]);
-            const uint32_t (&v1)[16] = *reinterpret_cast<const uint32_t (*)[16]>(&v[16]);
-            fma16(v0, c + b, a0, a1, a2, a3);
-            fma16(v1, c + b + 16, a0, a1, a2, a3);
+        float2 a0 = make_float2(0.0f, 0.0f), a1 = make_float2(0.0f, 0.0f);
+        const int nblk = mp >> 5;                              // whole blocks of 32 columns
+        uint32_t va[32], vb[32];
+        if (nblk > 0) tmem_ld32(t, va);
+        int k = 0;
+        for (; k + 2 <= nblk; k += 2) {
+            tmem_wait_ld32(va);
+            tmem_ld32(t + (uint32_t)(32 * (k + 1)), vb);
+            ffma32(va, c + 32 * k, a0, a1);
+            tmem_wait_ld32(vb);
+            if (k + 2 < nblk) tmem_ld32(t + (uint32_t)(32 * (k + 2)), va);
+            ffma32(vb, c + 32 * (k + 1), a0, a1);
         }
-        if (b < mp) {                                          // mp = 16 mod 32
+        if (k < nblk) {
+            tmem_wait_ld32(va);
+            ffma32(va, c + 32 * k, a0, a1);
+        }
+        if (mp & 16) {                                         // mp = 16 mod 32
             uint32_t v[16];
-            tmem_ld16(t + (uint32_t)b, v);
+            tmem_ld16(t + (uint32_t)(32 * nblk), v);
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            fma16(v, c + b, a0, a1, a2, a3);
+            float b0 = a0.x, b1 = a0.y, b2 = a1.x, b3 = a1.y;
+            fma16(v, c + 32 * nblk, b0, b1, b2, b3);
+            a0 = make_float2(b0, b1);
+            a1 = make_float2(b2, b3);
         }
-        if (row < mp) y[row] = (a0 + a1) + (a2 + a3);
+        if (row < mp) y[row] = (a0.x + a0.y) + (a1.x + a1.y);
     }
     g.sync();
 }
@@ -1069,12 +1103,17 @@ __device__ __forceinline__ void unstash_rows(const Group &g, int nunits, int nbi
 // (y^, z^) (Sec. 4.1), the new y, z, y^, z^, and the next iteration's right-hand side
 // b = v_f + Gamma(z^) - eta x - rho y^ - z^ (in FP64 from the FP64 v_f when `hp`).  `init64`, when
 // set, is the FP64 iterate block (x, y, z, y^, z^ of mp each) that takes over from this commit on.
+// With `lag` the next iteration does not evaluate the refinement residual: the owners store its
+// correction's right-hand side c = b^{i+1} - b^i directly (in bb, or as the BF16 hi / lo split when
+// chi is set), which is b^{i+1} + A x^i when x^i solved A x = -b^i exactly.  `bprev` carries this
+// thread's b from commit to commit (FP32 path).
 template <typename V, typename T, int S>
 __device__ __forceinline__ void owner_commit(const Group &g, int nunits, int nbil, V *y, V *z, V *yh, V *zh,
                                              const double *vfd, const T (&vfo)[S][3], const T *mut, T eta_, T rho_,
                                              bool nesterov, bool restart, T beta_, const V (&xnew)[S][3],
                                              const V (&ynew)[S][3], const V (&znew)[S][3], bool hp, T *bb, double *bbd,
-                                             double *init64, int mp) {
+                                             double *init64, int mp, bool lag, T (&bprev)[S][3],
+                                             __nv_bfloat16 *chi, __nv_bfloat16 *clo) {
     const V beta_n = V(beta_);
 #pragma unroll
     for (int sl = 0; sl < S; ++sl) {
@@ -1133,7 +1172,18 @@ __device__ __forceinline__ void owner_commit(const Group &g, int nunits, int nbi
 #pragma unroll
             for (int t = 0; t < 3; ++t) {
                 if (t >= cnt) break;
-                bb[r0 + t] = T(V(vfo[sl][t]) + (t == 2 ? sv : V(0)) - eta * xnew[sl][t] - rho * yhv[t] - zhv[t]);
+                const T bn = T(V(vfo[sl][t]) + (t == 2 ? sv : V(0)) - eta * xnew[sl][t] - rho * yhv[t] - zhv[t]);
+                if (!lag) {
+                    bb[r0 + t] = bn;
+                } else if (chi == nullptr) {
+                    bb[r0 + t] = bn - bprev[sl][t];
+                } else {
+                    const float v = (float)(bn - bprev[sl][t]);
+                    const __nv_bfloat16 h = __float2bfloat16(v);
+                    chi[r0 + t] = h;
+                    clo[r0 + t] = __float2bfloat16(v - __bfloat162float(h));
+                }
+                bprev[sl][t] = bn;
             }
         }
     }
@@ -2266,6 +2316,18 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
                 clo[r] = __float2bfloat16(0.0f);
             }
         }
+        // this thread's b of the coming iteration (its own rows, written just above), for the
+        // iterations that take c = b^i - b^{i-1} (residual_every > 1)
+        T bprev[S][3];
+#pragma unroll
+        for (int sl = 0; sl < S; ++sl) {
+            const int u = tid + sl * nthr;
+            const int r0 = u < nbil ? u : nbil + 3 * (u - nbil), cnt = u >= nunits ? 0 : u < nbil ? 1 : 3;
+#pragma unroll
+            for (int t = 0; t < 3; ++t) bprev[sl][t] = t < cnt ? bb[r0 + t] : T(0);
+        }
+        const int kres = a.residual_every;
+        bool lagged = false;     // this iteration takes c = b^i - b^{i-1} (stored by the last commit)
         g.sync();
         // The iterations run until Sec. 4.1's test passes; with ncp_stop the natural-map check follows
         // outside the loop (kept out of the loop body, which it would otherwise make slower) and the
@@ -2275,6 +2337,10 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
         T *ust = (T *)(smem + L.ust);
         for (;;) {
         for (; it <= a.iters; ++it) {
+            if (lagged) {
+                // c = b^i - b^{i-1} was stored by the owners' commit: publish it to the mat-vec
+                g.sync();
+            } else {
             // [8a] per body: g_b = M_b^-1 sum over the body's rows r of J_rb^T (P x)_r; LB lanes per
             // body take its rows round-robin, then a shuffle reduction
             for (int base = 0; base < nb * LB; base += nthr) {
@@ -2382,6 +2448,7 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
                 }
             }
             g.sync();
+            }
             // [8c] correction: xn = S c with S = -A^-1, so x^i = x^{i-1} + xn (ends with a barrier)
             bool done_c = false;
             if constexpr (sizeof(T) == 4) {
@@ -2428,18 +2495,23 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
                     c_prev = c_prev / T(0.999);
                 }
             }
+            // the next iteration evaluates the refinement residual in iterations 1, K+1, 2K+1, ... and
+            // throughout the FP64 end game; the others take c = b^{i+1} - b^i
+            lagged = kres > 1 && !hp && it % kres != 0;
             if (hpv) {
                 double xnD[S][3], ynD[S][3], znD[S][3];
                 unstash_rows<S>(g, nunits, nbil, x64, xnD);
                 unstash_rows<S>(g, nunits, nbil, yn64, ynD);
                 unstash_rows<S>(g, nunits, nbil, zn64, znD);
                 owner_commit<double, T, S>(g, nunits, nbil, y64, z64, yh64, zh64, vfd, vfo, mut, eta, rho, a.nesterov != 0,
-                                           restart, beta_n, xnD, ynD, znD, true, bb, bbd, nullptr, mp);
+                                           restart, beta_n, xnD, ynD, znD, true, bb, bbd, nullptr, mp, false, bprev,
+                                           nullptr, nullptr);
             } else {
                 // the iterates move to the FP64 vectors at this commit once the end game has started
                 double *init = hp && x64 != nullptr ? x64 : nullptr;
                 owner_commit<T, T, S>(g, nunits, nbil, y, z, yh, zh, vfd, vfo, mut, eta, rho, a.nesterov != 0, restart,
-                                      beta_n, xnT, ynT, znT, hp, bb, bbd, init, mp);
+                                      beta_n, xnT, ynT, znT, hp, bb, bbd, init, mp, lagged, bprev,
+                                      a.mixed && !tm ? chi : nullptr, clo);
                 hpv = init != nullptr;
             }
             if (converged) break;

@@ -34,7 +34,7 @@ class SolverParams(C.Structure):
     _fields_ = [("eta", C.c_double), ("rho", C.c_double), ("beta", C.c_double), ("margin", C.c_double),
                 ("nesterov", C.c_int32), ("precond", C.c_int32), ("warm_mode", C.c_int32), ("refine64", C.c_int32),
                 ("integrator", C.c_int32), ("cr_iters", C.c_int32), ("ncp_stop", C.c_int32),
-                ("stall_window", C.c_int32), ("schedule", C.c_int32)]
+                ("stall_window", C.c_int32), ("schedule", C.c_int32), ("residual_every", C.c_int32)]
 
 
 INTEGRATOR_EULER, INTEGRATOR_MIDPOINT = 0, 1
@@ -42,10 +42,12 @@ INTEGRATOR_EULER, INTEGRATOR_MIDPOINT = 0, 1
 
 def make_params(eta=1e-6, rho=0.1, beta=0.2, margin=0.005, nesterov=True, precond=True, warm_mode=WARM_COLD,
                 refine64=True, integrator=INTEGRATOR_EULER, cr_iters=0, ncp_stop=False, stall_window=0,
-                schedule=1):
-    """Solver parameters (kamino_solver_params); ``schedule`` 1 = KAMINO_SCHEDULE_LONGEST_FIRST."""
+                schedule=1, residual_every=4):
+    """Solver parameters (kamino_solver_params); ``schedule`` 1 = KAMINO_SCHEDULE_LONGEST_FIRST;
+    ``residual_every`` 4 = the dense x-step's refinement residual evaluated every 4th iteration."""
     return SolverParams(eta, rho, beta, margin, int(nesterov), int(precond), int(warm_mode), int(refine64),
-                        int(integrator), int(cr_iters), int(ncp_stop), int(stall_window), int(schedule))
+                        int(integrator), int(cr_iters), int(ncp_stop), int(stall_window), int(schedule),
+                        int(residual_every))
 
 
 _P = C.c_void_p

@@ -100,3 +100,67 @@ def test_the_rounded_inverse_alone_is_not_the_solution():
     u_kkt, _ = A.kkt_direct(J, M, M @ uf, B["v_star"])
     u = uf + Minv @ (J.T @ (p * y))
     assert np.abs(u - u_kkt).max() / max(np.abs(u_kkt).max(), 9.81 * 2e-3) > 1e-4
+
+
+def _lagged_x_step(S, Amat, every):
+    """The x-step of the kernel with ``residual_every`` = every: the refinement residual b + A x is
+    evaluated matrix-free in iterations 1, every + 1, 2 every + 1, ...; the others take
+    c = b^i - b^{i-1}, which is that residual whenever the previous x-step solved A x = -b exactly."""
+    state = {"it": 0, "b_prev": None}
+
+    def step(b, x):
+        state["it"] += 1
+        if (state["it"] - 1) % every == 0:
+            c = b + Amat @ x
+        else:
+            c = b - state["b_prev"]
+        state["b_prev"] = b
+        return x - S @ c
+    return step
+
+
+@pytest.mark.parametrize("maker,dt", [(wg.make_fourbar, 1e-3), (wg.make_stewart, 2e-3), (wg.make_biped, 2e-3)])
+def test_lagged_refinement_residual_keeps_the_fixed_point(maker, dt):
+    """Evaluating the refinement residual only every 4th iteration (c = b^i - b^{i-1} in between)
+    with the TF32- or BF16-rounded inverse: the error the rounded inverse leaves in the skipped
+    iterations is corrected at the next evaluated one, so the iteration reaches the exact x-step's
+    solution (direct KKT solve without contacts, the NCP conditions with them) in the same number of
+    iterations."""
+    B, Ds, vs, p, mus = _problem(maker, dt)
+    J, Minv, uf, nbil = B["J"], B["Minv"], B["u_free"], B["n_bilateral"]
+    eta, rho = 1e-6, 0.1
+    Amat = Ds + (eta + rho) * np.eye(len(vs))
+    Ainv = np.linalg.inv(Amat)
+    y_ref, it_ref, conv = _padmm_x_step(Ds, vs, nbil, mus, eta, rho, 1e-12, 50000, lambda b, x: -Ainv @ b)
+    assert conv
+    u_ref = uf + Minv @ (J.T @ (p * y_ref))
+    scale = max(np.abs(u_ref).max(), 9.81 * dt)
+    for bits in (10, 7):
+        S = _round_mantissa(Ainv, bits)
+        y, it, conv = _padmm_x_step(Ds, vs, nbil, mus, eta, rho, 1e-12, 50000, _lagged_x_step(S, Amat, 4))
+        assert conv, bits
+        assert abs(it - it_ref) <= 0.05 * it_ref + 2, (bits, it, it_ref)
+        lam = p * y
+        u = uf + Minv @ (J.T @ lam)
+        if B["contact_ids"]:
+            assert max(A.ncp_residual(J, u, B["v_star"], lam, p, nbil, B["mu"])) < 1e-10, bits
+        else:
+            M = np.linalg.inv(Minv)
+            u_kkt, _ = A.kkt_direct(J, M, M @ uf, B["v_star"])
+            assert np.abs(u - u_kkt).max() / scale < 1e-8, bits
+            assert np.abs(u - u_ref).max() / scale < 1e-9, bits
+
+
+def test_lagged_residual_without_evaluation_drifts():
+    """Planted mistake for the test above: never evaluating the residual (c = b^i - b^{i-1} in every
+    iteration after the first) lets the BF16 inverse's error accumulate, and the bilateral Stewart
+    platform's u+ leaves the direct KKT solution."""
+    B, Ds, vs, p, mus = _problem(wg.make_stewart, 2e-3)
+    J, Minv, uf, nbil = B["J"], B["Minv"], B["u_free"], B["n_bilateral"]
+    Amat = Ds + (1e-6 + 0.1) * np.eye(len(vs))
+    S = _round_mantissa(np.linalg.inv(Amat), 7)
+    y, _, _ = _padmm_x_step(Ds, vs, nbil, mus, 1e-6, 0.1, 1e-12, 5000, _lagged_x_step(S, Amat, 10 ** 9))
+    M = np.linalg.inv(Minv)
+    u_kkt, _ = A.kkt_direct(J, M, M @ uf, B["v_star"])
+    u = uf + Minv @ (J.T @ (p * y))
+    assert np.abs(u - u_kkt).max() / max(np.abs(u_kkt).max(), 9.81 * 2e-3) > 1e-4
