@@ -120,7 +120,8 @@ typedef struct {
                         * solved exactly.  What the reduced-precision inverse leaves is corrected
                         * at the next evaluated iteration, so the fixed point is the same; the
                         * skipped iterations save the per-body gather, the residual rows and one
-                        * barrier.  Ignored by the sparse formulation. */
+                        * barrier.  K is capped at 4 where the inverse is held as BF16 tiles (mixed
+                        * precision beyond tensor memory).  Ignored by the sparse formulation. */
 } kamino_solver_params;
 
 /* IN_ORDER: world w in CTA w.  LONGEST_FIRST: before each step a one-CTA kernel orders the worlds by

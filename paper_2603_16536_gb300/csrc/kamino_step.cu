@@ -537,8 +537,8 @@ __device__ __forceinline__ void ffma32(const uint32_t (&v)[32], const float *c, 
     }
 }
 
-// y = S c with S in tensor memory: lane = row, blocks of 32 columns, the load of the next block in
-// flight while the current one is multiplied (two register blocks), c broadcast from shared memory.
+// y = S c with S in tensor memory: lane = row, 32 columns per load, c broadcast from shared memory,
+// packed FP32 FMAs on four partial sums.
 __device__ void tmem_matvec(uint32_t tbase, int mp, const float *c, float *y, const Group &g) {
     const int warp = g.warp(), lane = g.lane();
     const int ch = warp >> 2;
@@ -547,20 +547,11 @@ __device__ void tmem_matvec(uint32_t tbase, int mp, const float *c, float *y, co
         const uint32_t t = tbase + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(256 * ch);
         float2 a0 = make_float2(0.0f, 0.0f), a1 = make_float2(0.0f, 0.0f);
         const int nblk = mp >> 5;                              // whole blocks of 32 columns
-        uint32_t va[32], vb[32];
-        if (nblk > 0) tmem_ld32(t, va);
-        int k = 0;
-        for (; k + 2 <= nblk; k += 2) {
-            tmem_wait_ld32(va);
-            tmem_ld32(t + (uint32_t)(32 * (k + 1)), vb);
-            ffma32(va, c + 32 * k, a0, a1);
-            tmem_wait_ld32(vb);
-            if (k + 2 < nblk) tmem_ld32(t + (uint32_t)(32 * (k + 2)), va);
-            ffma32(vb, c + 32 * (k + 1), a0, a1);
-        }
-        if (k < nblk) {
-            tmem_wait_ld32(va);
-            ffma32(va, c + 32 * k, a0, a1);
+        for (int k = 0; k < nblk; ++k) {
+            uint32_t v[32];
+            tmem_ld32(t + (uint32_t)(32 * k), v);
+            tmem_wait_ld32(v);
+            ffma32(v, c + 32 * k, a0, a1);
         }
         if (mp & 16) {                                         // mp = 16 mod 32
             uint32_t v[16];
@@ -1003,6 +994,33 @@ __device__ __forceinline__ double *fp64_iterates(unsigned char *smem, const Layo
     }
 }
 
+// |(a, b)| in the iteration's precision: in FP32 from the hardware reciprocal square root (a few
+// ulp, no slow path), in FP64 the rounded square root.
+template <typename V>
+__device__ __forceinline__ V hypot2(V a, V b) {
+    const V s = a * a + b * b;
+    if constexpr (sizeof(V) == 4) return s > 0.0f ? s * rsqrtf(s) : 0.0f;
+    else return sqrt(s);
+}
+
+// Projection of v onto the Coulomb cone {|y_t| <= mu y_n} (Sec. 3), `mui` = 1 / (1 + mu^2): the three
+// cases of the closed form (inside: v; in the polar cone: 0; else onto the cone's surface) as
+// selects, so that the lanes of a warp do not diverge over them.  FP32 divides by the hardware
+// reciprocal.
+template <typename V>
+__device__ __forceinline__ void cone_project(const V (&v)[3], V mu, V mui, V (&y)[3]) {
+    const V tn = hypot2(v[0], v[1]);
+    const bool inside = tn <= mu * v[2], polar = mu * tn <= -v[2];
+    const V nn = (mu * tn + v[2]) * mui;
+    V sc;
+    if constexpr (sizeof(V) == 4) sc = __fdividef(mu * nn, tn);
+    else sc = mu * nn / tn;
+    // tn > 0 whenever neither case holds, so the quotient is used only where it is finite
+    y[0] = inside ? v[0] : polar ? V(0) : sc * v[0];
+    y[1] = inside ? v[1] : polar ? V(0) : sc * v[1];
+    y[2] = inside ? v[2] : polar ? V(0) : nn;
+}
+
 // Owner phase of a PADMM iteration (Alg. 1) for the units of this thread, with the iterates of type
 // V (T, or FP64 in the refinement end game): x^i = x^{i-1} + xn (the refined x-step),
 // y^i = Pi_K(x^i - z^/rho) (identity on joint rows, the Coulomb cone on contacts),
@@ -1045,16 +1063,7 @@ __device__ __forceinline__ void owner_update(const Group &g, int nunits, int nfi
                 xv[t] = x[r0 + t] + V(xn[r0 + t]);
                 v[t] = xv[t] - zh[r0 + t] * irho;
             }
-            const V tn = sqrt(v[0] * v[0] + v[1] * v[1]);
-            if (tn <= mu * v[2]) {
-                yv[0] = v[0]; yv[1] = v[1]; yv[2] = v[2];
-            } else if (mu * tn <= -v[2]) {
-                yv[0] = yv[1] = yv[2] = V(0);
-            } else {
-                const V nn = (mu * tn + v[2]) * V(mui[k]);
-                const V sc = mu * nn / tn;
-                yv[0] = sc * v[0]; yv[1] = sc * v[1]; yv[2] = nn;
-            }
+            cone_project<V>(v, mu, V(mui[k]), yv);
             V ydz = V(0);
 #pragma unroll
             for (int t = 0; t < 3; ++t) {
@@ -1168,7 +1177,7 @@ __device__ __forceinline__ void owner_commit(const Group &g, int nunits, int nbi
             }
         } else {
             const V eta = V(eta_), rho = V(rho_);
-            const V sv = cnt == 3 ? V(mu) * sqrt(zhv[0] * zhv[0] + zhv[1] * zhv[1]) : V(0);
+            const V sv = cnt == 3 ? V(mu) * hypot2(zhv[0], zhv[1]) : V(0);
 #pragma unroll
             for (int t = 0; t < 3; ++t) {
                 if (t >= cnt) break;
@@ -2326,7 +2335,9 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
 #pragma unroll
             for (int t = 0; t < 3; ++t) bprev[sl][t] = t < cnt ? bb[r0 + t] : T(0);
         }
-        const int kres = a.residual_every;
+        // BF16 inverse tiles (mixed mode outside tensor memory) are lagged 4 iterations at most: their
+        // larger error, accumulated over a longer lag, costs short solves iterations
+        const int kres = a.mixed && !tm ? min(a.residual_every, 4) : a.residual_every;
         bool lagged = false;     // this iteration takes c = b^i - b^{i-1} (stored by the last commit)
         g.sync();
         // The iterations run until Sec. 4.1's test passes; with ncp_stop the natural-map check follows
@@ -2475,6 +2486,11 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
                                       lrd, lrc, lc);
             }
             x_in64 = hpv;
+            // Nesterov's next coefficients and the next iteration's kind depend on nothing the
+            // reduction returns: formed before it
+            const T an_next = T(0.5) * (T(1) + sqrt(T(1) + T(4) * acc_a * acc_a));
+            const T beta_next = (acc_a - T(1)) / an_next;
+            const bool lag_due = kres > 1 && it % kres != 0;
             group_reduce4(lrp, lrd, lrc, lc, red, it & 1, g);
             rp = lrp; rd = lrd; rc = lrc;
             converged = rp < a.tol && rd < a.tol && rc < a.tol;
@@ -2485,9 +2501,8 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
             bool restart = false;
             if (a.nesterov) {
                 if (lc < T(0.999) * c_prev) {
-                    const T an = T(0.5) * (T(1) + sqrt(T(1) + T(4) * acc_a * acc_a));
-                    beta_n = (acc_a - T(1)) / an;
-                    acc_a = an;
+                    beta_n = beta_next;
+                    acc_a = an_next;
                     c_prev = lc;
                 } else {
                     restart = true;
@@ -2497,7 +2512,7 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
             }
             // the next iteration evaluates the refinement residual in iterations 1, K+1, 2K+1, ... and
             // throughout the FP64 end game; the others take c = b^{i+1} - b^i
-            lagged = kres > 1 && !hp && it % kres != 0;
+            lagged = lag_due && !hp;
             if (hpv) {
                 double xnD[S][3], ynD[S][3], znD[S][3];
                 unstash_rows<S>(g, nunits, nbil, x64, xnD);

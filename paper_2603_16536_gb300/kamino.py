@@ -42,9 +42,9 @@ INTEGRATOR_EULER, INTEGRATOR_MIDPOINT = 0, 1
 
 def make_params(eta=1e-6, rho=0.1, beta=0.2, margin=0.005, nesterov=True, precond=True, warm_mode=WARM_COLD,
                 refine64=True, integrator=INTEGRATOR_EULER, cr_iters=0, ncp_stop=False, stall_window=0,
-                schedule=1, residual_every=4):
+                schedule=1, residual_every=8):
     """Solver parameters (kamino_solver_params); ``schedule`` 1 = KAMINO_SCHEDULE_LONGEST_FIRST;
-    ``residual_every`` 4 = the dense x-step's refinement residual evaluated every 4th iteration."""
+    ``residual_every`` 8 = the dense x-step's refinement residual evaluated every 8th iteration."""
     return SolverParams(eta, rho, beta, margin, int(nesterov), int(precond), int(warm_mode), int(refine64),
                         int(integrator), int(cr_iters), int(ncp_stop), int(stall_window), int(schedule),
                         int(residual_every))
