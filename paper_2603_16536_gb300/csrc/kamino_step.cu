@@ -994,6 +994,14 @@ __device__ __forceinline__ double *fp64_iterates(unsigned char *smem, const Layo
     }
 }
 
+// The owners' slots: slot j = tid + s * group size of a thread holds unit slot_unit(j).  Joint rows
+// keep slot = unit; the contacts start at slot `cslot0`, the first warp boundary after the joint
+// rows when the slots have room (else right after them), so that no warp mixes the two kinds of
+// unit and their different owner phases.  Returns a value >= nunits for an empty slot.
+__device__ __forceinline__ int slot_unit(int j, int nbil, int cslot0) {
+    return j < nbil ? j : j >= cslot0 ? nbil + (j - cslot0) : 0x3fffffff;
+}
+
 // |(a, b)| in the iteration's precision: in FP32 from the hardware reciprocal square root (a few
 // ulp, no slow path), in FP64 the rounded square root.
 template <typename V>
@@ -1031,7 +1039,7 @@ template <typename V, typename T, int S>
 __device__ __forceinline__ void owner_update(const Group &g, int nunits, int nfix, int nbil, V *x, const T *xn, const V *yh,
                                              const V *zh, const T *mut, const T *mui, const T *p, T *wv, T eta_, T rho_,
                                              T irho_, V (&xnew)[S][3], V (&ynew)[S][3], V (&znew)[S][3], T &lrp,
-                                             T &lrd, T &lrc, T &lc) {
+                                             T &lrd, T &lrc, T &lc, int cslot0) {
     const V eta = V(eta_), rho = V(rho_), irho = V(irho_);
 #pragma unroll
     for (int sl = 0; sl < S; ++sl)
@@ -1039,7 +1047,7 @@ __device__ __forceinline__ void owner_update(const Group &g, int nunits, int nfi
         for (int t = 0; t < 3; ++t) xnew[sl][t] = ynew[sl][t] = znew[sl][t] = V(0);
 #pragma unroll
     for (int sl = 0; sl < S; ++sl) {
-        const int u = g.tid + sl * g.size;
+        const int u = slot_unit(g.tid + sl * g.size, nbil, cslot0);
         if (u >= nunits) continue;
         if (u < nbil) {
             // joint and drive rows: the identity; joint-limit rows (u >= nfix): the ray R+ (Sec. 3)
@@ -1086,20 +1094,22 @@ __device__ __forceinline__ void owner_update(const Group &g, int nunits, int nfi
 
 // The rows of this thread's units from registers into a row vector and back.
 template <int S>
-__device__ __forceinline__ void stash_rows(const Group &g, int nunits, int nbil, const double (&v)[S][3], double *dst) {
+__device__ __forceinline__ void stash_rows(const Group &g, int nunits, int nbil, const double (&v)[S][3], double *dst,
+                                           int cslot0) {
 #pragma unroll
     for (int sl = 0; sl < S; ++sl) {
-        const int u = g.tid + sl * g.size;
+        const int u = slot_unit(g.tid + sl * g.size, nbil, cslot0);
         if (u >= nunits) continue;
         const int r0 = u < nbil ? u : nbil + 3 * (u - nbil), cnt = u < nbil ? 1 : 3;
         for (int t = 0; t < cnt; ++t) dst[r0 + t] = v[sl][t];
     }
 }
 template <int S>
-__device__ __forceinline__ void unstash_rows(const Group &g, int nunits, int nbil, const double *src, double (&v)[S][3]) {
+__device__ __forceinline__ void unstash_rows(const Group &g, int nunits, int nbil, const double *src, double (&v)[S][3],
+                                             int cslot0) {
 #pragma unroll
     for (int sl = 0; sl < S; ++sl) {
-        const int u = g.tid + sl * g.size;
+        const int u = slot_unit(g.tid + sl * g.size, nbil, cslot0);
 #pragma unroll
         for (int t = 0; t < 3; ++t) v[sl][t] = 0.0;
         if (u >= nunits) continue;
@@ -1122,11 +1132,11 @@ __device__ __forceinline__ void owner_commit(const Group &g, int nunits, int nbi
                                              bool nesterov, bool restart, T beta_, const V (&xnew)[S][3],
                                              const V (&ynew)[S][3], const V (&znew)[S][3], bool hp, T *bb, double *bbd,
                                              double *init64, int mp, bool lag, T (&bprev)[S][3],
-                                             __nv_bfloat16 *chi, __nv_bfloat16 *clo) {
+                                             __nv_bfloat16 *chi, __nv_bfloat16 *clo, int cslot0) {
     const V beta_n = V(beta_);
 #pragma unroll
     for (int sl = 0; sl < S; ++sl) {
-        const int u = g.tid + sl * g.size;
+        const int u = slot_unit(g.tid + sl * g.size, nbil, cslot0);
         if (u >= nunits) continue;
         const int r0 = u < nbil ? u : nbil + 3 * (u - nbil);
         const int cnt = u < nbil ? 1 : 3;
@@ -2297,16 +2307,21 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
         T acc_a = T(1), c_prev = T(INFINITY);
         // v_f of the owner's rows in the iteration's precision, in registers for the whole loop (the
         // conversion from the FP64 v_f would otherwise run on the slow FP64 pipe every iteration)
+        // contacts owned from the first warp boundary after the joint rows when the slots have room
+        const int cslot0 = ((nbil + 31) & ~31) + (nunits - nbil) <= S * nthr ? ((nbil + 31) & ~31) : nbil;
         T vfo[S][3];
 #pragma unroll
         for (int sl = 0; sl < S; ++sl) {
-            const int u = tid + sl * nthr;
+            const int u = slot_unit(tid + sl * nthr, nbil, cslot0);
             const int r0 = u < nbil ? u : nbil + 3 * (u - nbil), cnt = u >= nunits ? 0 : u < nbil ? 1 : 3;
 #pragma unroll
             for (int t = 0; t < 3; ++t) vfo[sl][t] = t < cnt ? T(vfd[r0 + t]) : T(0);
         }
-        // b = v_f + Gamma(z^) - eta x - rho y^ - z^ and w = P x for the first iteration
-        for (int u = tid; u < nunits; u += nthr) {
+        // b = v_f + Gamma(z^) - eta x - rho y^ - z^ and w = P x for the first iteration (by the owners)
+#pragma unroll
+        for (int sl = 0; sl < S; ++sl) {
+            const int u = slot_unit(tid + sl * nthr, nbil, cslot0);
+            if (u >= nunits) continue;
             if (u < nbil) {
                 bb[u] = T(vfd[u]) - eta * x[u] - rho * yh[u] - zh[u];
                 wv[u] = p[u] * x[u];
@@ -2330,7 +2345,7 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
         T bprev[S][3];
 #pragma unroll
         for (int sl = 0; sl < S; ++sl) {
-            const int u = tid + sl * nthr;
+            const int u = slot_unit(tid + sl * nthr, nbil, cslot0);
             const int r0 = u < nbil ? u : nbil + 3 * (u - nbil), cnt = u >= nunits ? 0 : u < nbil ? 1 : 3;
 #pragma unroll
             for (int t = 0; t < 3; ++t) bprev[sl][t] = t < cnt ? bb[r0 + t] : T(0);
@@ -2478,12 +2493,12 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
                 // the two spare vectors), not in registers across the reduction
                 double xnD[S][3], ynD[S][3], znD[S][3];
                 owner_update<double, T, S>(g, nunits, nfix, nbil, x64, xn, yh64, zh64, mut, mui, p, wv, eta, rho, irho, xnD, ynD,
-                                           znD, lrp, lrd, lrc, lc);
-                stash_rows<S>(g, nunits, nbil, ynD, yn64);
-                stash_rows<S>(g, nunits, nbil, znD, zn64);
+                                           znD, lrp, lrd, lrc, lc, cslot0);
+                stash_rows<S>(g, nunits, nbil, ynD, yn64, cslot0);
+                stash_rows<S>(g, nunits, nbil, znD, zn64, cslot0);
             } else {
                 owner_update<T, T, S>(g, nunits, nfix, nbil, x, xn, yh, zh, mut, mui, p, wv, eta, rho, irho, xnT, ynT, znT, lrp,
-                                      lrd, lrc, lc);
+                                      lrd, lrc, lc, cslot0);
             }
             x_in64 = hpv;
             // Nesterov's next coefficients and the next iteration's kind depend on nothing the
@@ -2515,18 +2530,18 @@ __device__ void world_step(const StepArgs<T> &a, int w, unsigned char *smem, con
             lagged = lag_due && !hp;
             if (hpv) {
                 double xnD[S][3], ynD[S][3], znD[S][3];
-                unstash_rows<S>(g, nunits, nbil, x64, xnD);
-                unstash_rows<S>(g, nunits, nbil, yn64, ynD);
-                unstash_rows<S>(g, nunits, nbil, zn64, znD);
+                unstash_rows<S>(g, nunits, nbil, x64, xnD, cslot0);
+                unstash_rows<S>(g, nunits, nbil, yn64, ynD, cslot0);
+                unstash_rows<S>(g, nunits, nbil, zn64, znD, cslot0);
                 owner_commit<double, T, S>(g, nunits, nbil, y64, z64, yh64, zh64, vfd, vfo, mut, eta, rho, a.nesterov != 0,
                                            restart, beta_n, xnD, ynD, znD, true, bb, bbd, nullptr, mp, false, bprev,
-                                           nullptr, nullptr);
+                                           nullptr, nullptr, cslot0);
             } else {
                 // the iterates move to the FP64 vectors at this commit once the end game has started
                 double *init = hp && x64 != nullptr ? x64 : nullptr;
                 owner_commit<T, T, S>(g, nunits, nbil, y, z, yh, zh, vfd, vfo, mut, eta, rho, a.nesterov != 0, restart,
                                       beta_n, xnT, ynT, znT, hp, bb, bbd, init, mp, lagged, bprev,
-                                      a.mixed && !tm ? chi : nullptr, clo);
+                                      a.mixed && !tm ? chi : nullptr, clo, cslot0);
                 hpv = init != nullptr;
             }
             if (converged) break;

@@ -83,13 +83,16 @@ def check_report(rep, infos):
 # The PADMM stopping test bounds residuals, not the distance to the solution: slow modes of
 # D_eta_rho amplify it (the FP64 oracle stopped at 1e-6 differs from itself at 1e-12 by ~1e-3 on
 # these four-bars, at 1e-8 by ~1e-5).  Parity therefore runs the GPU to 1e-12 (FP64) / 1e-8 (FP32).
+@pytest.mark.parametrize("every", [8, 1], ids=["lagged_residual", "residual_every_iteration"])
 @pytest.mark.parametrize("precision,bar,tol", [("fp64", 1e-9, 1e-12), ("fp32", 1e-4, 1e-8), ("mixed", 1e-4, 1e-8)])
-def test_fourbar_parity_over_steps(K, precision, bar, tol):
-    """64 four-bars (1 ms): every step of a 20-step run starts the oracle from the GPU state."""
+def test_fourbar_parity_over_steps(K, precision, bar, tol, every):
+    """64 four-bars (1 ms): every step of a 20-step run starts the oracle from the GPU state; with
+    the refinement residual evaluated every 8th iteration (4th for the mixed mode's BF16 inverse
+    tiles, the default) and in every iteration."""
     ws = wg.make_fourbar(num_worlds=64, seed=0)
     dt = 1e-3
     q, u = rnd(ws.body_q0, precision), rnd(ws.body_u0, precision)
-    model = K.Model(ws, precision, K.make_params(rho=0.1))
+    model = K.Model(ws, precision, K.make_params(rho=0.1, residual_every=every))
     worst = (0.0, 0.0)
     for k in range(20):
         qg, ug, rep, _ = gpu_step(K, ws, q, u, None, dt, 20000, tol, precision, model=model)
