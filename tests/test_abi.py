@@ -101,7 +101,8 @@ def test_non_finite_contact_point_is_rejected(lib):
 
 def test_bad_parameters_are_invalid_arg(lib):
     ws = wg.make_fourbar(num_worlds=1)
-    for p in (K.make_params(rho=0.0), K.make_params(eta=-1.0), K.make_params(beta=2.0), K.make_params(warm_mode=7)):
+    for p in (K.make_params(rho=0.0), K.make_params(eta=-1.0), K.make_params(beta=2.0), K.make_params(warm_mode=7),
+              K.make_params(residual_every=-1), K.make_params(residual_every=1025)):
         got, _ = _create(ws, params=p)
         assert got == 1
 
